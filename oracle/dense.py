@@ -1,0 +1,160 @@
+"""Direct dense solve of the discrete DVM equations on tiny grids (second route to the fixed point).
+
+TEST INFRASTRUCTURE ONLY.  Written independently of ``dvm_oracle.c``: it assembles the steady
+discrete equations of Sec. II.A (Eq. BGK with the time derivative dropped, Eq. diffuse2 walls,
+periodic ends, second-order upwind differences) as one matrix and solves it with LAPACK, with no
+iteration, no lagging and no sweep order.  Unknowns: h[k, g] for every velocity k and gas cell g,
+plus the scalar c that borders the system:
+
+    (delta_c + v.D) h_k - delta_c M_k(h) + delta_c c = F v1_k      (every gas cell, velocity)
+    sum_gas sum_k W_k h_k = 0                                       (mean density zero)
+
+with M_k(h) = sum_j W_j h_j [1 + 2 v_k.v_j + (|v_k|^2 - 1)(|v_j|^2 - 1)] (the moments rho, u, tau
+of Sec. II.A inserted in L).  Wall values h_w = alpha rho_w + (1 - alpha) h(mirror v), with
+rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W at the gas cell owning the face.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _solid(mask, px, py, i, j):
+    ny, nx = mask.shape
+    if i < 0 or i >= nx:
+        if not px:
+            return True
+        i %= nx
+    if j < 0 or j >= ny:
+        if not py:
+            return True
+        j %= ny
+    return bool(mask[j, i])
+
+
+def assemble(prob):
+    """Dense bordered matrix B and right-hand side b; also the gas-cell index map."""
+    mask = prob.mask
+    ny, nx = mask.shape
+    px, py = prob.periodic_x, prob.periodic_y
+    v1, v2, W = prob.velocities()
+    K = len(W)
+    gas_cells = [(i, j) for j in range(ny) for i in range(nx) if not mask[j, i]]
+    gid = {cell: g for g, cell in enumerate(gas_cells)}
+    G = len(gas_cells)
+    n = K * G
+    idx = lambda k, g: k * G + g
+    B = np.zeros((n + 1, n + 1))
+    b = np.zeros(n + 1)
+    dx = prob.dx
+    nv = prob.nv
+    e = v1 * v1 + v2 * v2 - 1.0
+    # collision kernel C[k, j] = W_j [1 + 2 v_k.v_j + e_k e_j]
+    Ckern = W[None, :] * (1.0 + 2.0 * (np.outer(v1, v1) + np.outer(v2, v2)) + np.outer(e, e))
+    # wall normalisers per side: W (normal +x), E (-x), S (+y), N (-y)
+    normal = {"W": (1.0, 0.0), "E": (-1.0, 0.0), "S": (0.0, 1.0), "N": (0.0, -1.0)}
+    vn = {s: v1 * nxy[0] + v2 * nxy[1] for s, nxy in normal.items()}
+    norm = {s: float(np.sum(np.where(vn[s] > 0, vn[s] * W, 0.0))) for s in normal}
+
+    def mirror(k, side):
+        a, bb = divmod(k, nv)
+        if side in ("W", "E"):
+            a = nv - 1 - a
+        else:
+            bb = nv - 1 - bb
+        return a * nv + bb
+
+    def add_wall(row, coef, owner_g, side, k):
+        # coef multiplies h_w on the right-hand side -> -coef on the left
+        inc = np.flatnonzero(vn[side] < 0)
+        for j in inc:
+            B[row, idx(j, owner_g)] -= coef * prob.alpha * (-vn[side][j]) * W[j] / norm[side]
+        if prob.alpha < 1.0:
+            B[row, idx(mirror(k, side), owner_g)] -= coef * (1.0 - prob.alpha)
+
+    for g, (i, j) in enumerate(gas_cells):
+        d = prob.delta[j, i]
+        for k in range(K):
+            row = idx(k, g)
+            diag = d
+            for axis in (0, 1):
+                va = v1[k] if axis == 0 else v2[k]
+                s = 1 if va > 0 else -1
+                ca = abs(va) / dx
+                di, dj = (1, 0) if axis == 0 else (0, 1)
+                side = ("W" if s > 0 else "E") if axis == 0 else ("S" if s > 0 else "N")
+                i1, j1 = i - s * di, j - s * dj
+                i2, j2 = i - 2 * s * di, j - 2 * s * dj
+                if _solid(mask, px, py, i1, j1):
+                    diag += ca * 2.0
+                    add_wall(row, ca * 2.0, g, side, k)
+                elif _solid(mask, px, py, i2, j2):
+                    diag += ca * 5.0 / 3.0
+                    g1 = gid[(i1 % nx, j1 % ny)]
+                    B[row, idx(k, g1)] -= ca * 3.0
+                    add_wall(row, -ca * 4.0 / 3.0, g1, side, k)
+                else:
+                    diag += ca * 1.5
+                    g1 = gid[(i1 % nx, j1 % ny)]
+                    g2 = gid[(i2 % nx, j2 % ny)]
+                    B[row, idx(k, g1)] -= ca * 2.0
+                    B[row, idx(k, g2)] -= ca * (-0.5)
+            B[row, idx(k, g)] += diag
+            # collision: -delta M_k(h) at this cell
+            for jv in range(K):
+                B[row, idx(jv, g)] -= d * Ckern[k, jv]
+            B[row, n] += d
+            b[row] = prob.force * v1[k]
+    for g in range(G):
+        for k in range(K):
+            B[n, idx(k, g)] = W[k]
+    return B, b, gas_cells
+
+
+def solve(prob):
+    """Direct solution: h [K][ny][nx] (0 in solid cells), c, Q, and the assembled system."""
+    B, b, gas_cells = assemble(prob)
+    ny, nx = prob.mask.shape
+    K = prob.nv * prob.nv
+    G = len(gas_cells)
+    if np.all(prob.delta == 0.0):
+        # free-molecular: the bordering column vanishes; solve the consistent system without c
+        x_h, *_ = np.linalg.lstsq(B[:, :-1], b, rcond=None)
+        x = np.append(x_h, 0.0)
+    else:
+        x = np.linalg.solve(B, b)
+    h = np.zeros((K, ny, nx))
+    for g, (i, j) in enumerate(gas_cells):
+        h[:, j, i] = x[np.arange(K) * G + g]
+    v1, v2, W = prob.velocities()
+    u1 = np.tensordot(W * v1, h, axes=(0, 0))
+    Q = float(u1[prob.mask == 0].sum() * prob.dx * prob.dx / (nx * prob.dx))
+    return dict(h=h, c=float(x[-1]), Q=Q, B=B, b=b, x=x, gas_cells=gas_cells)
+
+
+def adjoint_gradient(prob, sol=None):
+    """dQ/d delta_c from the transposed bordered system B^T Lambda = [g; 0].
+
+    dQ/d delta_c = -sum_k Lambda[k, c] (h_kc - M_kc(h) + c), the derivative of the rows of cell c.
+    """
+    if sol is None:
+        sol = solve(prob)
+    B, x, gas_cells = sol["B"], sol["x"], sol["gas_cells"]
+    ny, nx = prob.mask.shape
+    v1, v2, W = prob.velocities()
+    K = len(W)
+    G = len(gas_cells)
+    n = K * G
+    g = np.zeros(n + 1)
+    dA_over_L = prob.dx * prob.dx / (nx * prob.dx)
+    for k in range(K):
+        g[k * G:(k + 1) * G] = W[k] * v1[k] * dA_over_L
+    lam = np.linalg.solve(B.T, g)
+    e = v1 * v1 + v2 * v2 - 1.0
+    Ckern = W[None, :] * (1.0 + 2.0 * (np.outer(v1, v1) + np.outer(v2, v2)) + np.outer(e, e))
+    grad = np.zeros((ny, nx))
+    c = x[-1]
+    for gi, (i, j) in enumerate(gas_cells):
+        hc = x[np.arange(K) * G + gi]
+        Mc = Ckern @ hc
+        grad[j, i] = -np.dot(lam[np.arange(K) * G + gi], hc - Mc + c)
+    return grad

@@ -1,0 +1,181 @@
+"""Seeded synthetic geometries and workload lists.
+
+This module only builds inputs: solid masks, Knudsen numbers, velocity-grid choices and sampled
+cell lists.  It holds none of the solver's arithmetic, so both the CUDA path and the CPU oracle can
+be fed from it.
+
+The paper's own geometries are a Weierstrass-Mandelbrot rough wall (Sec. II, Eq. WM) and three
+porous media shown only as images (Sec. III, Fig. 4).  The generators below make stand-ins with
+the same structure: a staircase wall on a Cartesian grid (Sec. II.A, "stair case") and periodic
+cells of non-overlapping disks.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea & Flood 2014): state += golden gamma, then two xor-shift-multiply mixes."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        """Uniform double in [0, 1) from the top 53 bits."""
+        return (self.next_u64() >> 11) * (1.0 / (1 << 53))
+
+    def randint(self, lo: int, hi: int) -> int:
+        """Integer uniform in [lo, hi] (inclusive)."""
+        return lo + int(self.uniform() * (hi - lo + 1))
+
+
+def plates_mask(nx: int = 4, ny: int = 32) -> np.ndarray:
+    """Two parallel plates: all cells gas; the walls sit just outside rows 0 and ny-1 (y not periodic)."""
+    return np.zeros((ny, nx), dtype=np.uint8)
+
+
+def rough_channel_mask(n: int = 128, height_frac: float = 0.2, width_frac: float = 0.25) -> np.ndarray:
+    """Plates with one rectangular block per period on both walls.
+
+    The period is n x n cells (Lx = H).  Each block is round(height_frac n) rows high and
+    round(width_frac n) columns wide, centred at x = Lx/2, on the bottom and the top wall.
+    """
+    mask = np.zeros((n, n), dtype=np.uint8)
+    hb = int(round(height_frac * n))
+    wb = int(round(width_frac * n))
+    x0 = n // 2 - wb // 2
+    mask[:hb, x0:x0 + wb] = 1
+    mask[n - hb:, x0:x0 + wb] = 1
+    return mask
+
+
+def porous_disks_mask(n: int = 256, porosity: float = 0.6, rmin: int = 8, rmax: int = 20,
+                      seed: int = 1, gap: int = 1, max_reject: int = 100000):
+    """Periodic n x n cell of random non-overlapping disks (both axes periodic).
+
+    Disks with integer radius U{rmin..rmax} and centre U[0, n)^2 are added in sequence; a disk is
+    rejected when its periodic centre distance to an earlier disk is below r1 + r2 + gap.  Adding
+    stops when the gas fraction reaches the target.  A cell is solid when its centre lies inside a
+    disk.  Returns (mask, achieved porosity).  Raises ValueError after max_reject rejections in a row.
+    """
+    rng = SplitMix64(seed)
+    mask = np.zeros((n, n), dtype=np.uint8)
+    disks = []
+    yc, xc = np.mgrid[0:n, 0:n]
+    xc = xc + 0.5
+    yc = yc + 0.5
+    rejects = 0
+    while (1.0 - mask.mean()) > porosity:
+        r = rng.randint(rmin, rmax)
+        cx = rng.uniform() * n
+        cy = rng.uniform() * n
+        ok = True
+        for (ox, oy, orad) in disks:
+            dxp = abs(cx - ox)
+            dyp = abs(cy - oy)
+            dxp = min(dxp, n - dxp)
+            dyp = min(dyp, n - dyp)
+            if dxp * dxp + dyp * dyp < (r + orad + gap) ** 2:
+                ok = False
+                break
+        if not ok:
+            rejects += 1
+            if rejects > max_reject:
+                raise ValueError("porous_disks_mask: cannot reach the target porosity")
+            continue
+        rejects = 0
+        disks.append((cx, cy, r))
+        ddx = np.abs(xc - cx)
+        ddy = np.abs(yc - cy)
+        ddx = np.minimum(ddx, n - ddx)
+        ddy = np.minimum(ddy, n - ddy)
+        mask[(ddx * ddx + ddy * ddy) < r * r] = 1
+    return mask, float(1.0 - mask.mean())
+
+
+def kn_to_delta(kn: float) -> float:
+    """Rarefaction delta = sqrt(pi) / (2 Kn) (coefficient of the BGK operator); Kn = inf gives 0."""
+    return 0.0 if math.isinf(kn) else math.sqrt(math.pi) / (2.0 * kn)
+
+
+@dataclass
+class Instance:
+    """One solve: geometry, periodicity, Knudsen number and velocity grid."""
+
+    name: str
+    mask: np.ndarray
+    periodic_x: bool
+    periodic_y: bool
+    kn: float
+    quad: tuple            # (kind, n, vmax): kind in {"gh", "nc", "cubic"}
+    extra: dict = field(default_factory=dict)
+
+
+def plates_instance(kn: float = 0.1, nx: int = 4, ny: int = 32, nv: int = 12) -> Instance:
+    """Force-driven Poiseuille flow between two diffuse plates; Gauss-Hermite nv x nv velocities."""
+    return Instance(f"plates{nx}x{ny}_gh{nv}_kn{kn:g}", plates_mask(nx, ny), True, False, kn, ("gh", nv, 0.0))
+
+
+def rough_instance(kn: float, n: int = 128, nv: int = 32, vmax: float = 5.0) -> Instance:
+    """Rough channel, n x n cells, trapezoid Newton-Cotes nv x nv velocities on [-vmax, vmax]."""
+    return Instance(f"rough{n}_nc{nv}_kn{kn:g}", rough_channel_mask(n), True, False, kn, ("nc", nv, vmax))
+
+
+def porous_instance(kn: float, n: int = 256, nv: int = 48, porosity: float = 0.6, seed: int = 1,
+                    rmin: int = 8, rmax: int = 20) -> Instance:
+    """Periodic disk medium, n x n cells, cubic nv x nv velocities (Eq. nonuniform_v)."""
+    mask, phi = porous_disks_mask(n, porosity, rmin, rmax, seed)
+    return Instance(f"porous{n}_phi{porosity:g}_s{seed}_cubic{nv}_kn{kn:g}", mask, True, True, kn,
+                    ("cubic", nv, 4.0), {"porosity": phi, "seed": seed})
+
+
+def batched_instances(count: int = 64, seed0: int = 0):
+    """Mixed batch: side in {64..256}, rough or porous, Kn log-uniform in [0.01, 10], cubic Nv in {16..48}.
+
+    Instance i uses SplitMix64(seed0 + i) for every choice.  Porous media have porosity U[0.6, 0.75]
+    and disk radii scaled by side/256 (at least 4 cells), so that small cells still reach the target.
+    """
+    sides = [64, 96, 128, 192, 256]
+    nvs = [16, 24, 32, 40, 48]
+    out = []
+    for i in range(count):
+        rng = SplitMix64(seed0 + i)
+        side = sides[rng.randint(0, len(sides) - 1)]
+        nv = nvs[rng.randint(0, len(nvs) - 1)]
+        kn = 10.0 ** (-2.0 + 3.0 * rng.uniform())
+        if rng.uniform() < 0.5:
+            inst = Instance(f"b{i}_rough{side}_cubic{nv}_kn{kn:.4g}", rough_channel_mask(side), True, False,
+                            kn, ("cubic", nv, 4.0))
+        else:
+            phi = 0.6 + 0.15 * rng.uniform()
+            rmin = max(4, int(round(8 * side / 256)))
+            rmax = max(rmin + 1, int(round(20 * side / 256)))
+            mask, ach = porous_disks_mask(side, phi, rmin, rmax, seed=1000 + i)
+            inst = Instance(f"b{i}_porous{side}_cubic{nv}_kn{kn:.4g}", mask, True, True, kn,
+                            ("cubic", nv, 4.0), {"porosity": ach})
+        out.append(inst)
+    return out
+
+
+def sample_gas_cells(mask: np.ndarray, count: int, seed: int = 7) -> np.ndarray:
+    """count distinct gas-cell flat indices drawn with SplitMix64 (partial Fisher-Yates)."""
+    gas = np.flatnonzero(mask.ravel() == 0)
+    rng = SplitMix64(seed)
+    gas = gas.copy()
+    count = min(count, len(gas))
+    for t in range(count):
+        j = t + int(rng.uniform() * (len(gas) - t))
+        gas[t], gas[j] = gas[j], gas[t]
+    return np.sort(gas[:count])

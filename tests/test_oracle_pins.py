@@ -1,0 +1,226 @@
+"""Pins for the CPU oracle: closed forms, library routines, a second solution route, invariants.
+
+None of these re-types the oracle's own formulas: each compares it with something the paper or the
+mathematics fixes independently.
+  * Gauss-Hermite rule          vs numpy.polynomial.hermite.hermgauss (library routine)
+  * quadrature moment sums      vs erf closed forms
+  * free-molecular plates       vs the exact discrete solution h = v1 d / |v2| (stencil exact on lines)
+  * continuum limit             vs Q = delta/12 + sigma_P/2 with the published BGK slip coefficient
+  * iterative fixed point       vs a direct dense LAPACK solve of the same discrete equations
+  * adjoint gradient            vs the dense transposed solve and central finite differences
+  * symmetry and conservation   mirror symmetries of symmetric geometries, zero mass shift for
+                                exact quadrature
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_1704_03126_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- quadrature (Sec. II.A)
+
+@pytest.mark.parametrize("n", [2, 4, 8, 12, 16, 24, 32, 48])
+def test_gauss_hermite_matches_numpy(n):
+    x, w = oracle.quadrature("gh", n)
+    xr, wr = np.polynomial.hermite.hermgauss(n)
+    assert np.max(np.abs(x - xr)) < 1e-12 * max(1.0, np.abs(xr).max())
+    assert np.max(np.abs(w - wr / math.sqrt(math.pi))) < 1e-14
+
+
+def test_newton_cotes_moments_match_erf():
+    x, w = oracle.quadrature("nc", 32, 5.0)
+    assert np.allclose(x, np.linspace(-5, 5, 32), atol=1e-15, rtol=0)
+    # exact truncated moments of exp(-x^2)/sqrt(pi) on [-5, 5]
+    m0 = math.erf(5.0)
+    m2 = 0.5 * math.erf(5.0) - 5.0 * math.exp(-25.0) / math.sqrt(math.pi)
+    # trapezoid error (Euler-Maclaurin, first term): h^2/12 (f'(5) - f'(-5))
+    hstep = 10.0 / 31.0
+    fp = lambda t: -2.0 * t * math.exp(-t * t) / math.sqrt(math.pi)
+    fp2 = lambda t: (2.0 * t - 2.0 * t ** 3) * math.exp(-t * t) / math.sqrt(math.pi)
+    assert abs(w.sum() - (m0 + hstep ** 2 / 12.0 * (fp(5.0) - fp(-5.0)))) < 5e-13
+    assert abs((w * x * x).sum() - (m2 + hstep ** 2 / 12.0 * (fp2(5.0) - fp2(-5.0)))) < 2e-11
+
+
+@pytest.mark.parametrize("n,tol0,tol2,tol4", [(16, 1e-4, 1e-3, 2e-3), (32, 1e-7, 1e-6, 2e-5),
+                                            (48, 1e-7, 1e-6, 2e-5)])
+def test_cubic_grid_nodes_and_moments(n, tol0, tol2, tol4):
+    x, w = oracle.quadrature("cubic", n)
+    # Eq. (nonuniform_v): extreme nodes at +-4, symmetric, clustered at 0
+    assert abs(x[-1] - 4.0) < 1e-14 and abs(x[0] + 4.0) < 1e-14
+    assert np.allclose(x, -x[::-1], atol=1e-15)
+    assert abs(x[n // 2]) < 4.0 / (n - 1) ** 3 * 1.0000001
+    # moments 1, 1/2, 3/4 of exp(-x^2)/sqrt(pi); the rule is a trapezoid in s of a smooth
+    # integrand truncated at |v| = 4 (erfc(4) ~ 1.5e-8), so the defects shrink quickly with n
+    assert abs(w.sum() - 1.0) < tol0
+    assert abs((w * x * x).sum() - 0.5) < tol2
+    assert abs((w * x ** 4).sum() - 0.75) < tol4
+
+
+# ---------------------------------------------------------------- free-molecular plates
+
+@pytest.mark.parametrize("quad", [("gh", 12, 0.0), ("nc", 32, 5.0)])
+def test_free_molecular_plates_exact(quad):
+    """delta = 0 between diffuse plates: v2 dh/dy = v1 with h = 0 at the wall the molecule left
+    (rho_w = 0 by oddness in v1), so h = v1 d / |v2| with d the distance from that wall; the
+    second-order upwind stencils (interior, one- and two-point wall forms) are exact on it."""
+    ny = 32
+    p = oracle.Problem.make(inputs.plates_mask(4, ny), True, False, 0.0, quad)
+    # a fixed number of sweeps: the u1-based stop ends earlier, while grazing velocities still
+    # carry lagged seam values around the periodic x axis
+    r = oracle.solve(p, tol=0.0, max_iter=600)
+    v1, v2, W = p.velocities()
+    y = (np.arange(ny) + 0.5) / ny
+    d = np.where(v2[:, None] > 0, y[None, :], 1.0 - y[None, :])
+    h_exact = v1[:, None] * d / np.abs(v2)[:, None]
+    assert np.max(np.abs(r["h"][:, :, 0] - h_exact)) < 1e-10 * np.abs(h_exact).max()
+    q_exact = 0.5 * np.sum(W * v1 * v1 / np.abs(v2))
+    assert abs(r["Q"] - q_exact) < 1e-11 * q_exact
+
+
+# ---------------------------------------------------------------- continuum limit (Sec. III k_a)
+
+def test_continuum_limit_slip_coefficient():
+    """k_a = sqrt(4/pi) Q Kn -> 1/12 needs Q -> delta/12; the next term is sigma_P/2 (BGK slip).
+    Richardson in 1/delta from delta = 10 and 20 removes the O(1/delta) term."""
+    gold = json.load(open(os.path.join(GOLDEN, "bgk_slip_coefficient.json")))
+    qs = {}
+    for delta, ny in [(10.0, 64), (20.0, 128)]:
+        p = oracle.Problem.make(inputs.plates_mask(2, ny), True, False, delta, ("gh", 16, 0.0))
+        r = oracle.solve(p, tol=1e-10, max_iter=100000)
+        assert r["converged"]
+        qs[delta] = r["Q"] - delta / 12.0
+    slip_half = 2.0 * qs[20.0] - qs[10.0]
+    assert abs(slip_half - gold["value"] / 2.0) < gold["abs_uncertainty_for_test"] / 2.0
+    # apparent permeability of the plates approaches H^2/12 from above
+    for delta in (10.0, 20.0):
+        kn = math.sqrt(math.pi) / (2 * delta)
+        k_a = math.sqrt(4 / math.pi) * (qs[delta] + delta / 12.0) * kn
+        assert 1.0 / 12.0 < k_a < 1.0 / 12.0 * (1.0 + 12.0 / delta)
+
+
+# ---------------------------------------------------------------- dense direct solve
+
+def _tiny_cases():
+    block = np.zeros((6, 6), np.uint8)
+    block[2:4, 2:4] = 1
+    notch = np.zeros((8, 4), np.uint8)
+    notch[0:2, 1] = 1
+    notch[7, 2:4] = 1
+    dvar = np.full((6, 6), 1.3)
+    dvar[0, 0] = 0.4
+    dvar[5, 1] = 2.6
+    return [
+        ("block_periodic_cubic6", block, True, True, dvar, ("cubic", 6, 4.0), 1.0),
+        ("block_periodic_gh6_alpha0.6", block, True, True, 2.0, ("gh", 6, 0.0), 0.6),
+        ("plates_gh8", np.zeros((8, 4), np.uint8), True, False, 0.7, ("gh", 8, 0.0), 1.0),
+        ("notched_nc6", notch, True, False, 5.0, ("nc", 6, 4.0), 1.0),
+        ("block_periodic_nc8_small_delta", block, True, True, 0.05, ("nc", 8, 4.0), 1.0),
+    ]
+
+
+@pytest.mark.parametrize("case", _tiny_cases(), ids=lambda c: c[0])
+def test_iteration_matches_dense_solve(case):
+    name, mask, px, py, delta, quad, alpha = case
+    p = oracle.Problem.make(mask, px, py, delta, quad, alpha=alpha)
+    ds = dense.solve(p)
+    r = oracle.solve(p, tol=1e-14, max_iter=400000)
+    assert r["converged"]
+    assert abs(r["Q"] - ds["Q"]) < 1e-11 * abs(ds["Q"])
+    assert np.max(np.abs(r["h"] - ds["h"])) < 1e-10 * max(1.0, np.abs(ds["h"]).max())
+    assert abs(r["c"] - ds["c"]) < 1e-11
+    # the projection holds mean density at zero
+    assert abs(r["rho"][mask == 0].mean()) < 1e-13
+
+
+def test_dense_free_molecular_cubic_closed_form():
+    """The cubic grid's grazing velocities make the lagged iteration slow at delta = 0; the direct
+    solve of the same equations still reproduces Q = 1/2 sum W v1^2 / |v2| exactly."""
+    p = oracle.Problem.make(inputs.plates_mask(2, 8), True, False, 0.0, ("cubic", 8, 4.0))
+    ds = dense.solve(p)
+    v1, v2, W = p.velocities()
+    q_exact = 0.5 * np.sum(W * v1 * v1 / np.abs(v2))
+    assert abs(ds["Q"] - q_exact) < 1e-10 * q_exact
+
+
+# ---------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("case", _tiny_cases()[:4], ids=lambda c: c[0])
+def test_adjoint_matches_dense_transpose(case):
+    name, mask, px, py, delta, quad, alpha = case
+    p = oracle.Problem.make(mask, px, py, delta, quad, alpha=alpha)
+    ds = dense.solve(p)
+    g_dense = dense.adjoint_gradient(p, ds)
+    r = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_it, q_id, iters, ok = oracle.adjoint(p, r["h"], r["c"], tol=1e-13, max_iter=400000)
+    assert ok
+    scale = np.abs(g_dense).max()
+    assert np.max(np.abs(g_it - g_dense)) < 1e-9 * scale
+    # forward/adjoint identity Q = F sum z v1
+    assert abs(q_id - r["Q"]) < 1e-10 * abs(r["Q"])
+    assert np.all(g_it[mask == 1] == 0.0)
+
+
+def test_adjoint_matches_central_differences():
+    name, mask, px, py, delta, quad, alpha = _tiny_cases()[0]
+    p = oracle.Problem.make(mask, px, py, delta, quad, alpha=alpha)
+    g = dense.adjoint_gradient(p)
+    for (j, i) in [(0, 0), (5, 1), (1, 4), (4, 5)]:
+        step = 1e-5 * p.delta[j, i]
+        qs = []
+        for sgn in (1, -1):
+            d = p.delta.copy()
+            d[j, i] += sgn * step
+            qs.append(dense.solve(oracle.Problem(p.mask, px, py, d, p.xv, p.wv, alpha))["Q"])
+        fd = (qs[0] - qs[1]) / (2 * step)
+        assert abs(fd - g[j, i]) < 1e-6 * np.abs(g).max()
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_plates_invariants_and_zero_mass_shift():
+    """Plates: rho = tau = u2 = 0 (h odd in v1), x-invariance, u1 symmetric about the mid-plane;
+    with Gauss-Hermite weights (exact low moments) the scheme conserves mass, so c = 0."""
+    p = oracle.Problem.make(inputs.plates_mask(4, 32), True, False, oracle.delta_from_kn(0.1), ("gh", 12, 0.0))
+    r = oracle.solve(p, tol=1e-12, max_iter=100000)
+    assert r["converged"]
+    for f in ("rho", "tau", "u2"):
+        assert np.abs(r[f]).max() < 1e-12
+    u1 = r["u1"]
+    assert np.abs(u1 - u1[:, :1]).max() < 1e-12
+    assert np.abs(u1[:, 0] - u1[::-1, 0]).max() < 1e-12
+    assert abs(r["c"]) < 1e-13
+    assert r["Q"] > oracle.delta_from_kn(0.1) / 12.0  # slip only adds flow
+
+
+def test_rough_channel_mirror_symmetries():
+    """Blocks centred in x on both walls: u1 even in x and y, u2 odd in both, rho odd in x."""
+    mask = inputs.rough_channel_mask(32)
+    p = oracle.Problem.make(mask, True, False, oracle.delta_from_kn(1.0), ("nc", 8, 4.0))
+    r = oracle.solve(p, tol=1e-12, max_iter=100000)
+    assert r["converged"]
+    gas = mask == 0
+    u1, u2, rho = r["u1"], r["u2"], r["rho"]
+    tol = 1e-10 * np.abs(u1).max()
+    assert np.abs((u1 - u1[:, ::-1])[gas]).max() < tol
+    assert np.abs((u1 - u1[::-1, :])[gas]).max() < tol
+    assert np.abs((u2 + u2[:, ::-1])[gas]).max() < tol
+    assert np.abs((u2 + u2[::-1, :])[gas]).max() < tol
+    assert np.abs((rho + rho[:, ::-1])[gas]).max() < tol
+
+
+def test_sweep_selected_reproduces_fixed_point():
+    """At convergence one more sweep of any velocity returns the same h (fixed point of Eq. iteration)."""
+    mask = inputs.rough_channel_mask(16)
+    p = oracle.Problem.make(mask, True, False, 2.0, ("nc", 8, 4.0))
+    r = oracle.solve(p, tol=1e-14, max_iter=100000)
+    ks = [0, 5, 17, 40, 63]
+    out = oracle.sweep_selected(p, r["h"], r["c"], ks)
+    assert np.abs(out - r["h"][ks]).max() < 1e-11 * np.abs(r["h"]).max()
