@@ -1,0 +1,179 @@
+/*
+ * dvm.h -- C ABI of libdvm, a GB300 (sm_103a) solver for the steady linearized BGK equation by the
+ * discrete velocity method (DVM), for small force-driven gas flows through irregular 2D channels.
+ *
+ * Paper: S. Lindsay, W. Su, H. Liu and L. Wu, "Comparative study of the discrete velocity and
+ * lattice Boltzmann methods for rarefied gas flows through irregular channels", arXiv:1704.03126.
+ *
+ * The problem (Sec. II.A, Eq. BGK with the time derivative dropped):
+ *     v . grad h = L(rho, u, tau) - delta h + F v1,   L = delta [rho + 2 u.v + tau (|v|^2 - 1)],
+ * f = f_eq (1 + h), f_eq = exp(-|v|^2)/pi, delta = sqrt(pi)/(2 Kn) (Eq. BGK), moments
+ * rho = int h f_eq, u = int v h f_eq, tau = int |v|^2 h f_eq - rho, diffuse walls (Eq. diffuse2),
+ * staircase geometry on a Cartesian mask, periodic inlet/outlet (Sec. II.A; Sec. III for porous
+ * media with both axes periodic), the unit body force F v1 driving Poiseuille flow (Sec. III), and
+ * the source iteration of Eq. (iteration) with second-order upwind differences.
+ *
+ * Conventions for every call:
+ *   - Arrays named [ny][nx] are row-major with the x1 index fastest; row j is at x2 = (j + 1/2) H/ny.
+ *   - Pointers marked "host" are ordinary host memory; the library never keeps them.
+ *   - The library copies every input; outputs are caller-allocated.
+ *   - Calls return a dvm_status and never abort; dvm_last_error() describes the last failure on a
+ *     context.  A context is not thread-safe: one host thread at a time.
+ *   - Work runs on the CUDA stream given to dvm_create (NULL = the library creates its own); calls
+ *     that return host data synchronise that stream.
+ */
+#ifndef DVM_H
+#define DVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dvm_ctx dvm_ctx; /* opaque; created by dvm_create, released by dvm_destroy */
+
+typedef enum {
+  DVM_OK = 0,
+  DVM_EINVAL = 1,   /* invalid argument or unsupported configuration */
+  DVM_ENOMEM = 2,   /* host or device allocation failed */
+  DVM_ECUDA = 3,    /* a CUDA runtime call failed (message in dvm_last_error) */
+  DVM_ENOCONV = 4,  /* max_iter reached before the stopping test passed (results are the last iterate) */
+  DVM_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+  DVM_ENUMERIC = 6, /* a NaN or Inf appeared in the moments */
+  DVM_ESTATE = 7    /* call out of order (e.g. results requested before a successful solve) */
+} dvm_status;
+
+typedef enum {
+  DVM_QUAD_GAUSS_HERMITE = 0, /* n Gauss-Hermite nodes per axis */
+  DVM_QUAD_NEWTON_COTES = 1,  /* closed trapezoid rule on n equispaced nodes in [-vmax, vmax] */
+  DVM_QUAD_CUBIC = 2          /* Eq. (nonuniform_v): v = 4 s^3/(n-1)^3, s = -n+1, -n+3, ..., n-1 */
+} dvm_quad_kind;
+
+/* Velocity grid: the tensor product of one 1D rule on each axis; n must be even (no zero node). */
+typedef struct {
+  int kind;    /* dvm_quad_kind */
+  int n;       /* nodes per axis, 2..64, even */
+  double vmax; /* half-width for DVM_QUAD_NEWTON_COTES; ignored otherwise */
+} dvm_quad;
+
+typedef enum {
+  DVM_FP64 = 0,      /* distribution stored and swept in FP64 */
+  DVM_FP32_ACC64 = 1 /* distribution stored and swept in FP32; moments, wall fluxes, residual and Q in FP64 */
+} dvm_precision;
+
+typedef struct {
+  int nx, ny;                 /* cells along x1 (flow) and x2; both >= 2 */
+  int periodic_x, periodic_y; /* 1 = periodic axis; a non-periodic axis is closed by diffuse walls */
+  double ly;                  /* domain height H along x2 (cells are square, size ly/ny); > 0 */
+  double kn;                  /* Knudsen number (> 0, +INFINITY allowed for delta = 0), or <= 0 ... */
+  double delta;               /* ... to give delta >= 0 directly instead; exactly one of the two is set */
+  dvm_quad quad;
+  double accommodation;       /* 1 = fully diffuse walls (the paper's case); other values: DVM_EINVAL */
+  int precision;              /* dvm_precision */
+  double force;               /* body-force source coefficient F along x1 (1 for the paper's Poiseuille flow) */
+  int store_distribution;     /* 1 = also keep h in device memory (needed by dvm_distribution) */
+  int sweep_warps;            /* warps per sweep block, 1..32; 0 = choose automatically */
+} dvm_params;
+
+/* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
+ * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape. */
+dvm_status dvm_params_init(dvm_params *params);
+
+/* Build a solver for one geometry.
+ *   mask      host, uint8 [ny][nx]; nonzero = solid cell.  At least one gas cell.
+ *   params    host; copied.
+ *   stream    a cudaStream_t on the current device, or NULL.
+ *   out       receives the context; unchanged on failure.
+ * Allocates the device state (about 4 * ncell * 64 bytes of tables plus seams, and with
+ * store_distribution the full h: ncell * n^2 * (4 or 8) bytes) and sets the state to h = 0. */
+dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *stream, dvm_ctx **out);
+
+/* Per-cell collision rate delta_c (host, double [ny][nx], >= 0; solid entries ignored), or NULL to
+ * return to the uniform value of the parameters.  Resets the state to h = 0.  This is the field the
+ * adjoint differentiates. */
+dvm_status dvm_set_delta_field(dvm_ctx *ctx, const double *delta_c);
+
+/* Restart from h = 0 (the state a new context has). */
+dvm_status dvm_reset(dvm_ctx *ctx);
+
+/* Source iteration (Eq. iteration) from the current state until the stopping test passes or
+ * max_iter sweeps have run.  After sweep n the test uses eps_n = sum|u1^n - u1^(n-1)| / sum|u1^n|
+ * over gas cells and r = (eps_n / eps_(n-4))^(1/4) clipped to [0, 0.9999]; it passes when n >= 5
+ * and eps_n / (1 - r) < tol (an estimate of the relative distance to the fixed point; the paper
+ * stops on eps_n < 1e-5, Sec. II.A).  iters (may be NULL) receives the sweeps run by this call,
+ * est (may be NULL) the last estimate.  Returns DVM_ENOCONV if max_iter is reached. */
+dvm_status dvm_solve(dvm_ctx *ctx, double tol, int max_iter, int *iters, double *est);
+
+/* Run exactly n sweeps with no stopping test (timing and warm-up).  Synchronises the stream. */
+dvm_status dvm_iterate(dvm_ctx *ctx, int n);
+
+/* Mass flow rate Q = int v1 f dv dx1 dx2 / Lx = sum_gas u1 dA / Lx (Sec. III, Eq. Q) and apparent
+ * permeability k_a = sqrt(4/pi) Q Kn (Sec. III, Eq. k_a; NaN when delta is a field or 0).
+ * k_a may be NULL.  DVM_ESTATE before the first sweep. */
+dvm_status dvm_flowrate(const dvm_ctx *ctx, double *Q, double *k_a);
+
+/* Macroscopic fields of the current state (Sec. II.A): host double [ny][nx] each, NaN in solid
+ * cells; any pointer may be NULL.  tau is the temperature perturbation int |v|^2 h f_eq - rho. */
+dvm_status dvm_fields(const dvm_ctx *ctx, double *rho, double *u1, double *u2, double *tau);
+
+/* Diagnostics of the current state: sweeps run since the last reset, last eps and estimate, the
+ * accumulated mass shift c of the mean-density projection, and the stored status of the last solve. */
+typedef struct {
+  int iterations;
+  double eps, est, mass_shift, Q;
+  int status;
+} dvm_info;
+dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info);
+
+/* Distribution h of selected velocities (needs store_distribution = 1).  ks: host int [nk] with
+ * k = a * n + b for v = (x_a, x_b) on the 1D nodes in ascending order.  out: host double
+ * [nk][ny][nx]; solid cells 0. */
+dvm_status dvm_distribution(const dvm_ctx *ctx, const int *ks, int nk, double *out);
+
+/* The 1D nodes and weights the context uses (host double [n] each; weights approximate
+ * int g(x) exp(-x^2)/sqrt(pi) dx). */
+dvm_status dvm_quadrature(const dvm_ctx *ctx, double *nodes, double *weights);
+
+/* The 1D nodes (ascending) and weights of a velocity-grid description, without a context or a GPU
+ * (host double [q->n] each).  Gauss-Hermite uses the Golub-Welsch eigenvalue method. */
+dvm_status dvm_velocity_grid(const dvm_quad *q, double *nodes, double *weights);
+
+/* Batched solves: several contexts (independent geometries, Kn and velocity grids, one precision and
+ * one store_distribution setting, one device) advanced by one launch of each kernel per sweep, on the
+ * stream of the first context.  A batch records the contexts' configuration when it is created:
+ * re-create it after dvm_set_delta_field on a member.  The contexts must outlive the batch. */
+typedef struct dvm_batch dvm_batch;
+dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out);
+/* Source iteration of every member until each passes the stopping test of dvm_solve or has run
+ * max_iter sweeps in this call; converged members stop (their blocks return at once).  per (host,
+ * [n], may be NULL) receives each member's status; returns DVM_OK when every member converged,
+ * else the first failing status. */
+dvm_status dvm_batch_run(dvm_batch *batch, double tol, int max_iter, dvm_status *per);
+/* Exactly n sweeps of every member, no stopping test.  Synchronises the stream. */
+dvm_status dvm_batch_iterate(dvm_batch *batch, int n);
+/* Device time of the last single sweep run by dvm_batch_iterate(batch, 1): the sweep kernel and the
+ * two finalize kernels, in milliseconds (CUDA events recorded around them on the batch stream). */
+dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms);
+/* Kernel launches issued per sweep of the batch (sweep + finalize kernels). */
+int dvm_batch_kernels_per_sweep(const dvm_batch *batch);
+void dvm_batch_destroy(dvm_batch *batch);
+
+/* One-shot batch: create, run, destroy. */
+dvm_status dvm_batch_solve(dvm_ctx *const *ctxs, int n, double tol, int max_iter, dvm_status *per);
+
+/* Description of the last error on ctx (or of the last dvm_create failure when ctx is NULL). */
+const char *dvm_last_error(const dvm_ctx *ctx);
+
+/* Static name of a status code. */
+const char *dvm_status_string(dvm_status status);
+
+/* Release the context and its device memory.  NULL is ignored. */
+void dvm_destroy(dvm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DVM_H */

@@ -159,10 +159,20 @@ def delta_from_kn(kn: float) -> float:
     return 0.0 if math.isinf(kn) else math.sqrt(math.pi) / (2.0 * kn)
 
 
-def solve(prob: Problem, tol: float = 1e-10, max_iter: int = 100000, h0=None, c0: float = 0.0):
-    """Source iteration (Eq. iteration) to the stopping rule; returns a dict of results."""
+def solve(prob: Problem, tol: float = 1e-10, max_iter: int = 100000, h0=None, c0: float = 0.0,
+          inplace: bool = False):
+    """Source iteration (Eq. iteration) to the stopping rule; returns a dict of results.
+
+    h0: starting state [K][ny][nx] (zeros when None); with inplace=True it is advanced in place."""
     K = prob.nv * prob.nv
-    h = np.zeros((K, prob.ny, prob.nx)) if h0 is None else np.array(h0, dtype=np.float64, copy=True)
+    if h0 is None:
+        h = np.zeros((K, prob.ny, prob.nx))
+    elif inplace:
+        h = h0
+        if h.dtype != np.float64 or not h.flags.c_contiguous or h.shape != (K, prob.ny, prob.nx):
+            raise ValueError("in-place state must be a C-contiguous float64 array [K][ny][nx]")
+    else:
+        h = np.array(h0, dtype=np.float64, copy=True)
     rho, u1, u2, tau = (np.zeros((prob.ny, prob.nx)) for _ in range(4))
     eps_hist = np.zeros(max_iter)
     res = _Result()

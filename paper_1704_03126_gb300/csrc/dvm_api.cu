@@ -1,0 +1,832 @@
+// dvm_api.cu -- the C ABI of libdvm (include/dvm.h): contexts, device tables, the CUDA-graph solve
+// loop and batched solves.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dvm.h"
+#include "dvm_device.cuh"
+#include "dvm_kernels.h"
+#include "dvm_tables.h"
+
+using namespace dvm;
+
+struct dvm_ctx {
+  dvm_params P{};
+  int nx = 0, ny = 0, ncell = 0, nv = 0, half = 0, gq = 0, ngroups = 0;
+  bool fp64 = true, store_h = false, uniform = true;
+  double delta = 0.0, kn = 0.0;
+  std::vector<double> x1, w1;
+  Geometry geo;
+  cudaStream_t stream = nullptr;     // work stream (user's or own)
+  cudaStream_t cap_stream = nullptr; // private stream used for graph capture
+  bool own_stream = false;
+  int device = 0;
+  // device memory
+  void *d_vel = nullptr, *d_inv = nullptr, *d_rec = nullptr;
+  uint32_t *d_code4 = nullptr;
+  int *d_hw_src = nullptr;
+  double *d_delta_field = nullptr, *d_acc = nullptr, *d_facc = nullptr, *d_mom = nullptr, *d_u1prev = nullptr;
+  void *d_seamx = nullptr, *d_seamy = nullptr, *d_h = nullptr;
+  DeviceState *d_state = nullptr;
+  InstanceDesc hdesc{};
+  InstanceDesc *d_desc = nullptr;
+  int *d_sweep_map = nullptr, *d_fin_map = nullptr;
+  int warps = 0, cmax = 0;
+  dvm_batch *self = nullptr;       // batch of this context alone (built on first use)
+  DeviceState *h_state = nullptr;  // pinned
+  std::string err;
+};
+
+// A set of contexts advanced together: one launch of each kernel per sweep, replayed as CUDA graphs.
+struct dvm_batch {
+  std::vector<dvm_ctx *> ctxs;
+  bool fp64 = true, store_h = false, uniform = true;
+  int warps = 0, cmax = 0, nsweep = 0, nfin = 0;
+  InstanceDesc *d_descs = nullptr;
+  int *d_smap = nullptr, *d_fmap = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t g_many = nullptr;  // m sweeps
+  cudaGraphExec_t g_one = nullptr;   // one sweep with timing events
+  int m = 1;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool timed = false;
+};
+
+namespace {
+
+std::string g_create_error;
+
+dvm_status fail(dvm_ctx *ctx, dvm_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define DVM_CUDA(ctx, call)                                                                     \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(ctx, DVM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+constexpr int kFinBlock = 256;
+
+template <typename T>
+void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T> &inv) {
+  const int half = c->half, gq = c->gq;
+  const double dx = c->P.ly / c->ny;
+  vel.assign((size_t)c->ngroups * kNumVelFields * kLanes, T(0));
+  inv.assign((size_t)c->ngroups * 9 * kLanes, T(0));
+  const double kap[3] = {1.5, 5.0 / 3.0, 2.0};
+  for (int g = 0; g < c->ngroups; ++g) {
+    const int q = g / gq, gi = g % gq;
+    const double s1 = (q & 1) ? -1.0 : 1.0, s2 = (q & 2) ? -1.0 : 1.0;
+    for (int lane = 0; lane < kLanes; ++lane) {
+      const int pos = gi * kLanes + lane;
+      const bool valid = pos < half * half;
+      const int a = valid ? pos / half : 0, b = valid ? pos % half : 0;
+      const double v1 = s1 * c->x1[half + a], v2 = s2 * c->x1[half + b];
+      const double W = valid ? c->w1[half + a] * c->w1[half + b] : 0.0;
+      const double e = v1 * v1 + v2 * v2 - 1.0;
+      const double cx = std::fabs(v1) / dx, cy = std::fabs(v2) / dx;
+      const double f[kNumVelFields] = {v1, v2, e, cx, cy, W, W * v1, W * v2, W * (v1 * v1 + v2 * v2),
+                                       std::fabs(v1) * W, std::fabs(v2) * W};
+      for (int k = 0; k < kNumVelFields; ++k) vel[((size_t)g * kNumVelFields + k) * kLanes + lane] = (T)f[k];
+      for (int clx = 0; clx < 3; ++clx)
+        for (int cly = 0; cly < 3; ++cly)
+          inv[((size_t)g * 9 + clx * 3 + cly) * kLanes + lane] = (T)(1.0 / (c->delta + cx * kap[clx] + cy * kap[cly]));
+    }
+  }
+}
+
+void velocity_sums(const dvm_ctx *c, InstanceDesc &D) {
+  for (int k = 0; k < 4; ++k) D.sumW[k] = D.ain[k] = D.nrm[k] = 0.0;
+  const int n = c->nv;
+  for (int a = 0; a < n; ++a) {
+    for (int b = 0; b < n; ++b) {
+      const double v1 = c->x1[a], v2 = c->x1[b], W = c->w1[a] * c->w1[b];
+      D.sumW[0] += W;
+      D.sumW[1] += W * v1;
+      D.sumW[2] += W * v2;
+      D.sumW[3] += W * (v1 * v1 + v2 * v2);
+      const double vn[4] = {v1, -v1, v2, -v2};  // inward normal of a wall on side W, E, S, N
+      for (int s = 0; s < 4; ++s) {
+        if (vn[s] < 0) D.ain[s] += -vn[s] * W;
+        else D.nrm[s] += vn[s] * W;
+      }
+    }
+  }
+}
+
+int auto_warps(int nx, int ny) {
+  int R = 16;
+  R = std::min(R, std::max(1, nx));
+  R = std::min(R, std::max(1, ny));
+  return R;
+}
+
+template <typename T>
+void free_dev(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+void batch_free(dvm_batch *b);
+
+void release_device(dvm_ctx *c) {
+  if (c->self) batch_free(c->self);
+  c->self = nullptr;
+  free_dev(c->d_vel);
+  free_dev(c->d_inv);
+  free_dev(c->d_rec);
+  free_dev(c->d_code4);
+  free_dev(c->d_hw_src);
+  free_dev(c->d_delta_field);
+  free_dev(c->d_acc);
+  free_dev(c->d_facc);
+  free_dev(c->d_mom);
+  free_dev(c->d_u1prev);
+  free_dev(c->d_seamx);
+  free_dev(c->d_seamy);
+  free_dev(c->d_h);
+  free_dev(c->d_state);
+  free_dev(c->d_desc);
+  free_dev(c->d_sweep_map);
+  free_dev(c->d_fin_map);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  c->h_state = nullptr;
+}
+
+dvm_status reset_state(dvm_ctx *c) {
+  const size_t ts = c->fp64 ? 8 : 4;
+  DVM_CUDA(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * 4 * c->ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->d_facc, 0, sizeof(double) * 8 * c->ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->d_mom, 0, sizeof(double) * 4 * c->ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->d_u1prev, 0, sizeof(double) * c->ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->d_seamx, 0, ts * c->ngroups * c->ny * 2 * kLanes, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->d_seamy, 0, ts * c->ngroups * c->nx * 2 * kLanes, c->stream));
+  if (c->d_h) DVM_CUDA(c, cudaMemsetAsync(c->d_h, 0, ts * c->ngroups * (size_t)c->ncell * kLanes, c->stream));
+  DVM_CUDA(c, launch_reset(c->d_desc, c->ncell, c->fp64, c->stream));
+  DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DVM_OK;
+}
+
+dvm_status upload_desc(dvm_ctx *c) {
+  InstanceDesc &D = c->hdesc;
+  D.uniform_delta = c->uniform ? 1 : 0;
+  D.delta_field = c->d_delta_field;
+  DVM_CUDA(c, cudaMemcpyAsync(c->d_desc, &D, sizeof(InstanceDesc), cudaMemcpyHostToDevice, c->stream));
+  return DVM_OK;
+}
+
+LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const int *fin_map, int ninst, int warps,
+                       int cmax, bool fp64) {
+  LaunchDesc L;
+  L.inst = insts;
+  L.sweep_map = sweep_map;
+  L.fin_map = fin_map;
+  L.ninst = ninst;
+  L.warps = warps;
+  L.cmax = cmax;
+  L.stage_seams = fp64 ? 0 : 1;
+  return L;
+}
+
+// Capture `iters` sweeps (sweep + two finalize kernels) of a launch into a graph; with events,
+// record ev[0] before the sweep, ev[1] after it and ev[2] after the finalize kernels (iters = 1).
+dvm_status capture_graph(dvm_ctx *err_ctx, cudaStream_t cap, const LaunchDesc &L, int sweep_blocks, int fin_blocks,
+                         bool fp64, bool store_h, bool uniform, int iters, cudaEvent_t *ev, cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  DVM_CUDA(err_ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    if (ev) e = cudaEventRecord(ev[0], cap);
+    if (e == cudaSuccess) e = launch_sweep(fp64, store_h, uniform, L, sweep_blocks, cap);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], cap);
+    if (e == cudaSuccess) e = launch_finalize(L, fin_blocks, fp64, cap);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], cap);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(err_ctx, DVM_ECUDA,
+                std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(err_ctx, DVM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return DVM_OK;
+}
+
+int iters_per_graph(double updates_per_iter) {
+  if (updates_per_iter >= 5e7) return 4;
+  if (updates_per_iter >= 5e6) return 8;
+  if (updates_per_iter >= 5e5) return 16;
+  return 32;
+}
+
+void batch_free(dvm_batch *b) {
+  if (!b) return;
+  if (b->g_many) cudaGraphExecDestroy(b->g_many);
+  if (b->g_one) cudaGraphExecDestroy(b->g_one);
+  for (auto &e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->d_descs) cudaFree(b->d_descs);
+  if (b->d_smap) cudaFree(b->d_smap);
+  if (b->d_fmap) cudaFree(b->d_fmap);
+  delete b;
+}
+
+// Build a batch over ctxs (errors reported on ctxs[0]).
+dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
+  if (!ctxs || n < 1 || !ctxs[0]) return DVM_EINVAL;
+  dvm_ctx *c0 = ctxs[0];
+  if (n > 32767) return fail(c0, DVM_EINVAL, "too many instances in one batch");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(c0, DVM_EINVAL, "null context in batch");
+    if (ctxs[i]->fp64 != c0->fp64 || ctxs[i]->store_h != c0->store_h)
+      return fail(c0, DVM_EINVAL, "batched contexts must share precision and store_distribution");
+    if (ctxs[i]->device != c0->device) return fail(c0, DVM_EINVAL, "batched contexts must share a device");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return fail(c0, DVM_EINVAL, "a context appears twice in the batch");
+  }
+  dvm_batch *b = new (std::nothrow) dvm_batch();
+  if (!b) return fail(c0, DVM_ENOMEM, "host allocation failed");
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->fp64 = c0->fp64;
+  b->store_h = c0->store_h;
+  b->stream = c0->stream;
+  b->warps = kMaxWarps;
+  for (int i = 0; i < n; ++i) {
+    b->warps = std::min(b->warps, ctxs[i]->warps);
+    b->uniform = b->uniform && ctxs[i]->uniform;
+  }
+  b->cmax = 1;
+  std::vector<InstanceDesc> descs(n);
+  std::vector<int> smap, fmap;
+  std::vector<double> work(n);
+  double upd = 0.0;
+  for (int i = 0; i < n; ++i) {
+    b->cmax = std::max(b->cmax, (ctxs[i]->nx + b->warps - 1) / b->warps);
+    descs[i] = ctxs[i]->hdesc;
+    descs[i].uniform_delta = ctxs[i]->uniform ? 1 : 0;
+    descs[i].delta_field = ctxs[i]->d_delta_field;
+    for (int g = 0; g < ctxs[i]->ngroups; ++g) smap.push_back((i << 16) | g);
+    for (int blk = 0; blk < ctxs[i]->hdesc.fin_nblocks; ++blk) fmap.push_back((i << 16) | blk);
+    work[i] = (double)ctxs[i]->ncell;
+    upd += (double)ctxs[i]->geo.n_gas * ctxs[i]->nv * ctxs[i]->nv;
+  }
+  // longest sweeps first
+  std::stable_sort(smap.begin(), smap.end(), [&](int a, int c) { return work[a >> 16] > work[c >> 16]; });
+  b->nsweep = (int)smap.size();
+  b->nfin = (int)fmap.size();
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c0->device);
+  if (sweep_smem_bytes(b->fp64, b->warps, b->cmax) > (size_t)smem_optin) {
+    batch_free(b);
+    return fail(c0, DVM_EINVAL, "batched grids too wide for the sweep's shared memory");
+  }
+#define BATCH_CUDA(call)                                                                         \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      batch_free(b);                                                                             \
+      return fail(c0, DVM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    }                                                                                            \
+  } while (0)
+  BATCH_CUDA(cudaMalloc(&b->d_descs, sizeof(InstanceDesc) * n));
+  BATCH_CUDA(cudaMalloc(&b->d_smap, sizeof(int) * smap.size()));
+  BATCH_CUDA(cudaMalloc(&b->d_fmap, sizeof(int) * fmap.size()));
+  BATCH_CUDA(cudaMemcpyAsync(b->d_descs, descs.data(), sizeof(InstanceDesc) * n, cudaMemcpyHostToDevice, b->stream));
+  BATCH_CUDA(cudaMemcpyAsync(b->d_smap, smap.data(), sizeof(int) * smap.size(), cudaMemcpyHostToDevice, b->stream));
+  BATCH_CUDA(cudaMemcpyAsync(b->d_fmap, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice, b->stream));
+  BATCH_CUDA(cudaStreamSynchronize(b->stream));
+  for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
+#undef BATCH_CUDA
+  LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cmax, b->fp64);
+  b->m = iters_per_graph(upd);
+  dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, b->m,
+                                nullptr, &b->g_many);
+  if (st == DVM_OK)
+    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, 1, b->ev,
+                       &b->g_one);
+  if (st != DVM_OK) {
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return DVM_OK;
+}
+
+dvm_status batch_poll(dvm_batch *b, bool *all_done) {
+  dvm_ctx *c0 = b->ctxs[0];
+  for (dvm_ctx *c : b->ctxs)
+    DVM_CUDA(c0, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, b->stream));
+  DVM_CUDA(c0, cudaStreamSynchronize(b->stream));
+  bool all = true;
+  for (dvm_ctx *c : b->ctxs) all = all && c->h_state->done;
+  *all_done = all;
+  return DVM_OK;
+}
+
+// Arm every member for `count` more sweeps with the given tolerance; returns the start iterations.
+dvm_status batch_arm(dvm_batch *b, double tol, int count, std::vector<int> &start) {
+  dvm_ctx *c0 = b->ctxs[0];
+  for (dvm_ctx *c : b->ctxs)
+    if (c->stream != b->stream) DVM_CUDA(c0, cudaStreamSynchronize(c->stream));
+  for (dvm_ctx *c : b->ctxs)
+    DVM_CUDA(c0, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, b->stream));
+  DVM_CUDA(c0, cudaStreamSynchronize(b->stream));
+  start.resize(b->ctxs.size());
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    start[i] = b->ctxs[i]->h_state->iter;
+    const long long limit = (long long)start[i] + count;
+    if (limit > 2000000000LL) return fail(c0, DVM_EINVAL, "iteration limit too large");
+    DVM_CUDA(c0, launch_arm(b->ctxs[i]->d_state, tol, (int)limit, b->stream));
+  }
+  return DVM_OK;
+}
+
+dvm_status batch_run(dvm_batch *b, double tol, int max_iter, dvm_status *per, int *iters, double *est) {
+  dvm_ctx *c0 = b->ctxs[0];
+  if (max_iter < 1) return fail(c0, DVM_EINVAL, "max_iter must be >= 1");
+  std::vector<int> start;
+  dvm_status st = batch_arm(b, tol, max_iter, start);
+  if (st != DVM_OK) return st;
+  // every member is armed to stop after max_iter sweeps, so the loop ends after at most
+  // ceil(max_iter / m) replays; the bound below only guards against a flag that is never set
+  const long long max_replays = (long long)max_iter / b->m + 3;
+  for (long long replay = 0;; ++replay) {
+    if (replay >= max_replays) return fail(c0, DVM_ETIMEOUT, "device stop flag not set after max_iter sweeps");
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_many, b->stream));
+    bool all = false;
+    st = batch_poll(b, &all);
+    if (st != DVM_OK) return st;
+    if (all) break;
+  }
+  dvm_status result = DVM_OK;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    const dvm_status si = (dvm_status)b->ctxs[i]->h_state->status;
+    if (per) per[i] = si;
+    if (si != DVM_OK && result == DVM_OK) result = si;
+  }
+  if (iters) *iters = c0->h_state->iter - start[0];
+  if (est) *est = c0->h_state->est;
+  b->timed = false;
+  return result;
+}
+
+dvm_status batch_iterate(dvm_batch *b, int n) {
+  dvm_ctx *c0 = b->ctxs[0];
+  if (n < 1) return fail(c0, DVM_EINVAL, "n must be >= 1");
+  std::vector<int> start;
+  dvm_status st = batch_arm(b, -1.0, n, start);
+  if (st != DVM_OK) return st;
+  int left = n;
+  while (left >= b->m && b->m > 1) {
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_many, b->stream));
+    left -= b->m;
+  }
+  for (; left > 0; --left) DVM_CUDA(c0, cudaGraphLaunch(b->g_one, b->stream));
+  bool all = false;
+  st = batch_poll(b, &all);
+  if (st != DVM_OK) return st;
+  for (dvm_ctx *c : b->ctxs) {
+    const int s = c->h_state->status;
+    if (s != DVM_OK && s != DVM_ENOCONV) return fail(c0, (dvm_status)s, "a batch member failed during iteration");
+  }
+  b->timed = (n == 1) || (n % b->m != 0) || b->m == 1;
+  return DVM_OK;
+}
+
+dvm_status ensure_self(dvm_ctx *c) {
+  if (c->self) return DVM_OK;
+  dvm_ctx *one[1] = {c};
+  return batch_build(one, 1, &c->self);
+}
+
+}  // namespace
+
+extern "C" {
+
+dvm_status dvm_params_init(dvm_params *p) {
+  if (!p) return DVM_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = 0;
+  p->ny = 0;
+  p->periodic_x = 1;
+  p->periodic_y = 0;
+  p->ly = 1.0;
+  p->kn = 0.1;
+  p->delta = -1.0;
+  p->quad.kind = DVM_QUAD_GAUSS_HERMITE;
+  p->quad.n = 12;
+  p->quad.vmax = 5.0;
+  p->accommodation = 1.0;
+  p->precision = DVM_FP64;
+  p->force = 1.0;
+  p->store_distribution = 0;
+  p->sweep_warps = 0;
+  return DVM_OK;
+}
+
+const char *dvm_status_string(dvm_status s) {
+  switch (s) {
+    case DVM_OK: return "DVM_OK";
+    case DVM_EINVAL: return "DVM_EINVAL";
+    case DVM_ENOMEM: return "DVM_ENOMEM";
+    case DVM_ECUDA: return "DVM_ECUDA";
+    case DVM_ENOCONV: return "DVM_ENOCONV";
+    case DVM_ETIMEOUT: return "DVM_ETIMEOUT";
+    case DVM_ENUMERIC: return "DVM_ENUMERIC";
+    case DVM_ESTATE: return "DVM_ESTATE";
+  }
+  return "DVM_UNKNOWN";
+}
+
+const char *dvm_last_error(const dvm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *stream, dvm_ctx **out) {
+  if (!mask || !params || !out) return fail(nullptr, DVM_EINVAL, "null argument");
+  const dvm_params &P = *params;
+  if (P.nx < 2 || P.ny < 2 || P.nx > 65536 || P.ny > 65536)
+    return fail(nullptr, DVM_EINVAL, "nx and ny must be in [2, 65536]");
+  if (!(P.ly > 0.0) || !std::isfinite(P.ly)) return fail(nullptr, DVM_EINVAL, "ly must be positive");
+  if (P.accommodation != 1.0)
+    return fail(nullptr, DVM_EINVAL, "only fully diffuse walls (accommodation = 1) are supported");
+  if (P.precision != DVM_FP64 && P.precision != DVM_FP32_ACC64) return fail(nullptr, DVM_EINVAL, "bad precision");
+  if (!std::isfinite(P.force)) return fail(nullptr, DVM_EINVAL, "force must be finite");
+  double delta;
+  if (P.kn > 0.0) {
+    if (P.delta >= 0.0) return fail(nullptr, DVM_EINVAL, "set exactly one of kn and delta");
+    delta = std::isinf(P.kn) ? 0.0 : std::sqrt(M_PI) / (2.0 * P.kn);
+  } else if (P.delta >= 0.0 && std::isfinite(P.delta)) {
+    delta = P.delta;
+  } else {
+    return fail(nullptr, DVM_EINVAL, "set exactly one of kn (> 0) and delta (>= 0)");
+  }
+  if (P.sweep_warps < 0 || P.sweep_warps > kMaxWarps) return fail(nullptr, DVM_EINVAL, "sweep_warps must be 0..32");
+
+  dvm_ctx *c = new (std::nothrow) dvm_ctx();
+  if (!c) return fail(nullptr, DVM_ENOMEM, "host allocation failed");
+  c->P = P;
+  c->nx = P.nx;
+  c->ny = P.ny;
+  c->ncell = P.nx * P.ny;
+  c->fp64 = P.precision == DVM_FP64;
+  c->store_h = P.store_distribution != 0;
+  c->delta = delta;
+  c->kn = P.kn > 0.0 ? P.kn : (delta > 0 ? std::sqrt(M_PI) / (2.0 * delta) : INFINITY);
+  std::string qerr;
+  if (!quadrature_1d(P.quad.kind, P.quad.n, P.quad.vmax, c->x1, c->w1, qerr)) {
+    delete c;
+    return fail(nullptr, DVM_EINVAL, qerr);
+  }
+  c->nv = P.quad.n;
+  c->half = c->nv / 2;
+  c->gq = (c->half * c->half + kLanes - 1) / kLanes;
+  c->ngroups = 4 * c->gq;
+  build_geometry(mask, c->nx, c->ny, P.periodic_x != 0, P.periodic_y != 0, c->geo);
+  if (c->geo.n_gas == 0) {
+    delete c;
+    return fail(nullptr, DVM_EINVAL, "the mask has no gas cell");
+  }
+  c->warps = P.sweep_warps > 0 ? P.sweep_warps : auto_warps(c->nx, c->ny);
+  c->cmax = (c->nx + c->warps - 1) / c->warps;
+  const size_t smem = sweep_smem_bytes(c->fp64, c->warps, c->cmax);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, DVM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  c->device = dev;
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)smem_optin) {
+    delete c;
+    return fail(nullptr, DVM_EINVAL,
+                "grid too wide for the sweep's shared-memory ring (" + std::to_string(smem) + " > " +
+                    std::to_string(smem_optin) + " bytes); use fewer columns nx or FP32 storage");
+  }
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(nullptr, DVM_ECUDA, "cudaStreamCreate failed");
+    }
+    c->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return fail(nullptr, DVM_ECUDA, "cudaStreamCreate failed");
+  }
+
+  auto cleanup_fail = [&](dvm_status st, const std::string &msg) {
+    g_create_error = msg;
+    release_device(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return st;
+  };
+#define CREATE_CUDA(call)                                                                                   \
+  do {                                                                                                      \
+    cudaError_t e_ = (call);                                                                                \
+    if (e_ != cudaSuccess) {                                                                                \
+      return cleanup_fail(e_ == cudaErrorMemoryAllocation ? DVM_ENOMEM : DVM_ECUDA,                         \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                                       \
+  } while (0)
+
+  const size_t ts = c->fp64 ? 8 : 4;
+  const size_t recsz = c->fp64 ? sizeof(SweepRec<double>) : sizeof(SweepRec<float>);
+  const size_t ncell = (size_t)c->ncell;
+  CREATE_CUDA(cudaMalloc(&c->d_vel, ts * c->ngroups * kNumVelFields * kLanes));
+  CREATE_CUDA(cudaMalloc(&c->d_inv, ts * c->ngroups * 9 * kLanes));
+  CREATE_CUDA(cudaMalloc(&c->d_rec, recsz * 4 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_code4, sizeof(uint32_t) * 4 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_hw_src, sizeof(int) * 8 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_delta_field, sizeof(double) * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_acc, sizeof(double) * 4 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_facc, sizeof(double) * 8 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_mom, sizeof(double) * 4 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_u1prev, sizeof(double) * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_seamx, ts * c->ngroups * c->ny * 2 * kLanes));
+  CREATE_CUDA(cudaMalloc(&c->d_seamy, ts * c->ngroups * c->nx * 2 * kLanes));
+  if (c->store_h) CREATE_CUDA(cudaMalloc(&c->d_h, ts * c->ngroups * ncell * kLanes));
+  CREATE_CUDA(cudaMalloc(&c->d_state, sizeof(DeviceState)));
+  CREATE_CUDA(cudaMalloc(&c->d_desc, sizeof(InstanceDesc)));
+  CREATE_CUDA(cudaMallocHost(&c->h_state, sizeof(DeviceState)));
+
+  // velocity tables
+  if (c->fp64) {
+    std::vector<double> vel, inv;
+    build_velocity_tables<double>(c, vel, inv);
+    CREATE_CUDA(cudaMemcpy(c->d_vel, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(c->d_inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> vel, inv;
+    build_velocity_tables<float>(c, vel, inv);
+    CREATE_CUDA(cudaMemcpy(c->d_vel, vel.data(), vel.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(c->d_inv, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  CREATE_CUDA(cudaMemcpy(c->d_code4, c->geo.code4.data(), sizeof(uint32_t) * 4 * ncell, cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMemcpy(c->d_hw_src, c->geo.hw_src.data(), sizeof(int) * 8 * ncell, cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMemset(c->d_delta_field, 0, sizeof(double) * ncell));
+
+  // launch maps of a single-instance launch
+  std::vector<int> smap(c->ngroups), fmap;
+  for (int g = 0; g < c->ngroups; ++g) smap[g] = g;
+  const int fin_nblocks = (c->ncell + kFinBlock - 1) / kFinBlock;
+  if (fin_nblocks > 65535) return cleanup_fail(DVM_EINVAL, "grid has too many cells");
+  fmap.resize(fin_nblocks);
+  for (int b = 0; b < fin_nblocks; ++b) fmap[b] = b;
+  CREATE_CUDA(cudaMalloc(&c->d_sweep_map, sizeof(int) * smap.size()));
+  CREATE_CUDA(cudaMalloc(&c->d_fin_map, sizeof(int) * fmap.size()));
+  CREATE_CUDA(cudaMemcpy(c->d_sweep_map, smap.data(), sizeof(int) * smap.size(), cudaMemcpyHostToDevice));
+  CREATE_CUDA(cudaMemcpy(c->d_fin_map, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice));
+
+  InstanceDesc &D = c->hdesc;
+  std::memset(&D, 0, sizeof(D));
+  D.nx = c->nx;
+  D.ny = c->ny;
+  D.ncell = c->ncell;
+  D.periodic_x = P.periodic_x != 0;
+  D.periodic_y = P.periodic_y != 0;
+  D.ngroups = c->ngroups;
+  D.groups_per_quadrant = c->gq;
+  D.n_gas = c->geo.n_gas;
+  D.fin_nblocks = fin_nblocks;
+  D.dx = P.ly / c->ny;
+  D.dA_over_Lx = D.dx * D.dx / (c->nx * D.dx);
+  D.delta = delta;
+  D.force = P.force;
+  velocity_sums(c, D);
+  D.vel = c->d_vel;
+  D.inv_den = c->d_inv;
+  D.rec = c->d_rec;
+  D.code4 = c->d_code4;
+  D.hw_src = c->d_hw_src;
+  D.acc = c->d_acc;
+  D.facc = c->d_facc;
+  D.mom = c->d_mom;
+  D.u1prev = c->d_u1prev;
+  D.seam_x = c->d_seamx;
+  D.seam_y = c->d_seamy;
+  D.h = c->d_h;
+  D.state = c->d_state;
+  c->uniform = true;
+  if (upload_desc(c) != DVM_OK) return cleanup_fail(DVM_ECUDA, c->err);
+  if (reset_state(c) != DVM_OK) return cleanup_fail(DVM_ECUDA, c->err);
+#undef CREATE_CUDA
+  *out = c;
+  return DVM_OK;
+}
+
+dvm_status dvm_reset(dvm_ctx *ctx) {
+  if (!ctx) return DVM_EINVAL;
+  return reset_state(ctx);
+}
+
+dvm_status dvm_set_delta_field(dvm_ctx *ctx, const double *delta_c) {
+  if (!ctx) return DVM_EINVAL;
+  if (delta_c) {
+    std::vector<double> d((size_t)ctx->ncell, 0.0);
+    for (int cell = 0; cell < ctx->ncell; ++cell) {
+      if (ctx->geo.code4[(size_t)cell * 4] & kSolid) continue;
+      if (!(delta_c[cell] >= 0.0) || !std::isfinite(delta_c[cell]))
+        return fail(ctx, DVM_EINVAL, "delta field entries must be finite and >= 0 in gas cells");
+      d[cell] = delta_c[cell];
+    }
+    DVM_CUDA(ctx, cudaMemcpyAsync(ctx->d_delta_field, d.data(), sizeof(double) * ctx->ncell, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    DVM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->uniform = false;
+  } else {
+    ctx->uniform = true;
+  }
+  if (ctx->self) {
+    batch_free(ctx->self);
+    ctx->self = nullptr;
+  }
+  dvm_status st = upload_desc(ctx);
+  if (st != DVM_OK) return st;
+  return reset_state(ctx);
+}
+
+dvm_status dvm_solve(dvm_ctx *ctx, double tol, int max_iter, int *iters, double *est) {
+  if (!ctx) return DVM_EINVAL;
+  if (!(tol > 0.0)) return fail(ctx, DVM_EINVAL, "tol must be > 0");
+  dvm_status st = ensure_self(ctx);
+  if (st != DVM_OK) return st;
+  return batch_run(ctx->self, tol, max_iter, nullptr, iters, est);
+}
+
+dvm_status dvm_iterate(dvm_ctx *ctx, int n) {
+  if (!ctx) return DVM_EINVAL;
+  dvm_status st = ensure_self(ctx);
+  if (st != DVM_OK) return st;
+  return batch_iterate(ctx->self, n);
+}
+
+dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info) {
+  if (!ctx || !info) return DVM_EINVAL;
+  dvm_ctx *c = const_cast<dvm_ctx *>(ctx);
+  DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
+  DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+  info->iterations = c->h_state->iter;
+  info->eps = c->h_state->eps;
+  info->est = c->h_state->est;
+  info->mass_shift = c->h_state->c;
+  info->Q = c->h_state->Q;
+  info->status = c->h_state->status;
+  return DVM_OK;
+}
+
+dvm_status dvm_flowrate(const dvm_ctx *ctx, double *Q, double *k_a) {
+  if (!ctx || !Q) return DVM_EINVAL;
+  dvm_info info;
+  dvm_status st = dvm_get_info(ctx, &info);
+  if (st != DVM_OK) return st;
+  if (info.iterations < 1) return fail(const_cast<dvm_ctx *>(ctx), DVM_ESTATE, "no sweep has run yet");
+  *Q = info.Q;
+  if (k_a) *k_a = (ctx->uniform && ctx->delta > 0.0) ? std::sqrt(4.0 / M_PI) * info.Q * ctx->kn : NAN;
+  return DVM_OK;
+}
+
+dvm_status dvm_fields(const dvm_ctx *ctx, double *rho, double *u1, double *u2, double *tau) {
+  if (!ctx) return DVM_EINVAL;
+  dvm_ctx *c = const_cast<dvm_ctx *>(ctx);
+  std::vector<double> mom((size_t)4 * c->ncell);
+  DVM_CUDA(c, cudaMemcpyAsync(mom.data(), c->d_mom, sizeof(double) * 4 * c->ncell, cudaMemcpyDeviceToHost, c->stream));
+  DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+  double *outs[4] = {rho, u1, u2, tau};
+  for (int cell = 0; cell < c->ncell; ++cell) {
+    const bool solid = (c->geo.code4[(size_t)cell * 4] & kSolid) != 0;
+    for (int m = 0; m < 4; ++m)
+      if (outs[m]) outs[m][cell] = solid ? NAN : mom[(size_t)cell * 4 + m];
+  }
+  return DVM_OK;
+}
+
+dvm_status dvm_distribution(const dvm_ctx *ctx, const int *ks, int nk, double *out) {
+  if (!ctx || (nk > 0 && (!ks || !out)) || nk < 0) return DVM_EINVAL;
+  dvm_ctx *c = const_cast<dvm_ctx *>(ctx);
+  if (!c->d_h) return fail(c, DVM_ESTATE, "the distribution is not kept (store_distribution = 0)");
+  const size_t ts = c->fp64 ? 8 : 4;
+  std::vector<unsigned char> buf(ts * c->ncell);
+  // the stored sweep output is the state before its last mass shift s
+  DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
+  DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double shift = c->h_state->iter > 0 ? c->h_state->s : 0.0;
+  for (int m = 0; m < nk; ++m) {
+    const int k = ks[m];
+    if (k < 0 || k >= c->nv * c->nv) return fail(c, DVM_EINVAL, "velocity index out of range");
+    const int a = k / c->nv, b = k % c->nv;
+    const int s1neg = a < c->half, s2neg = b < c->half;
+    const int ap = s1neg ? c->half - 1 - a : a - c->half;
+    const int bp = s2neg ? c->half - 1 - b : b - c->half;
+    const int q = s1neg + 2 * s2neg;
+    const int pos = ap * c->half + bp;
+    const int g = q * c->gq + pos / kLanes, lane = pos % kLanes;
+    const char *src = static_cast<const char *>(c->d_h) + ((size_t)g * c->ncell * kLanes + lane) * ts;
+    DVM_CUDA(c, cudaMemcpy2DAsync(buf.data(), ts, src, ts * kLanes, ts, c->ncell, cudaMemcpyDeviceToHost, c->stream));
+    DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int cell = 0; cell < c->ncell; ++cell) {
+      double v;
+      if (c->fp64) std::memcpy(&v, &buf[(size_t)cell * 8], 8);
+      else {
+        float f;
+        std::memcpy(&f, &buf[(size_t)cell * 4], 4);
+        v = f;
+      }
+      v = (c->geo.code4[(size_t)cell * 4] & kSolid) ? 0.0 : v - shift;
+      out[(size_t)m * c->ncell + cell] = v;
+    }
+  }
+  return DVM_OK;
+}
+
+dvm_status dvm_quadrature(const dvm_ctx *ctx, double *nodes, double *weights) {
+  if (!ctx) return DVM_EINVAL;
+  for (int a = 0; a < ctx->nv; ++a) {
+    if (nodes) nodes[a] = ctx->x1[a];
+    if (weights) weights[a] = ctx->w1[a];
+  }
+  return DVM_OK;
+}
+
+dvm_status dvm_velocity_grid(const dvm_quad *q, double *nodes, double *weights) {
+  if (!q || !nodes || !weights) return DVM_EINVAL;
+  std::vector<double> x, w;
+  std::string err;
+  if (!quadrature_1d(q->kind, q->n, q->vmax, x, w, err)) return fail(nullptr, DVM_EINVAL, err);
+  for (int a = 0; a < q->n; ++a) {
+    nodes[a] = x[a];
+    weights[a] = w[a];
+  }
+  return DVM_OK;
+}
+
+dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
+  if (!out) return DVM_EINVAL;
+  return batch_build(ctxs, n, out);
+}
+
+dvm_status dvm_batch_run(dvm_batch *batch, double tol, int max_iter, dvm_status *per) {
+  if (!batch) return DVM_EINVAL;
+  if (!(tol > 0.0)) return fail(batch->ctxs[0], DVM_EINVAL, "tol must be > 0");
+  return batch_run(batch, tol, max_iter, per, nullptr, nullptr);
+}
+
+dvm_status dvm_batch_iterate(dvm_batch *batch, int n) {
+  if (!batch) return DVM_EINVAL;
+  return batch_iterate(batch, n);
+}
+
+dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms) {
+  if (!batch) return DVM_EINVAL;
+  if (!batch->timed) return fail(batch->ctxs[0], DVM_ESTATE, "no timed single sweep has run on this batch");
+  float a = 0.f, b = 0.f;
+  DVM_CUDA(batch->ctxs[0], cudaEventElapsedTime(&a, batch->ev[0], batch->ev[1]));
+  DVM_CUDA(batch->ctxs[0], cudaEventElapsedTime(&b, batch->ev[1], batch->ev[2]));
+  if (sweep_ms) *sweep_ms = a;
+  if (finalize_ms) *finalize_ms = b;
+  return DVM_OK;
+}
+
+int dvm_batch_kernels_per_sweep(const dvm_batch *batch) { return batch ? 3 : 0; }
+
+void dvm_batch_destroy(dvm_batch *batch) {
+  if (!batch) return;
+  cudaStreamSynchronize(batch->stream);
+  batch_free(batch);
+}
+
+dvm_status dvm_batch_solve(dvm_ctx *const *ctxs, int n, double tol, int max_iter, dvm_status *per) {
+  if (!ctxs || n < 1 || !(tol > 0.0) || max_iter < 1) return DVM_EINVAL;
+  dvm_batch *b = nullptr;
+  dvm_status st = batch_build(ctxs, n, &b);
+  if (st != DVM_OK) return st;
+  st = batch_run(b, tol, max_iter, per, nullptr, nullptr);
+  batch_free(b);
+  return st;
+}
+
+void dvm_destroy(dvm_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release_device(ctx);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
+}  // extern "C"

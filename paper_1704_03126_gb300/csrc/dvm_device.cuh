@@ -1,0 +1,117 @@
+// dvm_device.cuh -- device-side data layout of libdvm (internal; not part of the C ABI).
+//
+// One "instance" is one geometry + Knudsen number + velocity grid.  The distribution h of an
+// instance is split into velocity groups of 32 velocities of one quadrant (sign(v1), sign(v2));
+// one thread block sweeps one group over the whole grid (lanes = velocities, warps = rows in
+// flight).  Several instances can share a launch (batched solves).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dvm {
+
+constexpr int kLanes = 32;       // velocities per group = warp width
+constexpr int kRingPad = 33;     // padded row stride (elements) of the shared-memory ring buffer
+constexpr int kMaxWarps = 32;
+
+// Per-cell code bits for one quadrant (static geometry, see dvm_tables.cpp).
+enum : uint32_t {
+  kSolid = 1u,
+  kClsXShift = 1,  // 2 bits: 0 interior stencil, 1 two-point wall stencil, 2 one-point wall stencil
+  kClsYShift = 3,
+  kIncX = 1u << 5, // the cell owns a wall face on its downstream x side (incident for this quadrant)
+  kIncY = 1u << 6,
+};
+enum : int { kFull = 0, kWall3 = 1, kWall1 = 2 };
+// sides of a cell: the solid neighbour lies at -x (W), +x (E), -y (S), +y (N)
+enum : int { kW = 0, kE = 1, kS = 2, kN = 3 };
+
+// Sweep record: everything the sweep needs per cell and quadrant, rewritten every iteration by the
+// finalize kernel.  R_k = A + B v1 + C v2 + D (|v|^2 - 1) is the right-hand side of Eq. (iteration)
+// (delta (rho - c) + (2 delta u1 + F) v1 + 2 delta u2 v2 + delta tau (|v|^2 - 1)); hwx / hwy are the
+// wall values used by the x / y upstream stencil; delta the cell's collision rate.
+template <typename T> struct SweepRec;
+template <> struct alignas(16) SweepRec<float> {
+  float A, B, C, D;
+  float hwx, hwy;
+  uint32_t code;
+  float delta;
+};
+template <> struct alignas(16) SweepRec<double> {
+  double A, B, C, D;
+  double hwx, hwy;
+  uint32_t code;
+  uint32_t pad;
+  double delta;
+};
+static_assert(sizeof(SweepRec<float>) == 32, "record layout");
+static_assert(sizeof(SweepRec<double>) == 64, "record layout");
+
+// Per-lane velocity table fields ([group][field][lane], in the sweep precision).
+enum : int {
+  kV1 = 0, kV2, kE2m1, kCx, kCy,   // v1, v2, |v|^2 - 1, |v1|/dx, |v2|/dx
+  kW0, kW1, kW2, kW3,              // W, W v1, W v2, W |v|^2 (moment weights; W = 0 on padded lanes)
+  kWnx, kWny,                      // |v1| W, |v2| W (incident wall flux weights)
+  kNumVelFields
+};
+
+// Solver state of one instance (device memory; read back by the host between graph replays).
+struct DeviceState {
+  int iter;        // sweeps completed
+  int done;        // 1 = stop: every kernel of the instance returns immediately
+  int status;      // dvm_status of the solve so far
+  int max_iter;    // stop with DVM_ENOCONV when iter reaches it
+  int nan_flag;
+  int pad0;
+  unsigned int ticket1, ticket2;  // last-block counters of the two finalize kernels
+  double tol;
+  double c;        // accumulated mass shift (bordering unknown)
+  double s;        // shift still to subtract from the stored seam values
+  double s_new;    // shift of the current iteration
+  double eps, est, Q;
+  double eps_ring[4];
+  double mass_acc, du_acc, u_acc, q_acc;
+};
+
+struct InstanceDesc {
+  int nx, ny, ncell;
+  int periodic_x, periodic_y;
+  int ngroups, groups_per_quadrant;
+  int n_gas;
+  int uniform_delta;
+  int fin_nblocks;      // blocks of this instance in the finalize grids
+  double dx;            // cell size
+  double dA_over_Lx;    // dx^2 / (nx dx)
+  double delta;         // uniform collision rate
+  double force;         // F
+  double sumW[4];       // sum W, sum W v1, sum W v2, sum W |v|^2
+  double ain[4];        // per side: sum_{v.n<0} |v.n| W  (incident weight of a constant)
+  double nrm[4];        // per side: sum_{v.n>0} (v.n) W  (outgoing normaliser)
+  const void *vel;      // [ngroups][kNumVelFields][32] T
+  const void *inv_den;  // [ngroups][9][32] T: 1 / (delta + cx kx + cy ky), uniform delta only
+  void *rec;            // [4][ncell] SweepRec<T>
+  const uint32_t *code4;   // [ncell][4]
+  const int *hw_src;       // [ncell][8]: (quadrant, axis) -> owner cell * 4 + side, or -1
+  const double *delta_field;  // [ncell] or nullptr
+  double *acc;          // [ncell][4]   moment accumulators of the running sweep
+  double *facc;         // [2][ncell][4] incident wall-flux accumulators (by iteration parity)
+  double *mom;          // [ncell][4]   rho, u1, u2, tau of the current state
+  double *u1prev;       // [ncell]
+  void *seam_x;         // [ngroups][ny][2][32] T: last two columns of the previous sweep
+  void *seam_y;         // [ngroups][nx][2][32] T: last two rows of the previous sweep
+  void *h;              // [ngroups][ncell][32] T, or nullptr
+  DeviceState *state;
+};
+
+// Launch descriptor shared by the kernels of one (possibly batched) iteration.
+struct LaunchDesc {
+  const InstanceDesc *inst;  // device array [ninst]
+  const int *sweep_map;      // [sweep blocks]: instance << 16 | group
+  const int *fin_map;        // [finalize blocks]: instance << 16 | block within instance
+  int ninst;
+  int warps;                 // sweep warps per block (R)
+  int cmax;                  // max over instances of ceil(nx / R)
+  int stage_seams;           // shared-memory staging of periodic-y seam rows (FP32 path)
+};
+
+}  // namespace dvm

@@ -1,0 +1,256 @@
+// dvm_finalize.cu -- per-iteration reductions after the sweep (FP64 throughout).
+//
+// fin1: the mean gas density of the swept state gives the mass shift s = sum_gas rho / (n_gas sum W)
+//       that projects the null mode h = const out of the iteration (the constant solves the
+//       homogeneous problem: the sweep reproduces constants exactly and the walls conserve mass).
+// fin2: shifted moments rho, u1, u2, tau (Sec. II.A), the accumulated bordering unknown c += s, the
+//       stopping quantities eps_n = sum|u1^n - u1^{n-1}| / sum|u1^n| and the flow rate
+//       Q = sum u1 dA / Lx (Sec. III), the diffuse wall values rho_w = incident flux / outgoing
+//       normaliser (Eq. diffuse2), and the sweep records of the next iteration.  The last block of
+//       each instance applies the stopping test and sets the instance's done flag.
+#include <cmath>
+#include <cstdint>
+
+#include "dvm_device.cuh"
+#include "dvm_kernels.h"
+
+namespace dvm {
+namespace {
+
+constexpr int kFinBlock = 256;
+
+struct alignas(32) Dbl4 {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kFinBlock) fin1_kernel(LaunchDesc L) {
+  __shared__ double sh[32];
+  const int map = L.fin_map[blockIdx.x];
+  const InstanceDesc *D = L.inst + (map >> 16);
+  DeviceState *st = D->state;
+  if (*reinterpret_cast<volatile int *>(&st->done)) return;
+  const int cell = (map & 0xffff) * kFinBlock + threadIdx.x;
+  double v = 0.0;
+  if (cell < D->ncell && !(D->code4[(size_t)cell * 4] & kSolid)) v = D->acc[(size_t)cell * 4];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(&st->mass_acc, v);
+    __threadfence();
+    const unsigned t = atomicAdd(&st->ticket1, 1u);
+    if (t == (unsigned)D->fin_nblocks - 1u) {
+      __threadfence();
+      const double mass = atomicAdd(&st->mass_acc, 0.0);
+      st->s_new = mass / ((double)D->n_gas * D->sumW[0]);
+      st->mass_acc = 0.0;
+      st->ticket1 = 0u;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_rec(SweepRec<T> *dst, double A, double B, double C, double Dd, double hwx,
+                                          double hwy, uint32_t code, double delta) {
+  SweepRec<T> r;
+  r.A = (T)A;
+  r.B = (T)B;
+  r.C = (T)C;
+  r.D = (T)Dd;
+  r.hwx = (T)hwx;
+  r.hwy = (T)hwy;
+  r.code = code;
+  r.delta = (T)delta;
+  *dst = r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
+  __shared__ double sh[32];
+  const int map = L.fin_map[blockIdx.x];
+  const InstanceDesc *D = L.inst + (map >> 16);
+  DeviceState *st = D->state;
+  if (*reinterpret_cast<volatile int *>(&st->done)) return;
+  const int ncell = D->ncell;
+  const int cell = (map & 0xffff) * kFinBlock + threadIdx.x;
+  const double s = st->s_new;
+  const double c_new = st->c + s;
+  const int parity = (st->iter + 1) & 1;
+  const double *fcur = D->facc + (size_t)parity * ncell * 4;
+  double *fnext = D->facc + (size_t)(parity ^ 1) * ncell * 4;
+  double du = 0.0, ua = 0.0, uq = 0.0, bad = 0.0;
+  if (cell < ncell) {
+    const uint32_t code0 = D->code4[(size_t)cell * 4];
+    if (!(code0 & kSolid)) {
+      Dbl4 *acc4 = reinterpret_cast<Dbl4 *>(D->acc);
+      const Dbl4 a = acc4[cell];
+      acc4[cell] = Dbl4{0.0, 0.0, 0.0, 0.0};
+      const double rho = a.x - s * D->sumW[0];
+      const double u1 = a.y - s * D->sumW[1];
+      const double u2 = a.z - s * D->sumW[2];
+      const double tau = (a.w - s * D->sumW[3]) - rho;
+      reinterpret_cast<Dbl4 *>(D->mom)[cell] = Dbl4{rho, u1, u2, tau};
+      const double d = D->uniform_delta ? D->delta : D->delta_field[cell];
+      const double A = d * (rho - c_new);
+      const double B = 2.0 * d * u1 + D->force;
+      const double Cc = 2.0 * d * u2;
+      const double Dd = d * tau;
+      SweepRec<T> *rec = static_cast<SweepRec<T> *>(D->rec);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double hw[2];
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+          const int src = D->hw_src[(size_t)cell * 8 + q * 2 + ax];
+          if (src >= 0) {
+            const int side = src & 3;
+            hw[ax] = (fcur[src] - s * D->ain[side]) / D->nrm[side];
+          } else {
+            hw[ax] = 0.0;
+          }
+        }
+        store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+      }
+      du = fabs(u1 - D->u1prev[cell]);
+      ua = fabs(u1);
+      uq = u1;
+      D->u1prev[cell] = u1;
+      if (!isfinite(rho) || !isfinite(u1) || !isfinite(u2) || !isfinite(tau)) bad = 1.0;
+    }
+    reinterpret_cast<Dbl4 *>(fnext)[cell] = Dbl4{0.0, 0.0, 0.0, 0.0};
+  }
+  du = block_sum(du, sh);
+  ua = block_sum(ua, sh);
+  uq = block_sum(uq, sh);
+  bad = block_sum(bad, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(&st->du_acc, du);
+    atomicAdd(&st->u_acc, ua);
+    atomicAdd(&st->q_acc, uq);
+    if (bad > 0.0) atomicExch(&st->nan_flag, 1);
+    __threadfence();
+    const unsigned t = atomicAdd(&st->ticket2, 1u);
+    if (t == (unsigned)D->fin_nblocks - 1u) {
+      __threadfence();
+      const double dsum = atomicAdd(&st->du_acc, 0.0);
+      const double usum = atomicAdd(&st->u_acc, 0.0);
+      const double qsum = atomicAdd(&st->q_acc, 0.0);
+      const int n = st->iter + 1;
+      const double eps = usum > 0.0 ? dsum / usum : 0.0;
+      const double back = st->eps_ring[n & 3];  // eps_{n-4}
+      st->eps_ring[n & 3] = eps;
+      double est = INFINITY;
+      int done = 0, status = 0;
+      if (n >= 5) {
+        double r = back > 0.0 ? pow(eps / back, 0.25) : 0.0;
+        if (r > 0.9999) r = 0.9999;
+        est = eps / (1.0 - r);
+        if (est < st->tol) {
+          done = 1;
+          status = 0;
+        }
+      }
+      if (!done && n >= st->max_iter) {
+        done = 1;
+        status = 4;  // DVM_ENOCONV
+      }
+      if (atomicAdd(&st->nan_flag, 0) != 0) {
+        done = 1;
+        status = 6;  // DVM_ENUMERIC
+      }
+      st->iter = n;
+      st->c = c_new;
+      st->s = s;
+      st->eps = eps;
+      st->est = est;
+      st->Q = qsum * D->dA_over_Lx;
+      st->du_acc = 0.0;
+      st->u_acc = 0.0;
+      st->q_acc = 0.0;
+      st->ticket2 = 0u;
+      st->status = status;
+      __threadfence();
+      st->done = done;
+    }
+  }
+}
+
+// h = 0: records with B = F (force) and everything else zero; state cleared.
+template <typename T>
+__global__ void reset_kernel(const InstanceDesc *D) {
+  const int ncell = D->ncell;
+  SweepRec<T> *rec = static_cast<SweepRec<T> *>(D->rec);
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncell; cell += gridDim.x * blockDim.x) {
+    const uint32_t code0 = D->code4[(size_t)cell * 4];
+    const double d = (code0 & kSolid) ? 0.0 : (D->uniform_delta ? D->delta : D->delta_field[cell]);
+    const double B = (code0 & kSolid) ? 0.0 : D->force;
+    for (int q = 0; q < 4; ++q)
+      store_rec<T>(rec + (size_t)q * ncell + cell, 0.0, B, 0.0, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DeviceState *st = D->state;
+    st->iter = 0;
+    st->done = 0;
+    st->status = 0;
+    st->max_iter = 0;
+    st->nan_flag = 0;
+    st->ticket1 = st->ticket2 = 0u;
+    st->tol = 0.0;
+    st->c = st->s = st->s_new = 0.0;
+    st->eps = st->est = st->Q = 0.0;
+    for (int k = 0; k < 4; ++k) st->eps_ring[k] = 0.0;
+    st->mass_acc = st->du_acc = st->u_acc = st->q_acc = 0.0;
+  }
+}
+
+__global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
+  st->tol = tol;
+  st->max_iter = max_iter_abs;
+  st->status = 0;
+  st->nan_flag = 0;
+  st->done = (st->iter >= max_iter_abs) ? 1 : 0;
+  if (st->done) st->status = 4;
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream) {
+  fin1_kernel<<<nblocks, kFinBlock, 0, stream>>>(L);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (fp64)
+    fin2_kernel<double><<<nblocks, kFinBlock, 0, stream>>>(L);
+  else
+    fin2_kernel<float><<<nblocks, kFinBlock, 0, stream>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream) {
+  const int blocks = (ncell + 255) / 256 < 1024 ? (ncell + 255) / 256 : 1024;
+  if (fp64)
+    reset_kernel<double><<<blocks, 256, 0, stream>>>(inst_dev);
+  else
+    reset_kernel<float><<<blocks, 256, 0, stream>>>(inst_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arm(DeviceState *st, double tol, int max_iter_abs, cudaStream_t stream) {
+  arm_kernel<<<1, 1, 0, stream>>>(st, tol, max_iter_abs);
+  return cudaGetLastError();
+}
+
+}  // namespace dvm

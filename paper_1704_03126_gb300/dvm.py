@@ -1,0 +1,282 @@
+"""ctypes binding of libdvm (include/dvm.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels.  Loading fails loudly when libdvm.so is
+missing or no CUDA device is present; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdvm.so")
+
+DVM_OK, DVM_EINVAL, DVM_ENOMEM, DVM_ECUDA, DVM_ENOCONV, DVM_ETIMEOUT, DVM_ENUMERIC, DVM_ESTATE = range(8)
+QUAD_KINDS = {"gh": 0, "nc": 1, "cubic": 2}
+FP64, FP32_ACC64 = 0, 1
+
+
+class DvmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS_NAMES = {0: "DVM_OK", 1: "DVM_EINVAL", 2: "DVM_ENOMEM", 3: "DVM_ECUDA", 4: "DVM_ENOCONV",
+                 5: "DVM_ETIMEOUT", 6: "DVM_ENUMERIC", 7: "DVM_ESTATE"}
+
+
+class Quad(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("vmax", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int),
+        ("ly", ctypes.c_double), ("kn", ctypes.c_double), ("delta", ctypes.c_double),
+        ("quad", Quad), ("accommodation", ctypes.c_double), ("precision", ctypes.c_int),
+        ("force", ctypes.c_double), ("store_distribution", ctypes.c_int), ("sweep_warps", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("eps", ctypes.c_double), ("est", ctypes.c_double),
+                ("mass_shift", ctypes.c_double), ("Q", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdvm.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdvm.so not found at {LIB_PATH}; build it first (python -c "
+                               "'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.dvm_params_init.argtypes = [ctypes.POINTER(Params)]
+        L.dvm_create.argtypes = [P, ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+        L.dvm_set_delta_field.argtypes = [P, P]
+        L.dvm_reset.argtypes = [P]
+        L.dvm_solve.argtypes = [P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.dvm_iterate.argtypes = [P, I]
+        L.dvm_flowrate.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.dvm_fields.argtypes = [P, P, P, P, P]
+        L.dvm_get_info.argtypes = [P, ctypes.POINTER(Info)]
+        L.dvm_distribution.argtypes = [P, P, I, P]
+        L.dvm_quadrature.argtypes = [P, P, P]
+        L.dvm_batch_solve.argtypes = [P, I, D, I, P]
+        L.dvm_velocity_grid.argtypes = [ctypes.POINTER(Quad), P, P]
+        L.dvm_batch_create.argtypes = [P, I, ctypes.POINTER(P)]
+        L.dvm_batch_run.argtypes = [P, D, I, P]
+        L.dvm_batch_iterate.argtypes = [P, I]
+        L.dvm_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+        L.dvm_batch_kernels_per_sweep.argtypes = [P]
+        L.dvm_batch_kernels_per_sweep.restype = I
+        L.dvm_batch_destroy.argtypes = [P]
+        L.dvm_last_error.argtypes = [P]
+        L.dvm_last_error.restype = ctypes.c_char_p
+        L.dvm_status_string.argtypes = [I]
+        L.dvm_status_string.restype = ctypes.c_char_p
+        L.dvm_destroy.argtypes = [P]
+        for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
+                     "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
+                     "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
+                     "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing"):
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One geometry: wraps a dvm_ctx.
+
+    mask: uint8 [ny][nx] (1 = solid); quad = (kind, n, vmax) with kind in {"gh", "nc", "cubic"};
+    exactly one of kn (> 0, inf allowed) and delta (>= 0).  stream: a cudaStream_t as int (e.g.
+    torch.cuda.current_stream().cuda_stream) or None.
+    """
+
+    def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
+                 precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None):
+        L = lib()
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self.mask = mask
+        p = Params()
+        L.dvm_params_init(ctypes.byref(p))
+        p.ny, p.nx = mask.shape
+        p.periodic_x = int(bool(periodic_x))
+        p.periodic_y = int(bool(periodic_y))
+        p.ly = float(ly)
+        if (kn is None) == (delta is None):
+            raise ValueError("give exactly one of kn and delta")
+        p.kn = float(kn) if kn is not None else -1.0
+        p.delta = float(delta) if delta is not None else -1.0
+        p.quad.kind = QUAD_KINDS[quad[0]]
+        p.quad.n = int(quad[1])
+        p.quad.vmax = float(quad[2]) if len(quad) > 2 else 5.0
+        p.precision = {"fp64": FP64, "fp32": FP32_ACC64}[precision]
+        p.force = float(force)
+        p.store_distribution = int(bool(store_distribution))
+        p.sweep_warps = int(sweep_warps)
+        self.params = p
+        self.nv = p.quad.n
+        self._ctx = ctypes.c_void_p()
+        st = L.dvm_create(_ptr(mask), ctypes.byref(p), ctypes.c_void_p(stream or 0), ctypes.byref(self._ctx))
+        if st != DVM_OK:
+            raise DvmError(st, L.dvm_last_error(None).decode())
+
+    def _check(self, st, allow=(DVM_OK,)):
+        if st not in allow:
+            raise DvmError(st, lib().dvm_last_error(self._ctx).decode())
+        return st
+
+    @property
+    def shape(self):
+        return self.mask.shape
+
+    def set_delta_field(self, delta_c):
+        if delta_c is None:
+            return self._check(lib().dvm_set_delta_field(self._ctx, None))
+        d = np.ascontiguousarray(delta_c, dtype=np.float64)
+        assert d.shape == self.shape
+        return self._check(lib().dvm_set_delta_field(self._ctx, _ptr(d)))
+
+    def reset(self):
+        return self._check(lib().dvm_reset(self._ctx))
+
+    def solve(self, tol=1e-10, max_iter=100000, raise_on_noconv=True):
+        """Returns (status, sweeps run, error estimate)."""
+        it = ctypes.c_int(0)
+        est = ctypes.c_double(0.0)
+        st = lib().dvm_solve(self._ctx, float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(est))
+        self._check(st, (DVM_OK,) if raise_on_noconv else (DVM_OK, DVM_ENOCONV))
+        return st, it.value, est.value
+
+    def iterate(self, n):
+        return self._check(lib().dvm_iterate(self._ctx, int(n)))
+
+    def flowrate(self):
+        q = ctypes.c_double()
+        ka = ctypes.c_double()
+        self._check(lib().dvm_flowrate(self._ctx, ctypes.byref(q), ctypes.byref(ka)))
+        return q.value, ka.value
+
+    def fields(self):
+        out = {k: np.empty(self.shape) for k in ("rho", "u1", "u2", "tau")}
+        self._check(lib().dvm_fields(self._ctx, _ptr(out["rho"]), _ptr(out["u1"]), _ptr(out["u2"]), _ptr(out["tau"])))
+        return out
+
+    def info(self):
+        inf = Info()
+        self._check(lib().dvm_get_info(self._ctx, ctypes.byref(inf)))
+        return dict(iterations=inf.iterations, eps=inf.eps, est=inf.est, mass_shift=inf.mass_shift, Q=inf.Q,
+                    status=inf.status)
+
+    def distribution(self, ks):
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        out = np.empty((len(ks),) + self.shape)
+        self._check(lib().dvm_distribution(self._ctx, _ptr(ks), len(ks), _ptr(out)))
+        return out
+
+    def quadrature(self):
+        x = np.empty(self.nv)
+        w = np.empty(self.nv)
+        self._check(lib().dvm_quadrature(self._ctx, _ptr(x), _ptr(w)))
+        return x, w
+
+    def close(self):
+        if self._ctx:
+            lib().dvm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Solvers advanced by one launch of each kernel per sweep (dvm_batch_*)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._ctx.value for s in self.solvers])
+        self._b = ctypes.c_void_p()
+        st = lib().dvm_batch_create(arr, len(self.solvers), ctypes.byref(self._b))
+        if st != DVM_OK:
+            raise DvmError(st, lib().dvm_last_error(self.solvers[0]._ctx).decode())
+
+    def _err(self, st):
+        raise DvmError(st, lib().dvm_last_error(self.solvers[0]._ctx).decode())
+
+    def run(self, tol=1e-10, max_iter=100000):
+        per = np.zeros(len(self.solvers), dtype=np.int32)
+        st = lib().dvm_batch_run(self._b, float(tol), int(max_iter), _ptr(per))
+        if st not in (DVM_OK, DVM_ENOCONV):
+            self._err(st)
+        return per
+
+    def iterate(self, n=1):
+        st = lib().dvm_batch_iterate(self._b, int(n))
+        if st != DVM_OK:
+            self._err(st)
+
+    def timing(self):
+        """(sweep_ms, finalize_ms) of the last single sweep."""
+        a = ctypes.c_float()
+        f = ctypes.c_float()
+        st = lib().dvm_batch_timing(self._b, ctypes.byref(a), ctypes.byref(f))
+        if st != DVM_OK:
+            self._err(st)
+        return a.value, f.value
+
+    def kernels_per_sweep(self):
+        return lib().dvm_batch_kernels_per_sweep(self._b)
+
+    def close(self):
+        if self._b:
+            lib().dvm_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_solve(solvers, tol=1e-10, max_iter=100000):
+    """Solve several Solvers in one batched launch per sweep; returns the per-instance statuses."""
+    n = len(solvers)
+    arr = (ctypes.c_void_p * n)(*[s._ctx.value for s in solvers])
+    per = np.zeros(n, dtype=np.int32)
+    st = lib().dvm_batch_solve(arr, n, float(tol), int(max_iter), _ptr(per))
+    if st not in (DVM_OK, DVM_ENOCONV):
+        raise DvmError(st, lib().dvm_last_error(solvers[0]._ctx).decode())
+    return per
+
+
+def velocity_grid(kind: str, n: int, vmax: float = 5.0):
+    """Library's 1D nodes and weights (host only, no GPU needed)."""
+    q = Quad(QUAD_KINDS[kind], int(n), float(vmax))
+    x = np.empty(n)
+    w = np.empty(n)
+    st = lib().dvm_velocity_grid(ctypes.byref(q), _ptr(x), _ptr(w))
+    if st != DVM_OK:
+        raise DvmError(st, lib().dvm_last_error(None).decode())
+    return x, w
+
+
+def kn_to_delta(kn: float) -> float:
+    return 0.0 if math.isinf(kn) else math.sqrt(math.pi) / (2.0 * kn)

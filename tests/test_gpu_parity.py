@@ -1,0 +1,189 @@
+"""GPU parity: libdvm (CUDA, through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated in the test, from the target accuracy of the two storage precisions):
+  FP64 path: |Q - Q_oracle| / |Q_oracle| < 1e-10, fields within 1e-9 absolute.
+  FP32 storage / FP64 accumulation: |Q - Q_oracle| / |Q_oracle| < 1e-5, fields within 1e-4 absolute.
+Both sides run the same discrete iteration (same stopping rule); parity is judged on converged fixed
+points, so iteration counts may differ by a sweep or two at the stopping knife edge.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03126_gb300 import build as dvm_build
+from paper_1704_03126_gb300 import dvm, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(q=1e-10, field=1e-9), "fp32": dict(q=1e-5, field=1e-4)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    dvm_build.build()
+    return dvm.lib()
+
+
+def _oracle_problem(mask, px, py, delta, quad):
+    return oracle.Problem.make(mask, px, py, delta, quad)
+
+
+def _compare(sol, orc, mask, precision):
+    tol = TOL[precision]
+    q, _ = sol.flowrate()
+    assert abs(q - orc["Q"]) < tol["q"] * abs(orc["Q"]), (q, orc["Q"])
+    f = sol.fields()
+    gas = mask == 0
+    for name in ("rho", "u1", "u2", "tau"):
+        err = np.abs(f[name][gas] - orc[name][gas]).max()
+        assert err < tol["field"], (name, err)
+        assert np.all(np.isnan(f[name][~gas]))
+
+
+def _solve_both(mask, px, py, kn, quad, precision, gpu_tol, orc_tol=1e-12, **kw):
+    delta = dvm.kn_to_delta(kn)
+    sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision=precision, **kw)
+    st, iters, est = sol.solve(tol=gpu_tol, max_iter=200000)
+    orc = oracle.solve(_oracle_problem(mask, px, py, delta, quad), tol=orc_tol, max_iter=200000)
+    assert orc["converged"]
+    return sol, orc, iters
+
+
+def test_plates_fp64_matches_oracle():
+    """Force-driven Poiseuille flow between diffuse plates: 4 x 32 cells, 12 x 12 Gauss-Hermite, Kn = 0.1."""
+    inst = inputs.plates_instance(kn=0.1)
+    sol, orc, iters = _solve_both(inst.mask, True, False, 0.1, inst.quad, "fp64", 1e-12)
+    _compare(sol, orc, inst.mask, "fp64")
+    assert abs(iters - orc["iters"]) <= 2
+    info = sol.info()
+    assert abs(info["mass_shift"] - orc["c"]) < 1e-12
+
+
+def test_plates_fp32_matches_oracle():
+    inst = inputs.plates_instance(kn=0.1)
+    sol, orc, iters = _solve_both(inst.mask, True, False, 0.1, inst.quad, "fp32", 1e-6)
+    _compare(sol, orc, inst.mask, "fp32")
+
+
+def _block_mask(nx, ny):
+    m = np.zeros((ny, nx), np.uint8)
+    m[ny // 3: ny // 3 + 3, nx // 2: nx // 2 + 4] = 1
+    return m
+
+
+CASES = [
+    # name, mask, periodic_x, periodic_y, kn, quad, sweep_warps
+    ("rough32_nc8_kn1", inputs.rough_channel_mask(32), True, False, 1.0, ("nc", 8, 4.0), 0),
+    ("rough32_nc8_kn0.1", inputs.rough_channel_mask(32), True, False, 0.1, ("nc", 8, 4.0), 0),
+    ("porous48_cubic12_kn0.5", inputs.porous_disks_mask(48, 0.6, 4, 7, seed=3)[0], True, True, 0.5, ("cubic", 12, 4.0), 0),
+    ("ragged37x29_block_gh8", _block_mask(37, 29), True, True, 0.3, ("gh", 8, 0.0), 0),
+    ("ragged37x29_warps5", _block_mask(37, 29), True, True, 0.3, ("gh", 8, 0.0), 5),
+    ("ragged_warps1", _block_mask(9, 7), True, True, 2.0, ("gh", 6, 0.0), 1),
+    ("narrow3x40_nonperiodic_y", np.zeros((40, 3), np.uint8), True, False, 0.05, ("gh", 10, 0.0), 0),
+    ("closed_box_16", _block_mask(16, 16), False, False, 1.0, ("nc", 10, 4.0), 0),
+    ("periodic_y_only", _block_mask(12, 20).T.copy(), False, True, 1.0, ("gh", 8, 0.0), 0),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small_geometries_match_oracle(case, precision):
+    name, mask, px, py, kn, quad, warps = case
+    gpu_tol = 1e-12 if precision == "fp64" else 1e-6
+    sol, orc, iters = _solve_both(mask, px, py, kn, quad, precision, gpu_tol, sweep_warps=warps)
+    _compare(sol, orc, mask, precision)
+
+
+def test_delta_field_matches_oracle():
+    mask = _block_mask(20, 16)
+    rng = np.random.default_rng(5)
+    d = rng.uniform(0.3, 3.0, size=mask.shape)
+    quad = ("cubic", 10, 4.0)
+    sol = dvm.Solver(mask, True, True, delta=1.0, quad=quad, precision="fp64")
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-12, max_iter=100000)
+    orc = oracle.solve(_oracle_problem(mask, True, True, d, quad), tol=1e-12, max_iter=100000)
+    _compare(sol, orc, mask, "fp64")
+    q, ka = sol.flowrate()
+    assert np.isnan(ka)
+
+
+def test_one_sweep_matches_oracle_velocity_by_velocity():
+    """From the GPU's stored state h^n, the oracle sweeps selected velocities once; the GPU's h^{n+1}
+    must agree (after the same mass shift)."""
+    mask = inputs.rough_channel_mask(24)
+    quad = ("nc", 8, 4.0)
+    sol = dvm.Solver(mask, True, False, kn=0.5, quad=quad, precision="fp64", store_distribution=True)
+    sol.iterate(3)
+    K = quad[1] ** 2
+    h_n = sol.distribution(np.arange(K))
+    c_n = sol.info()["mass_shift"]
+    sol.iterate(1)
+    c_np1 = sol.info()["mass_shift"]
+    ks = [0, 9, 27, 36, 63]
+    h_np1 = sol.distribution(ks)
+    p = _oracle_problem(mask, True, False, dvm.kn_to_delta(0.5), quad)
+    ref = oracle.sweep_selected(p, h_n, c_n, ks) - (c_np1 - c_n)
+    gas = mask == 0
+    err = np.abs((ref - h_np1)[:, gas]).max()
+    assert err < 1e-12 * max(1.0, np.abs(ref).max()), err
+
+
+def test_batch_matches_single_solves():
+    specs = [
+        (inputs.rough_channel_mask(32), True, False, 1.0, ("nc", 8, 4.0)),
+        (inputs.porous_disks_mask(40, 0.65, 4, 6, seed=2)[0], True, True, 0.2, ("cubic", 12, 4.0)),
+        (inputs.plates_mask(4, 24), True, False, 5.0, ("gh", 16, 0.0)),
+    ]
+    singles, batch = [], []
+    for (m, px, py, kn, quad) in specs:
+        s = dvm.Solver(m, px, py, kn=kn, quad=quad, precision="fp64")
+        s.solve(tol=1e-12, max_iter=100000)
+        singles.append(s.flowrate()[0])
+        batch.append(dvm.Solver(m, px, py, kn=kn, quad=quad, precision="fp64"))
+    per = dvm.batch_solve(batch, tol=1e-12, max_iter=100000)
+    assert list(per) == [0, 0, 0]
+    for s, q in zip(batch, singles):
+        assert abs(s.flowrate()[0] - q) < 1e-11 * abs(q)
+
+
+def test_results_before_solve_rejected():
+    sol = dvm.Solver(inputs.plates_mask(4, 8), True, False, kn=1.0, quad=("gh", 4, 0.0))
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.flowrate()
+    assert ei.value.status == dvm.DVM_ESTATE
+
+
+def test_max_iter_reports_noconv():
+    sol = dvm.Solver(inputs.plates_mask(4, 16), True, False, kn=0.1, quad=("gh", 8, 0.0))
+    st, iters, est = sol.solve(tol=1e-14, max_iter=7, raise_on_noconv=False)
+    assert st == dvm.DVM_ENOCONV and iters == 7
+    # continuing picks up where it stopped and matches an uninterrupted solve
+    sol.solve(tol=1e-12, max_iter=100000)
+    ref = dvm.Solver(inputs.plates_mask(4, 16), True, False, kn=0.1, quad=("gh", 8, 0.0))
+    ref.solve(tol=1e-12, max_iter=100000)
+    assert abs(sol.flowrate()[0] - ref.flowrate()[0]) < 1e-10 * abs(ref.flowrate()[0])
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def test_rough_channel_full_size_fixed_point():
+    """Rough channel 128 x 128, 32 x 32 trapezoid velocities on [-5, 5], Kn = 1, in the launch
+    configuration the benchmark times (FP32 storage).  At this size the oracle checks, velocity by
+    velocity, that the GPU state is a fixed point of its own sweep, and the mirror symmetries."""
+    inst = inputs.rough_instance(1.0)
+    sol = dvm.Solver(inst.mask, True, False, kn=1.0, quad=inst.quad, precision="fp32", store_distribution=True)
+    st, iters, est = sol.solve(tol=1e-6, max_iter=20000)
+    K = inst.quad[1] ** 2
+    h = sol.distribution(np.arange(K))
+    c = sol.info()["mass_shift"]
+    p = _oracle_problem(inst.mask, True, False, dvm.kn_to_delta(1.0), inst.quad)
+    ks = [0, 33, 200, 511, 512, 700, 1023]
+    out = oracle.sweep_selected(p, h, c, ks)
+    gas = inst.mask == 0
+    scale = np.abs(h).max()
+    assert np.abs((out - h[ks])[:, gas]).max() < 1e-5 * scale
+    f = sol.fields()
+    u1 = f["u1"]
+    assert np.nanmax(np.abs(u1 - u1[:, ::-1])) < 1e-4
+    assert np.nanmax(np.abs(u1 - u1[::-1, :])) < 1e-4

@@ -1,0 +1,94 @@
+"""Host-side checks of libdvm that need no GPU: the C ABI loads and exports every declared symbol,
+argument validation, and the library's own velocity quadratures (Golub-Welsch Gauss-Hermite,
+trapezoid Newton-Cotes, the cubic grid of Eq. nonuniform_v) against numpy and the oracle."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03126_gb300 import build as dvm_build
+from paper_1704_03126_gb300 import dvm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    dvm_build.build()
+    return dvm.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dvm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dvm_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "dvm_create" in names and "dvm_solve" in names and "dvm_batch_solve" in names
+    L = dvm.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("n", [2, 8, 12, 16, 32, 48, 64])
+def test_library_gauss_hermite_matches_numpy(n):
+    x, w = dvm.velocity_grid("gh", n)
+    xr, wr = np.polynomial.hermite.hermgauss(n)
+    assert np.max(np.abs(x - xr)) < 1e-12 * max(1.0, np.abs(xr).max())
+    # Golub-Welsch weights come from eigenvector components: absolute accuracy ~1e-15
+    assert np.max(np.abs(w - wr / math.sqrt(math.pi))) < 5e-15
+    assert np.all(x == -x[::-1])
+
+
+@pytest.mark.parametrize("kind,n,vmax", [("nc", 32, 5.0), ("nc", 8, 4.0), ("cubic", 48, 4.0), ("cubic", 16, 4.0),
+                                         ("gh", 24, 0.0)])
+def test_library_grids_match_oracle(kind, n, vmax):
+    x, w = dvm.velocity_grid(kind, n, vmax)
+    xo, wo = oracle.quadrature(kind, n, vmax)
+    assert np.max(np.abs(x - xo)) < 5e-14
+    assert np.max(np.abs(w - wo)) < 5e-15
+    assert np.all(x == -x[::-1])
+
+
+def test_library_rejects_invalid_grids():
+    for kind, n in [("gh", 7), ("nc", 1), ("cubic", 66)]:
+        with pytest.raises(dvm.DvmError) as ei:
+            dvm.velocity_grid(kind, n)
+        assert ei.value.status == dvm.DVM_EINVAL
+
+
+@pytest.mark.parametrize("kwargs", [
+    dict(mask=np.zeros((8, 1), np.uint8), kn=1.0),                     # nx < 2
+    dict(mask=np.ones((8, 8), np.uint8), kn=1.0),                      # no gas cell
+    dict(mask=np.zeros((8, 8), np.uint8), kn=-1.0),                    # neither kn nor delta
+    dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, quad=("gh", 7)),     # odd velocity grid
+    dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, ly=0.0),             # bad height
+])
+def test_create_rejects_invalid_parameters(kwargs):
+    with pytest.raises(dvm.DvmError) as ei:
+        dvm.Solver(**kwargs)
+    assert ei.value.status == dvm.DVM_EINVAL
+
+
+def test_both_kn_and_delta_rejected_by_the_library():
+    L = dvm.lib()
+    p = dvm.Params()
+    L.dvm_params_init(p)
+    p.nx, p.ny, p.kn, p.delta = 4, 4, 1.0, 1.0
+    mask = np.zeros((4, 4), np.uint8)
+    import ctypes
+    ctx = ctypes.c_void_p()
+    st = L.dvm_create(mask.ctypes.data_as(ctypes.c_void_p), ctypes.byref(p), None, ctypes.byref(ctx))
+    assert st == dvm.DVM_EINVAL
+    assert b"exactly one" in L.dvm_last_error(None)
+
+
+def test_status_strings():
+    L = dvm.lib()
+    assert L.dvm_status_string(0) == b"DVM_OK"
+    assert L.dvm_status_string(4) == b"DVM_ENOCONV"
