@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dvm_oracle.c")
 _SO = os.path.join(_HERE, "_build", "liboracle.so")
 
-ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_ENOCONV = 0, 1, 2, 4
+ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_ENOCONV, ORC_ENUMERIC = 0, 1, 2, 4, 6
 
 _lib_handle = None
 
@@ -184,7 +184,8 @@ def solve(prob: Problem, tol: float = 1e-10, max_iter: int = 100000, h0=None, c0
     if st == ORC_ENOMEM:
         raise MemoryError("oracle out of memory")
     return dict(h=h, rho=rho, u1=u1, u2=u2, tau=tau, Q=res.Q, c=res.c_shift, iters=res.iters,
-                eps=res.eps, est=res.est, eps_hist=eps_hist[:res.iters], converged=(st == ORC_OK))
+                eps=res.eps, est=res.est, eps_hist=eps_hist[:res.iters], converged=(st == ORC_OK),
+                status=st)
 
 
 def sweep_selected(prob: Problem, h_in: np.ndarray, c_shift: float, ks):

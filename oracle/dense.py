@@ -2,15 +2,17 @@
 
 TEST INFRASTRUCTURE ONLY.  Written independently of ``dvm_oracle.c``: it assembles the steady
 discrete equations of Sec. II.A (Eq. BGK with the time derivative dropped, Eq. diffuse2 walls,
-periodic ends, second-order upwind differences) as one matrix and solves it with LAPACK, with no
+periodic ends, second-order upwind differences -- linear through the wall-face value in the cell
+next to a wall, first order in the cell after it) as one matrix and solves it with LAPACK, with no
 iteration, no lagging and no sweep order.  Unknowns: h[k, g] for every velocity k and gas cell g,
 plus the scalar c that borders the system:
 
     (delta_c + v.D) h_k - delta_c M_k(h) + delta_c c = F v1_k      (every gas cell, velocity)
     sum_gas sum_k W_k h_k = 0                                       (mean density zero)
 
-with M_k(h) = sum_j W_j h_j [1 + 2 v_k.v_j + (|v_k|^2 - 1)(|v_j|^2 - 1)] (the moments rho, u, tau
-of Sec. II.A inserted in L).  Wall values h_w = alpha rho_w + (1 - alpha) h(mirror v), with
+with M_k(h) = sum_j W_j psi(v_k)^T G^{-1} psi(v_j) h_j, psi = (1, v1, v2, |v|^2), G the quadrature
+Gram matrix of psi: the projection of h onto the collision invariants, which for an exact quadrature
+is rho + 2 u.v + tau (|v|^2 - 1) with the moments rho, u, tau of Sec. II.A.  Wall values h_w = alpha rho_w + (1 - alpha) h(mirror v), with
 rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W at the gas cell owning the face.
 """
 from __future__ import annotations
@@ -31,6 +33,13 @@ def _solid(mask, px, py, i, j):
     return bool(mask[j, i])
 
 
+def collision_kernel(v1, v2, W):
+    """C[k, j] = W_j psi(v_k)^T G^{-1} psi(v_j): M_k(h) = sum_j C[k, j] h_j."""
+    psi = np.stack([np.ones_like(v1), v1, v2, v1 * v1 + v2 * v2])  # [4][K]
+    G = (psi * W[None, :]) @ psi.T
+    return (psi.T @ np.linalg.inv(G) @ psi) * W[None, :]
+
+
 def assemble(prob):
     """Dense bordered matrix B and right-hand side b; also the gas-cell index map."""
     mask = prob.mask
@@ -47,9 +56,7 @@ def assemble(prob):
     b = np.zeros(n + 1)
     dx = prob.dx
     nv = prob.nv
-    e = v1 * v1 + v2 * v2 - 1.0
-    # collision kernel C[k, j] = W_j [1 + 2 v_k.v_j + e_k e_j]
-    Ckern = W[None, :] * (1.0 + 2.0 * (np.outer(v1, v1) + np.outer(v2, v2)) + np.outer(e, e))
+    Ckern = collision_kernel(v1, v2, W)
     # wall normalisers per side: W (normal +x), E (-x), S (+y), N (-y)
     normal = {"W": (1.0, 0.0), "E": (-1.0, 0.0), "S": (0.0, 1.0), "N": (0.0, -1.0)}
     vn = {s: v1 * nxy[0] + v2 * nxy[1] for s, nxy in normal.items()}
@@ -88,10 +95,10 @@ def assemble(prob):
                     diag += ca * 2.0
                     add_wall(row, ca * 2.0, g, side, k)
                 elif _solid(mask, px, py, i2, j2):
-                    diag += ca * 5.0 / 3.0
+                    # second cell from a wall: first-order upwind through the gas neighbour
+                    diag += ca
                     g1 = gid[(i1 % nx, j1 % ny)]
-                    B[row, idx(k, g1)] -= ca * 3.0
-                    add_wall(row, -ca * 4.0 / 3.0, g1, side, k)
+                    B[row, idx(k, g1)] -= ca
                 else:
                     diag += ca * 1.5
                     g1 = gid[(i1 % nx, j1 % ny)]
@@ -149,8 +156,7 @@ def adjoint_gradient(prob, sol=None):
     for k in range(K):
         g[k * G:(k + 1) * G] = W[k] * v1[k] * dA_over_L
     lam = np.linalg.solve(B.T, g)
-    e = v1 * v1 + v2 * v2 - 1.0
-    Ckern = W[None, :] * (1.0 + 2.0 * (np.outer(v1, v1) + np.outer(v2, v2)) + np.outer(e, e))
+    Ckern = collision_kernel(v1, v2, W)
     grad = np.zeros((ny, nx))
     c = x[-1]
     for gi, (i, j) in enumerate(gas_cells):

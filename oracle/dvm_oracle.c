@@ -25,12 +25,20 @@
  *             [-vmax, vmax]; Gauss-Hermite nodes/weights divided by sqrt(pi).
  *   stencil   cell-centred grid, walls on cell faces.  Along one axis, with s = sign(v_a),
  *             u1 = cell - s, u2 = cell - 2 s, the term v_a dh/dx_a is (|v_a|/dx) (kappa h0 - combo):
- *               both upstream cells gas : kappa = 3/2, combo = 2 h(u1) - h(u2)/2
- *               u1 gas, u2 solid        : kappa = 5/3, combo = 3 h(u1) - 4/3 h_w(face u1|u2)
+ *               both upstream cells gas : kappa = 3/2, combo = 2 h(u1) - h(u2)/2  (second order)
+ *               u1 gas, u2 solid        : kappa = 1,   combo = h(u1)              (first order)
  *               u1 solid                : kappa = 2,   combo = 2 h_w(face cell|u1)
- *             (the quadratic / linear upwind interpolants through the wall face value).
+ *             The last is the linear interpolant through the wall-face value.  Every form is exact
+ *             on linear fields.  The quadratic through h0, h(u1) and the wall value would put a
+ *             negative weight on the lagged wall value, and the iteration then diverges in narrow
+ *             pores (an oscillating mode), so the second cell from a wall is first order.
  *   wall      h_w = alpha rho_w + (1 - alpha) h(mirror v) at the face's gas cell, where
  *             rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W (discrete zero mass flux).
+ *   collision the discrete L is the projection of h onto span{1, v1, v2, |v|^2} in the quadrature
+ *             inner product, L = delta sum_i a_i psi_i(v) with a = G^{-1} m, G_ij = sum_k W psi_i psi_j
+ *             and m_j = sum_k W psi_j h (psi = 1, v1, v2, |v|^2).  For an exact quadrature this is
+ *             delta [rho + 2 u.v + tau (|v|^2 - 1)] of Eq. BGK; for an inexact one it still conserves
+ *             the discrete mass, momentum and energy, as the BGK operator does.
  *   lagging   values across a periodic seam and the wall values come from the previous iterate.
  *   mass      h = const solves the homogeneous problem; after every sweep the mean density over
  *             the gas cells is projected to zero by a constant shift s, accumulated in c, and the
@@ -50,6 +58,7 @@
 #define ORC_EINVAL 1
 #define ORC_ENOMEM 2
 #define ORC_ENOCONV 4
+#define ORC_ENUMERIC 6
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -192,6 +201,53 @@ static int mirror_velocity(const orc_problem *p, int k, int side) {
   return a * p->nv + b;
 }
 
+/* Inverse of the 4 x 4 Gram matrix G_ij = sum_k W_k psi_i(v_k) psi_j(v_k), psi = (1, v1, v2, |v|^2),
+ * by Gauss-Jordan elimination with partial pivoting.  Returns 0 when G is singular. */
+static int gram_inverse(const orc_problem *p, double ginv[16]) {
+  double a[4][8];
+  int K = p->nv * p->nv;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) a[i][j] = (j - 4 == i) ? 1.0 : 0.0;
+  for (int k = 0; k < K; ++k) {
+    double v1 = p->xv[k / p->nv], v2 = p->xv[k % p->nv];
+    double W = p->wv[k / p->nv] * p->wv[k % p->nv];
+    double psi[4] = {1.0, v1, v2, v1 * v1 + v2 * v2};
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) a[i][j] += W * psi[i] * psi[j];
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+    if (a[piv][col] == 0.0) return 0;
+    for (int j = 0; j < 8; ++j) { double t = a[col][j]; a[col][j] = a[piv][j]; a[piv][j] = t; }
+    double d = a[col][col];
+    for (int j = 0; j < 8; ++j) a[col][j] /= d;
+    for (int r = 0; r < 4; ++r) {
+      if (r == col) continue;
+      double f = a[r][col];
+      for (int j = 0; j < 8; ++j) a[r][j] -= f * a[col][j];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) ginv[i * 4 + j] = a[i][j + 4];
+  return 1;
+}
+
+/* Collision coefficients a = G^{-1} m of every gas cell from the moments (m = rho, u1, u2, tau + rho). */
+static void collision_coefficients(const orc_problem *p, const double ginv[16], const double *rho,
+                                   const double *u1, const double *u2, const double *tau, double *a) {
+  size_t ncell = (size_t)p->nx * p->ny;
+  for (size_t c = 0; c < ncell; ++c) {
+    double m[4] = {rho[c], u1[c], u2[c], tau[c] + rho[c]};
+    for (int i = 0; i < 4; ++i) {
+      double s = 0;
+      for (int j = 0; j < 4; ++j) s += ginv[i * 4 + j] * m[j];
+      a[c * 4 + i] = p->mask[c] ? 0.0 : s;
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Moments, wall values and one transport sweep.                                              */
 /* ------------------------------------------------------------------------------------------ */
@@ -277,9 +333,8 @@ static void upwind_axis(const orc_problem *p, const double *hk, const double *rh
     *kappa = 2.0;
     *combo = 2.0 * wall_value(p, rho_w, h_old, cell_id(p, i, j), side, k);
   } else if (solid_at(p, i2, j2)) {
-    *kappa = 5.0 / 3.0;
-    *combo = 3.0 * hk[cell_id(p, i1, j1)] -
-             (4.0 / 3.0) * wall_value(p, rho_w, h_old, cell_id(p, i1, j1), side, k);
+    *kappa = 1.0;
+    *combo = hk[cell_id(p, i1, j1)];
   } else {
     *kappa = 1.5;
     *combo = 2.0 * hk[cell_id(p, i1, j1)] - 0.5 * hk[cell_id(p, i2, j2)];
@@ -288,13 +343,14 @@ static void upwind_axis(const orc_problem *p, const double *hk, const double *rh
 
 /* Sweep velocity k over all gas cells in its upwind order, in place in hk = h[k]:
  *   (delta + sum_a |v_a|/dx kappa_a) h = R + sum_a |v_a|/dx combo_a,
- *   R = delta (rho + 2 u.v + tau (|v|^2 - 1) - c) + F v1        [Eq. iteration, Eq. BGK] */
-static void sweep_velocity(const orc_problem *p, int k, double *hk, const double *rho,
-                           const double *u1, const double *u2, const double *tau, double c_shift,
-                           const double *rho_w, const double *h_old) {
+ *   R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v1         [Eq. iteration, Eq. BGK]
+ * with the collision coefficients a of each cell (exact quadrature: a0 + a3 |v|^2 + ... =
+ * rho + 2 u.v + tau (|v|^2 - 1)). */
+static void sweep_velocity(const orc_problem *p, int k, double *hk, const double *acoef,
+                           double c_shift, const double *rho_w, const double *h_old) {
   double v1 = p->xv[k / p->nv], v2 = p->xv[k % p->nv];
   int s1 = v1 > 0 ? 1 : -1, s2 = v2 > 0 ? 1 : -1;
-  double cx = fabs(v1) / p->dx, cy = fabs(v2) / p->dx, e = v1 * v1 + v2 * v2 - 1.0;
+  double cx = fabs(v1) / p->dx, cy = fabs(v2) / p->dx, vsq = v1 * v1 + v2 * v2;
   for (int jj = 0; jj < p->ny; ++jj) {
     int j = s2 > 0 ? jj : p->ny - 1 - jj;
     for (int ii = 0; ii < p->nx; ++ii) {
@@ -305,7 +361,8 @@ static void sweep_velocity(const orc_problem *p, int k, double *hk, const double
       upwind_axis(p, hk, rho_w, h_old, k, i, j, 1, 0, s1, &kx, &bx);
       upwind_axis(p, hk, rho_w, h_old, k, i, j, 0, 1, s2, &ky, &by);
       double d = p->delta[c];
-      double R = d * (rho[c] + 2.0 * (u1[c] * v1 + u2[c] * v2) + tau[c] * e - c_shift) + p->force * v1;
+      const double *a = acoef + c * 4;
+      double R = d * (a[0] + a[1] * v1 + a[2] * v2 + a[3] * vsq - c_shift) + p->force * v1;
       hk[c] = (R + cx * bx + cy * by) / (d + cx * kx + cy * ky);
     }
   }
@@ -346,12 +403,15 @@ int orc_solve(const orc_problem *p, double tol, int max_iter, double *h, double 
   double sumW = 0;
   for (int k = 0; k < K; ++k) sumW += p->wv[k / p->nv] * p->wv[k % p->nv];
 
+  double ginv[16];
+  if (!gram_inverse(p, ginv)) return ORC_EINVAL;
   double *rho_w = (double *)calloc(ncell * 4, sizeof(double));
   double *u1_prev = (double *)calloc(ncell, sizeof(double));
+  double *acoef = (double *)calloc(ncell * 4, sizeof(double));
   double *h_old = (p->alpha < 1.0) ? (double *)malloc((size_t)K * ncell * sizeof(double)) : NULL;
   double eps_ring[4] = {0, 0, 0, 0}; /* slot n % 4 holds eps_{n-4} */
-  if (!rho_w || !u1_prev || (p->alpha < 1.0 && !h_old)) {
-    free(rho_w); free(u1_prev); free(h_old);
+  if (!rho_w || !u1_prev || !acoef || (p->alpha < 1.0 && !h_old)) {
+    free(rho_w); free(u1_prev); free(acoef); free(h_old);
     return ORC_ENOMEM;
   }
   compute_moments(p, h, rho, u1, u2, tau);
@@ -362,10 +422,11 @@ int orc_solve(const orc_problem *p, double tol, int max_iter, double *h, double 
   for (n = 1; n <= max_iter; ++n) {
     /* wall values and (for alpha < 1) the specular source from the previous iterate */
     compute_wall_density(p, h, rho_w);
+    collision_coefficients(p, ginv, rho, u1, u2, tau, acoef);
     if (h_old) memcpy(h_old, h, (size_t)K * ncell * sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < K; ++k)
-      sweep_velocity(p, k, h + (size_t)k * ncell, rho, u1, u2, tau, c_shift, rho_w, h_old);
+      sweep_velocity(p, k, h + (size_t)k * ncell, acoef, c_shift, rho_w, h_old);
 
     /* project the mean gas density to zero: s = sum_gas rho / (n_gas sum W) */
     double mass = 0;
@@ -383,11 +444,14 @@ int orc_solve(const orc_problem *p, double tol, int max_iter, double *h, double 
 
     compute_moments(p, h, rho, u1, u2, tau);
     double dsum = 0, usum = 0;
+    int finite = isfinite(s);
     for (size_t c = 0; c < ncell; ++c) {
       if (p->mask[c]) continue;
       dsum += fabs(u1[c] - u1_prev[c]);
       usum += fabs(u1[c]);
+      finite = finite && isfinite(rho[c]) && isfinite(u1[c]) && isfinite(u2[c]) && isfinite(tau[c]);
     }
+    if (!finite) { status = ORC_ENUMERIC; break; }
     memcpy(u1_prev, u1, ncell * sizeof(double));
     eps = usum > 0 ? dsum / usum : 0.0;
     if (eps_hist) eps_hist[n - 1] = eps;
@@ -407,7 +471,7 @@ int orc_solve(const orc_problem *p, double tol, int max_iter, double *h, double 
   res->est = est;
   res->c_shift = c_shift;
   res->Q = q_flow(p, u1);
-  free(rho_w); free(u1_prev); free(h_old);
+  free(rho_w); free(u1_prev); free(acoef); free(h_old);
   return status;
 }
 
@@ -418,17 +482,20 @@ int orc_sweep_selected(const orc_problem *p, const double *h_in, double c_shift,
                        int nk, double *out) {
   size_t ncell = (size_t)p->nx * p->ny;
   int K = p->nv * p->nv;
-  double *rho = (double *)malloc(ncell * sizeof(double) * 4);
+  double ginv[16];
+  if (!gram_inverse(p, ginv)) return ORC_EINVAL;
+  double *rho = (double *)malloc(ncell * sizeof(double) * 8);
   double *rho_w = (double *)calloc(ncell * 4, sizeof(double));
   if (!rho || !rho_w) { free(rho); free(rho_w); return ORC_ENOMEM; }
-  double *u1 = rho + ncell, *u2 = rho + 2 * ncell, *tau = rho + 3 * ncell;
+  double *u1 = rho + ncell, *u2 = rho + 2 * ncell, *tau = rho + 3 * ncell, *acoef = rho + 4 * ncell;
   compute_moments(p, h_in, rho, u1, u2, tau);
+  collision_coefficients(p, ginv, rho, u1, u2, tau, acoef);
   compute_wall_density(p, h_in, rho_w);
   int status = ORC_OK;
   for (int m = 0; m < nk; ++m) {
     if (ks[m] < 0 || ks[m] >= K) { status = ORC_EINVAL; break; }
     memcpy(out + (size_t)m * ncell, h_in + (size_t)ks[m] * ncell, ncell * sizeof(double));
-    sweep_velocity(p, ks[m], out + (size_t)m * ncell, rho, u1, u2, tau, c_shift, rho_w, h_in);
+    sweep_velocity(p, ks[m], out + (size_t)m * ncell, acoef, c_shift, rho_w, h_in);
   }
   free(rho); free(rho_w);
   return status;
@@ -446,7 +513,8 @@ int orc_sweep_selected(const orc_problem *p, const double *h_in, double c_shift,
  *   lambda' = lambda + rho (mu - sum lambda)              (transpose of P)
  *   z       = T^{-T} lambda'                              (reverse-order sweep per velocity)
  *   lambda  = (delta M)^T z + L^T z + g,  mu = mu - sum delta z
- * and dQ/d delta_c = sum_k z_kc (M_kc - c - h_kc).  Identity at convergence: Q = F sum z v1.
+ * and dQ/d delta_c = sum_k z_kc (M_kc - c - h_kc), M_kc = a(c) . psi(v_k) the collision part.
+ * Identity at convergence: Q = F sum z v1.
  */
 
 /* Push form of the transposed upwind sweep for velocity k: acc holds lambda'_k on entry and is
@@ -472,7 +540,7 @@ static void adjoint_sweep_velocity(const orc_problem *p, int k, double *acc, dou
       for (int ax = 0; ax < 2; ++ax) {
         int di = ax == 0, dj = ax == 1, s = ax == 0 ? s1 : s2;
         if (solid_at(p, i - s * di, j - s * dj)) kap[ax] = 2.0;
-        else if (solid_at(p, i - 2 * s * di, j - 2 * s * dj)) kap[ax] = 5.0 / 3.0;
+        else if (solid_at(p, i - 2 * s * di, j - 2 * s * dj)) kap[ax] = 1.0;
         else kap[ax] = 1.5;
         diag += cxy[ax] * kap[ax];
       }
@@ -493,10 +561,8 @@ static void adjoint_sweep_velocity(const orc_problem *p, int k, double *acc, dou
           ref_cell[0] = c; ref_is_wall[0] = 1; ref_wrapped[0] = 0; ref_coef[0] = 2.0; nref = 1;
         } else if (solid_at(p, i2, j2)) {
           ref_cell[0] = cell_id(p, i1, j1); ref_is_wall[0] = 0; ref_wrapped[0] = wrapped1;
-          ref_coef[0] = 3.0;
-          ref_cell[1] = cell_id(p, i1, j1); ref_is_wall[1] = 1; ref_wrapped[1] = 0;
-          ref_coef[1] = -4.0 / 3.0;
-          nref = 2;
+          ref_coef[0] = 1.0;
+          nref = 1;
         } else {
           ref_cell[0] = cell_id(p, i1, j1); ref_is_wall[0] = 0; ref_wrapped[0] = wrapped1;
           ref_coef[0] = 2.0;
@@ -561,6 +627,13 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
   }
   double *rho = mom, *u1 = mom + ncell, *u2 = mom + 2 * ncell, *tau = mom + 3 * ncell;
   compute_moments(p, h, rho, u1, u2, tau);
+  double ginv[16];
+  double *acoef = (double *)malloc(4 * ncell * sizeof(double));
+  if (!acoef || !gram_inverse(p, ginv)) {
+    free(lam); free(lam_new); free(acc); free(z); free(mom); free(gprev); free(acoef);
+    return acoef ? ORC_EINVAL : ORC_ENOMEM;
+  }
+  collision_coefficients(p, ginv, rho, u1, u2, tau, acoef);
   double dA_over_L = p->dx * p->dx / (p->nx * p->dx);
   double mu = 0.0;
   double eps_ring[4] = {0, 0, 0, 0}; /* slot n % 4 holds eps_{n-4} */
@@ -583,20 +656,22 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
     double dz = 0;
     for (size_t c = 0; c < ncell; ++c) {
       if (p->mask[c]) continue;
-      double Z0 = 0, Z1 = 0, Z2 = 0, Ze = 0;
+      /* M_k(h) = sum_j W_j psi(v_k)^T G^{-1} psi(v_j) h_j, so (delta M)^T z at velocity j is
+       * delta W_j psi(v_j)^T G^{-1} Z with Z = sum_k psi(v_k) z_k */
+      double Z[4] = {0, 0, 0, 0}, GZ[4];
       for (int k = 0; k < K; ++k) {
         double v1 = p->xv[k / p->nv], v2 = p->xv[k % p->nv];
         double zz = z[(size_t)k * ncell + c];
-        Z0 += zz; Z1 += v1 * zz; Z2 += v2 * zz; Ze += (v1 * v1 + v2 * v2 - 1.0) * zz;
+        Z[0] += zz; Z[1] += v1 * zz; Z[2] += v2 * zz; Z[3] += (v1 * v1 + v2 * v2) * zz;
       }
+      for (int i = 0; i < 4; ++i) GZ[i] = ginv[i * 4] * Z[0] + ginv[i * 4 + 1] * Z[1] + ginv[i * 4 + 2] * Z[2] + ginv[i * 4 + 3] * Z[3];
       double d = p->delta[c];
-      dz += d * Z0;
+      dz += d * Z[0];
       for (int k = 0; k < K; ++k) {
         double v1 = p->xv[k / p->nv], v2 = p->xv[k % p->nv];
         double W = p->wv[k / p->nv] * p->wv[k % p->nv];
         lam_new[(size_t)k * ncell + c] +=
-            d * W * (Z0 + 2.0 * (v1 * Z1 + v2 * Z2) + (v1 * v1 + v2 * v2 - 1.0) * Ze) +
-            W * v1 * dA_over_L;
+            d * W * (GZ[0] + GZ[1] * v1 + GZ[2] * v2 + GZ[3] * (v1 * v1 + v2 * v2)) + W * v1 * dA_over_L;
       }
     }
     mu -= dz;
@@ -608,7 +683,8 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
       if (!p->mask[c]) {
         for (int k = 0; k < K; ++k) {
           double v1 = p->xv[k / p->nv], v2 = p->xv[k % p->nv];
-          double M = rho[c] + 2.0 * (u1[c] * v1 + u2[c] * v2) + tau[c] * (v1 * v1 + v2 * v2 - 1.0);
+          const double *a = acoef + c * 4;
+          double M = a[0] + a[1] * v1 + a[2] * v2 + a[3] * (v1 * v1 + v2 * v2);
           g += z[(size_t)k * ncell + c] * (M - c_shift - h[(size_t)k * ncell + c]);
         }
       }
@@ -634,6 +710,6 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
   }
   *q_identity = qid;
   *iters_out = n;
-  free(lam); free(lam_new); free(acc); free(z); free(mom); free(gprev);
+  free(lam); free(lam_new); free(acc); free(z); free(mom); free(gprev); free(acoef);
   return status;
 }

@@ -50,7 +50,8 @@ struct dvm_batch {
   int *d_smap = nullptr, *d_fmap = nullptr;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t g_many = nullptr;  // m sweeps
-  cudaGraphExec_t g_one = nullptr;   // one sweep with timing events
+  cudaGraphExec_t g_sweep = nullptr; // one sweep kernel (timed single sweeps)
+  cudaGraphExec_t g_fin = nullptr;   // the two finalize kernels of that sweep
   int m = 1;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timed = false;
@@ -81,7 +82,7 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
   const double dx = c->P.ly / c->ny;
   vel.assign((size_t)c->ngroups * kNumVelFields * kLanes, T(0));
   inv.assign((size_t)c->ngroups * 9 * kLanes, T(0));
-  const double kap[3] = {1.5, 5.0 / 3.0, 2.0};
+  const double kap[3] = {1.5, 1.0, 2.0};  // interior, second cell from a wall, next to a wall
   for (int g = 0; g < c->ngroups; ++g) {
     const int q = g / gq, gi = g % gq;
     const double s1 = (q & 1) ? -1.0 : 1.0, s2 = (q & 2) ? -1.0 : 1.0;
@@ -103,23 +104,54 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
   }
 }
 
-void velocity_sums(const dvm_ctx *c, InstanceDesc &D) {
+// Quadrature sums of the velocity table exactly as the kernels see it (values rounded to the sweep
+// precision): the moment weights w_i = (W, W v1, W v2, W |v|^2), the basis the right-hand side is
+// built from psi = (1, v1, v2, (|v|^2 - 1) + 1), and the wall-flux weights |v_n| W.  With
+// G_ij = sum_k w_i(v_k) psi_j(v_k) and collision coefficients a = G^{-1} m, the collision operator
+// L = delta psi . a is the projection onto span(psi) that conserves the kernel's own moments exactly
+// (for FP64 tables and an exact quadrature: the delta [rho + 2 u.v + tau (|v|^2 - 1)] of Eq. BGK).
+template <typename T>
+bool table_sums(const dvm_ctx *c, const std::vector<T> &vel, InstanceDesc &D) {
+  double g[4][8] = {};
   for (int k = 0; k < 4; ++k) D.sumW[k] = D.ain[k] = D.nrm[k] = 0.0;
-  const int n = c->nv;
-  for (int a = 0; a < n; ++a) {
-    for (int b = 0; b < n; ++b) {
-      const double v1 = c->x1[a], v2 = c->x1[b], W = c->w1[a] * c->w1[b];
-      D.sumW[0] += W;
-      D.sumW[1] += W * v1;
-      D.sumW[2] += W * v2;
-      D.sumW[3] += W * (v1 * v1 + v2 * v2);
-      const double vn[4] = {v1, -v1, v2, -v2};  // inward normal of a wall on side W, E, S, N
-      for (int s = 0; s < 4; ++s) {
-        if (vn[s] < 0) D.ain[s] += -vn[s] * W;
-        else D.nrm[s] += vn[s] * W;
+  for (int grp = 0; grp < c->ngroups; ++grp) {
+    for (int lane = 0; lane < kLanes; ++lane) {
+      auto f = [&](int field) { return (double)vel[((size_t)grp * kNumVelFields + field) * kLanes + lane]; };
+      const double w[4] = {f(kW0), f(kW1), f(kW2), f(kW3)};
+      if (w[0] == 0.0) continue;  // padded lane
+      const double psi[4] = {1.0, f(kV1), f(kV2), f(kE2m1) + 1.0};
+      for (int i = 0; i < 4; ++i) {
+        D.sumW[i] += w[i];
+        for (int j = 0; j < 4; ++j) g[i][j] += w[i] * psi[j];
       }
+      const double v1 = f(kV1), v2 = f(kV2), wnx = f(kWnx), wny = f(kWny);
+      // side W: inward normal +x, outgoing v1 > 0; E: -x; S: +y; N: -y
+      (v1 > 0 ? D.nrm[kW] : D.ain[kW]) += wnx;
+      (v1 < 0 ? D.nrm[kE] : D.ain[kE]) += wnx;
+      (v2 > 0 ? D.nrm[kS] : D.ain[kS]) += wny;
+      (v2 < 0 ? D.nrm[kN] : D.ain[kN]) += wny;
     }
   }
+  // Gauss-Jordan inverse with partial pivoting
+  for (int i = 0; i < 4; ++i) g[i][4 + i] = 1.0;
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (std::fabs(g[r][col]) > std::fabs(g[piv][col])) piv = r;
+    if (g[piv][col] == 0.0) return false;
+    if (piv != col)
+      for (int j = 0; j < 8; ++j) std::swap(g[piv][j], g[col][j]);
+    const double d = g[col][col];
+    for (int j = 0; j < 8; ++j) g[col][j] /= d;
+    for (int r = 0; r < 4; ++r) {
+      if (r == col) continue;
+      const double fr = g[r][col];
+      for (int j = 0; j < 8; ++j) g[r][j] -= fr * g[col][j];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) D.ginv[i * 4 + j] = g[i][4 + j];
+  return true;
 }
 
 int auto_warps(int nx, int ny) {
@@ -196,19 +228,17 @@ LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const in
   return L;
 }
 
-// Capture `iters` sweeps (sweep + two finalize kernels) of a launch into a graph; with events,
-// record ev[0] before the sweep, ev[1] after it and ev[2] after the finalize kernels (iters = 1).
+// Capture `iters` sweeps of a launch into a graph: each the sweep kernel (when `sweep`) followed by
+// the two finalize kernels (when `fin`).
 dvm_status capture_graph(dvm_ctx *err_ctx, cudaStream_t cap, const LaunchDesc &L, int sweep_blocks, int fin_blocks,
-                         bool fp64, bool store_h, bool uniform, int iters, cudaEvent_t *ev, cudaGraphExec_t *out) {
+                         bool fp64, bool store_h, bool uniform, int iters, bool sweep, bool fin,
+                         cudaGraphExec_t *out) {
   cudaGraph_t graph = nullptr;
   DVM_CUDA(err_ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    if (ev) e = cudaEventRecord(ev[0], cap);
-    if (e == cudaSuccess) e = launch_sweep(fp64, store_h, uniform, L, sweep_blocks, cap);
-    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], cap);
-    if (e == cudaSuccess) e = launch_finalize(L, fin_blocks, fp64, cap);
-    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], cap);
+    if (sweep) e = launch_sweep(fp64, store_h, uniform, L, sweep_blocks, cap);
+    if (e == cudaSuccess && fin) e = launch_finalize(L, fin_blocks, fp64, cap);
   }
   cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -232,7 +262,8 @@ int iters_per_graph(double updates_per_iter) {
 void batch_free(dvm_batch *b) {
   if (!b) return;
   if (b->g_many) cudaGraphExecDestroy(b->g_many);
-  if (b->g_one) cudaGraphExecDestroy(b->g_one);
+  if (b->g_sweep) cudaGraphExecDestroy(b->g_sweep);
+  if (b->g_fin) cudaGraphExecDestroy(b->g_fin);
   for (auto &e : b->ev)
     if (e) cudaEventDestroy(e);
   if (b->d_descs) cudaFree(b->d_descs);
@@ -310,10 +341,13 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
   LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cmax, b->fp64);
   b->m = iters_per_graph(upd);
   dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, b->m,
-                                nullptr, &b->g_many);
+                                true, true, &b->g_many);
   if (st == DVM_OK)
-    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, 1, b->ev,
-                       &b->g_one);
+    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, 1, true, false,
+                       &b->g_sweep);
+  if (st == DVM_OK)
+    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, 1, false, true,
+                       &b->g_fin);
   if (st != DVM_OK) {
     batch_free(b);
     return st;
@@ -391,7 +425,14 @@ dvm_status batch_iterate(dvm_batch *b, int n) {
     DVM_CUDA(c0, cudaGraphLaunch(b->g_many, b->stream));
     left -= b->m;
   }
-  for (; left > 0; --left) DVM_CUDA(c0, cudaGraphLaunch(b->g_one, b->stream));
+  for (; left > 0; --left) {
+    // single sweeps: stream events around the sweep and the finalize kernels time them
+    DVM_CUDA(c0, cudaEventRecord(b->ev[0], b->stream));
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_sweep, b->stream));
+    DVM_CUDA(c0, cudaEventRecord(b->ev[1], b->stream));
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_fin, b->stream));
+    DVM_CUDA(c0, cudaEventRecord(b->ev[2], b->stream));
+  }
   bool all = false;
   st = batch_poll(b, &all);
   if (st != DVM_OK) return st;
@@ -565,18 +606,24 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   CREATE_CUDA(cudaMalloc(&c->d_desc, sizeof(InstanceDesc)));
   CREATE_CUDA(cudaMallocHost(&c->h_state, sizeof(DeviceState)));
 
-  // velocity tables
+  // velocity tables and the quadrature sums of exactly those values
+  InstanceDesc &D = c->hdesc;
+  std::memset(&D, 0, sizeof(D));
+  bool sums_ok;
   if (c->fp64) {
     std::vector<double> vel, inv;
     build_velocity_tables<double>(c, vel, inv);
+    sums_ok = table_sums<double>(c, vel, D);
     CREATE_CUDA(cudaMemcpy(c->d_vel, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice));
     CREATE_CUDA(cudaMemcpy(c->d_inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
   } else {
     std::vector<float> vel, inv;
     build_velocity_tables<float>(c, vel, inv);
+    sums_ok = table_sums<float>(c, vel, D);
     CREATE_CUDA(cudaMemcpy(c->d_vel, vel.data(), vel.size() * sizeof(float), cudaMemcpyHostToDevice));
     CREATE_CUDA(cudaMemcpy(c->d_inv, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
+  if (!sums_ok) return cleanup_fail(DVM_EINVAL, "velocity grid moments are degenerate");
   CREATE_CUDA(cudaMemcpy(c->d_code4, c->geo.code4.data(), sizeof(uint32_t) * 4 * ncell, cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(c->d_hw_src, c->geo.hw_src.data(), sizeof(int) * 8 * ncell, cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemset(c->d_delta_field, 0, sizeof(double) * ncell));
@@ -593,8 +640,6 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   CREATE_CUDA(cudaMemcpy(c->d_sweep_map, smap.data(), sizeof(int) * smap.size(), cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(c->d_fin_map, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice));
 
-  InstanceDesc &D = c->hdesc;
-  std::memset(&D, 0, sizeof(D));
   D.nx = c->nx;
   D.ny = c->ny;
   D.ncell = c->ncell;
@@ -608,7 +653,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   D.dA_over_Lx = D.dx * D.dx / (c->nx * D.dx);
   D.delta = delta;
   D.force = P.force;
-  velocity_sums(c, D);
+  D.fp32 = c->fp64 ? 0 : 1;
   D.vel = c->d_vel;
   D.inv_den = c->d_inv;
   D.rec = c->d_rec;

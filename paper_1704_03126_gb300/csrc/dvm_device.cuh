@@ -17,19 +17,21 @@ constexpr int kMaxWarps = 32;
 // Per-cell code bits for one quadrant (static geometry, see dvm_tables.cpp).
 enum : uint32_t {
   kSolid = 1u,
-  kClsXShift = 1,  // 2 bits: 0 interior stencil, 1 two-point wall stencil, 2 one-point wall stencil
+  kClsXShift = 1,  // 2 bits: 0 interior (second order), 1 second cell from a wall (first order),
+                   //         2 next to a wall (linear through the wall value)
   kClsYShift = 3,
   kIncX = 1u << 5, // the cell owns a wall face on its downstream x side (incident for this quadrant)
   kIncY = 1u << 6,
 };
-enum : int { kFull = 0, kWall3 = 1, kWall1 = 2 };
+enum : int { kFull = 0, kNear = 1, kWall = 2 };
 // sides of a cell: the solid neighbour lies at -x (W), +x (E), -y (S), +y (N)
 enum : int { kW = 0, kE = 1, kS = 2, kN = 3 };
 
 // Sweep record: everything the sweep needs per cell and quadrant, rewritten every iteration by the
-// finalize kernel.  R_k = A + B v1 + C v2 + D (|v|^2 - 1) is the right-hand side of Eq. (iteration)
-// (delta (rho - c) + (2 delta u1 + F) v1 + 2 delta u2 v2 + delta tau (|v|^2 - 1)); hwx / hwy are the
-// wall values used by the x / y upstream stencil; delta the cell's collision rate.
+// finalize kernel.  R_k = A + B v1 + C v2 + D (|v|^2 - 1) is the right-hand side of Eq. (iteration),
+// delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v1 with the collision coefficients a = G^{-1} m
+// (for an exact quadrature: delta (rho - c) + (2 delta u1 + F) v1 + 2 delta u2 v2 + delta tau (|v|^2 - 1));
+// hwx / hwy are the wall values used by the x / y upstream stencil; delta the cell's collision rate.
 template <typename T> struct SweepRec;
 template <> struct alignas(16) SweepRec<float> {
   float A, B, C, D;
@@ -80,11 +82,13 @@ struct InstanceDesc {
   int n_gas;
   int uniform_delta;
   int fin_nblocks;      // blocks of this instance in the finalize grids
+  int fp32;             // 1 = FP32 storage (enables the noise-floor exit of the stopping test)
   double dx;            // cell size
   double dA_over_Lx;    // dx^2 / (nx dx)
   double delta;         // uniform collision rate
   double force;         // F
   double sumW[4];       // sum W, sum W v1, sum W v2, sum W |v|^2
+  double ginv[16];      // inverse Gram matrix of psi = (1, v1, v2, |v|^2) under the weights W
   double ain[4];        // per side: sum_{v.n<0} |v.n| W  (incident weight of a constant)
   double nrm[4];        // per side: sum_{v.n>0} (v.n) W  (outgoing normaliser)
   const void *vel;      // [ngroups][kNumVelFields][32] T

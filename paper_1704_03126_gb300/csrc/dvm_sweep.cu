@@ -5,9 +5,9 @@
 //     (delta + sum_a |v_a|/dx kappa_a) h = R + sum_a |v_a|/dx combo_a,
 //     R = delta (rho + 2 u.v + tau (|v|^2 - 1) - c) + F v1                    (Eq. BGK)
 // where along each axis (s = sign v_a, u1 = cell - s, u2 = cell - 2 s)
-//     interior            kappa = 3/2, combo = 2 h(u1) - h(u2)/2
-//     u2 solid            kappa = 5/3, combo = 3 h(u1) - 4/3 h_w(face of u1)
-//     u1 solid            kappa = 2,   combo = 2 h_w(own face)
+//     interior            kappa = 3/2, combo = 2 h(u1) - h(u2)/2   (second order)
+//     u2 solid            kappa = 1,   combo = h(u1)               (first order)
+//     u1 solid            kappa = 2,   combo = 2 h_w(own face)     (linear through the wall value)
 // h_w is the diffuse wall value (Eq. diffuse2) of the previous iterate, and upstream cells across a
 // periodic seam also take the previous iterate (lagged).
 //
@@ -56,7 +56,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 template <typename T>
 __device__ __forceinline__ T kappa_of(int cls) {
-  return cls == kFull ? T(1.5) : (cls == kWall3 ? T(5.0 / 3.0) : T(2.0));
+  return cls == kFull ? T(1.5) : (cls == kNear ? T(1.0) : T(2.0));
 }
 
 template <typename T>
@@ -199,10 +199,8 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes, 1) sweep_kernel(LaunchDesc
         }
         const T Rk = fma(r.D, em1, fma(r.C, v2, fma(r.B, v1, r.A)));
         const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
-        const T bx = clx == kFull ? fma(T(2), hp1, T(-0.5) * hp2)
-                                  : (clx == kWall3 ? fma(T(3), hp1, T(-4.0 / 3.0) * r.hwx) : T(2) * r.hwx);
-        const T by = cly == kFull ? fma(T(2), hq1, T(-0.5) * hq2)
-                                  : (cly == kWall3 ? fma(T(3), hq1, T(-4.0 / 3.0) * r.hwy) : T(2) * r.hwy);
+        const T bx = clx == kFull ? fma(T(2), hp1, T(-0.5) * hp2) : (clx == kNear ? hp1 : T(2) * r.hwx);
+        const T by = cly == kFull ? fma(T(2), hq1, T(-0.5) * hq2) : (cly == kNear ? hq1 : T(2) * r.hwy);
         T inv;
         if (UNIF) {
           inv = invt[(clx * 3 + cly) * kLanes + lane];

@@ -148,11 +148,10 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
           const int side = sx > 0 ? kW : kE;
           int cls = kFull, src = -1;
           if (solid(i - sx, j)) {
-            cls = kWall1;
+            cls = kWall;
             src = cell * 4 + side;
           } else if (solid(i - 2 * sx, j)) {
-            cls = kWall3;
-            src = id(i - sx, j) * 4 + side;
+            cls = kNear;  // first order through the gas neighbour: no wall value
           }
           code |= (uint32_t)cls << kClsXShift;
           G.hw_src[(size_t)cell * 8 + q * 2 + 0] = src;
@@ -162,11 +161,10 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
           const int side = sy > 0 ? kS : kN;
           int cls = kFull, src = -1;
           if (solid(i, j - sy)) {
-            cls = kWall1;
+            cls = kWall;
             src = cell * 4 + side;
           } else if (solid(i, j - 2 * sy)) {
-            cls = kWall3;
-            src = id(i, j - sy) * 4 + side;
+            cls = kNear;
           }
           code |= (uint32_t)cls << kClsYShift;
           G.hw_src[(size_t)cell * 8 + q * 2 + 1] = src;
