@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--skip-extras", action="store_true", help="only the timed steps (profiling runs)")
+    ap.add_argument("--single", action="store_true", help="time only the selected precision")
+    ap.add_argument("--min-warmup-s", type=float, default=1.0,
+                    help="keep warming up for at least this long (clock sampling); 0 for profiling")
     return ap.parse_args()
 
 
@@ -132,7 +135,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def timed_steps(batch, steps, warmup, sampler=None):
-        t_end = time.perf_counter() + 1.0
+        t_end = time.perf_counter() + args.min_warmup_s
         w = 0
         while w < warmup or time.perf_counter() < t_end:  # at least `warmup` steps and ~1 s of load
             batch.iterate(1)
@@ -162,7 +165,8 @@ def run_ours(args, rank, world, local_rank):
     results = {}
     sampler = ClockSampler(local_rank)
     sampler.start()
-    for precision in (args.precision, "fp64" if args.precision == "fp32" else "fp32"):
+    precisions = [args.precision] + ([] if args.single else ["fp64" if args.precision == "fp32" else "fp32"])
+    for precision in precisions:
         solvers = make(precision)
         batch = dvm.Batch(solvers)
         total_ms, sweep_ms, fin_ms, wsteps = timed_steps(batch, args.steps, args.warmup)
@@ -208,13 +212,14 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps * (main["kernels_per_step"] + len(KNS)),
     }
     other = "fp64" if args.precision == "fp32" else "fp32"
-    out[other] = {"value": world * args.steps * upd / (results[other]["total_ms"] / 1e3),
-                  "ms_per_step": results[other]["total_ms"] / args.steps, "roofline": roofline(other)}
+    if other in results:
+        out[other] = {"value": world * args.steps * upd / (results[other]["total_ms"] / 1e3),
+                      "ms_per_step": results[other]["total_ms"] / args.steps, "roofline": roofline(other)}
+    hbm = float(peaks.get("hbm_gbs", 6762.6)) * 1e9
+    vals = {p: world * args.steps * upd / (results[p]["total_ms"] / 1e3) for p in results}
     out["effective_hbm_fraction"] = {
         "note": "updates/s x bytes a non-fused sweep would move (write + read h) / measured HBM copy bandwidth",
-        "fp32": value * 8 / (float(peaks.get("hbm_gbs", 6762.6)) * 1e9),
-        "fp64": out[other]["value"] * 16 / (float(peaks.get("hbm_gbs", 6762.6)) * 1e9)
-        if other == "fp64" else None,
+        **{p: vals[p] * (8 if p == "fp32" else 16) / hbm for p in vals},
     }
 
     if not args.skip_extras:

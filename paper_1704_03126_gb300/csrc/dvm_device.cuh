@@ -64,7 +64,7 @@ struct DeviceState {
   int status;      // dvm_status of the solve so far
   int max_iter;    // stop with DVM_ENOCONV when iter reaches it
   int nan_flag;
-  int pad0;
+  int iter_min;    // sweep of the smallest eps so far (FP32 stall test)
   unsigned int ticket1, ticket2;  // last-block counters of the two finalize kernels
   double tol;
   double c;        // accumulated mass shift (bordering unknown)
@@ -72,6 +72,7 @@ struct DeviceState {
   double s_new;    // shift of the current iteration
   double eps, est, Q;
   double eps_ring[4];
+  double eps_min;  // smallest eps so far
   double mass_acc, du_acc, u_acc, q_acc;
 };
 

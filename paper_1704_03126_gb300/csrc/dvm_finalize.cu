@@ -167,12 +167,20 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
         double r = back > 0.0 ? pow(eps / back, 0.25) : 0.0;
         if (r > 0.9999) r = 0.9999;
         est = eps / (1.0 - r);
-        // with FP32 storage the change per sweep stalls at the rounding noise floor, where the
-        // rate estimate r -> 1 says nothing: a change below tol / 8 also ends the iteration
-        if (est < st->tol || (D->fp32 && eps < 0.125 * st->tol)) {
+        if (est < st->tol) {
           done = 1;
           status = 0;
         }
+      }
+      // With FP32 storage the change per sweep stalls at the rounding noise floor, where the rate
+      // estimate says nothing: below tol, 16 sweeps without a new smallest eps also end the iteration.
+      if (eps < st->eps_min) {
+        st->eps_min = eps;
+        st->iter_min = n;
+      }
+      if (!done && D->fp32 && n >= 5 && eps < st->tol && n - st->iter_min >= 16) {
+        done = 1;
+        status = 0;
       }
       if (!done && n >= st->max_iter) {
         done = 1;
@@ -223,12 +231,16 @@ __global__ void reset_kernel(const InstanceDesc *D) {
     st->c = st->s = st->s_new = 0.0;
     st->eps = st->est = st->Q = 0.0;
     for (int k = 0; k < 4; ++k) st->eps_ring[k] = 0.0;
+    st->eps_min = INFINITY;
+    st->iter_min = 0;
     st->mass_acc = st->du_acc = st->u_acc = st->q_acc = 0.0;
   }
 }
 
 __global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
   st->tol = tol;
+  st->eps_min = INFINITY;
+  st->iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;

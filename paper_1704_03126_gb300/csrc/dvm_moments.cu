@@ -1,0 +1,118 @@
+// dvm_moments.cu -- moments and mass flow rate of a distribution held by the caller.
+//
+// rho = sum_k W_k h_k, u_i = sum_k W_k v_i h_k, tau = sum_k W_k |v_k|^2 h_k - rho (the quadrature
+// forms of the moments of Sec. II.A) at every cell, and Q = sum_gas u1 dA / L (Sec. III, Eq. Q).
+// One thread per cell walks the velocities (coalesced over cells for the [K][ncell] layout);
+// block partial sums of Q go to scratch memory and the last block adds them in block order, so Q
+// is deterministic.
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dvm.h"
+#include "dvm_tables.h"
+
+namespace dvm {
+namespace {
+
+constexpr int kMomBlock = 256;
+constexpr int kMomMaxBlocks = 1024;
+
+struct VelTable {
+  int n;
+  double x[64];
+  double w[64];
+};
+
+__global__ void __launch_bounds__(kMomBlock) moments_kernel(const double *__restrict__ h, const uint8_t *__restrict__ mask,
+                                                            int ncell, VelTable vt, double dA_over_L,
+                                                            double *__restrict__ mom, double *__restrict__ Q,
+                                                            double *partials, unsigned int *ticket) {
+  __shared__ double sh[kMomBlock / 32];
+  const int n = vt.n;
+  double q_local = 0.0;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncell; cell += gridDim.x * blockDim.x) {
+    const bool gas = !mask || !mask[cell];
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+    if (gas) {
+      for (int a = 0; a < n; ++a) {
+        const double v1 = vt.x[a], wa = vt.w[a];
+        for (int b = 0; b < n; ++b) {
+          const double v2 = vt.x[b];
+          const double wh = wa * vt.w[b] * h[(size_t)(a * n + b) * ncell + cell];
+          m0 += wh;
+          m1 += wh * v1;
+          m2 += wh * v2;
+          m3 += wh * (v1 * v1 + v2 * v2);
+        }
+      }
+      q_local += m1;
+    }
+    mom[(size_t)cell * 4 + 0] = m0;
+    mom[(size_t)cell * 4 + 1] = m1;
+    mom[(size_t)cell * 4 + 2] = m2;
+    mom[(size_t)cell * 4 + 3] = m3 - m0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q_local += __shfl_xor_sync(0xffffffffu, q_local, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = q_local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int wi = 0; wi < kMomBlock / 32; ++wi) s += sh[wi];
+    partials[blockIdx.x] = s;
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    if (t == gridDim.x - 1) {
+      __threadfence();
+      double total = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) total += *((volatile double *)&partials[b]);
+      *Q = total * dA_over_L;
+      *ticket = 0u;
+    }
+  }
+}
+
+// Validate arguments and build the velocity table; returns DVM_OK or the failure.
+dvm_status prepare(const dvm_quad *q, const double *h, int ncell, double *mom, double *Q, VelTable &vt,
+                   int &blocks) {
+  if (!q || !h || !mom || !Q || ncell < 1) return DVM_EINVAL;
+  std::vector<double> x, w;
+  std::string err;
+  if (!quadrature_1d(q->kind, q->n, q->vmax, x, w, err)) return DVM_EINVAL;
+  vt.n = q->n;
+  for (int a = 0; a < q->n; ++a) {
+    vt.x[a] = x[a];
+    vt.w[a] = w[a];
+  }
+  const long long want = ((long long)ncell + kMomBlock - 1) / kMomBlock;
+  blocks = (int)(want < kMomMaxBlocks ? want : kMomMaxBlocks);
+  return DVM_OK;
+}
+
+}  // namespace
+}  // namespace dvm
+
+extern "C" dvm_status dvm_moments(const dvm_quad *q, const double *h, const uint8_t *mask, int ncell,
+                                  double dA_over_L, double *mom, double *Q, void *stream) {
+  using namespace dvm;
+  VelTable vt;
+  int blocks = 0;
+  dvm_status st = prepare(q, h, ncell, mom, Q, vt, blocks);
+  if (st != DVM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void *scratch = nullptr;  // block partials, then the last-block ticket
+  const size_t bytes = sizeof(double) * kMomMaxBlocks + 256;
+  if (cudaMalloc(&scratch, bytes) != cudaSuccess) return DVM_ENOMEM;
+  double *partials = static_cast<double *>(scratch);
+  unsigned int *ticket = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + sizeof(double) * kMomMaxBlocks);
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) {
+    moments_kernel<<<blocks, kMomBlock, 0, s>>>(h, mask, ncell, vt, dA_over_L, mom, Q, partials, ticket);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  return e == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
