@@ -180,6 +180,24 @@ dvm_status dvm_batch_solve(dvm_ctx *const *ctxs, int n, double tol, int max_iter
 dvm_status dvm_moments(const dvm_quad *q, const double *h, const uint8_t *mask, int ncell, double dA_over_L,
                        double *mom, double *Q, void *stream);
 
+/* dvm_moments without any device allocation, for callers that cannot allocate during a call:
+ * cudaMalloc and cudaFree synchronise the whole device and can fail under memory pressure, so a
+ * caller inside a latency-critical loop, a caller whose device memory is all reserved by its own
+ * allocator at start-up, or a caller that must not touch the allocator while other streams run cannot
+ * use dvm_moments.  The paper has no counterpart: this is a deployment variant of the reduction above.
+ * Arguments and results are those of dvm_moments.  Differences:
+ *   - scratch is a fixed device array of about 8.3 KB inside the library, present on every device
+ *     that loads it until the process exits; ncell may be at most 16,777,216 (DVM_EINVAL beyond,
+ *     message in dvm_last_error(NULL));
+ *   - the call is asynchronous on `stream` (results are ready when the stream reaches them);
+ *   - every call shares the array: calls that overlap on one device (for example on two streams)
+ *     race and must be serialised by the caller;
+ *   - the first call on a device looks up the array's address with that device current; make that
+ *     first call before any stream capture.
+ * Errors are reported through dvm_last_error(NULL). */
+dvm_status dvm_moments_noalloc(const dvm_quad *q, const double *h, const uint8_t *mask, int ncell,
+                               double dA_over_L, double *mom, double *Q, void *stream);
+
 /* Description of the last error on ctx (or of the last dvm_create failure when ctx is NULL). */
 const char *dvm_last_error(const dvm_ctx *ctx);
 

@@ -14,6 +14,14 @@
 
 using namespace dvm;
 
+namespace dvm {
+namespace {
+std::string g_create_error;
+}  // namespace
+// Errors of context-free calls (dvm_create failures, dvm_moments_noalloc) are read with dvm_last_error(NULL).
+void set_moments_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace dvm
+
 struct dvm_ctx {
   dvm_params P{};
   int nx = 0, ny = 0, ncell = 0, nv = 0, half = 0, gq = 0, ngroups = 0;
@@ -58,8 +66,6 @@ struct dvm_batch {
 };
 
 namespace {
-
-std::string g_create_error;
 
 dvm_status fail(dvm_ctx *ctx, dvm_status st, const std::string &msg) {
   if (ctx) ctx->err = msg;

@@ -7,6 +7,7 @@
 // is deterministic.
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -14,6 +15,10 @@
 #include "dvm_tables.h"
 
 namespace dvm {
+
+// Records the message that dvm_last_error(NULL) returns (defined with the other C ABI calls).
+void set_moments_error(const std::string &msg);
+
 namespace {
 
 constexpr int kMomBlock = 256;
@@ -115,4 +120,85 @@ extern "C" dvm_status dvm_moments(const dvm_quad *q, const double *h, const uint
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(scratch);
   return e == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+// ------------------------------------------------------------------------------------------------
+// dvm_moments_noalloc: the same reduction with its scratch in a fixed device array, for callers that
+// cannot allocate device memory during a call.  cudaMalloc / cudaFree synchronise the whole device
+// and can fail under memory pressure; a caller in a latency-critical loop, a caller whose device
+// memory is all reserved by a framework allocator at start-up, or a caller that may not touch the
+// allocator while other streams run therefore cannot use dvm_moments, which allocates per call.
+//
+// The scratch below (block partial sums of Q and the last-block ticket, about 8.3 KB) lives in every
+// device that loads this library until the process exits.  Every call shares it and it keeps the
+// last call's contents; the ticket, which must start at zero, is cleared at the start of each call.
+// Calls on one device that overlap on the GPU (for example on two streams) race on the same array and
+// must be serialised by the caller.  The first call on a device looks up the array's device address
+// (cudaGetSymbolAddress, with that device current); make that first call before any stream capture.
+namespace dvm {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = sizeof(double) * kMomMaxBlocks + 256;
+constexpr long long kNoAllocMaxCells = (long long)kMomMaxBlocks * kMomBlock * 64;  // 16,777,216 cells
+
+__device__ __align__(256) unsigned char g_moments_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_moments_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace dvm
+
+extern "C" dvm_status dvm_moments_noalloc(const dvm_quad *q, const double *h, const uint8_t *mask, int ncell,
+                                          double dA_over_L, double *mom, double *Q, void *stream) {
+  using namespace dvm;
+  if ((long long)ncell > kNoAllocMaxCells) {
+    set_moments_error("dvm_moments_noalloc: ncell = " + std::to_string(ncell) + " exceeds the maximum of " +
+                      std::to_string(kNoAllocMaxCells) + " cells of the fixed scratch; use dvm_moments");
+    return DVM_EINVAL;
+  }
+  VelTable vt;
+  int blocks = 0;
+  dvm_status st = prepare(q, h, ncell, mom, Q, vt, blocks);
+  if (st != DVM_OK) {
+    set_moments_error("dvm_moments_noalloc: invalid argument");
+    return st;
+  }
+  void *scratch = nullptr;
+  cudaError_t e = scratch_address(&scratch);
+  if (e != cudaSuccess) {
+    set_moments_error(std::string("dvm_moments_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    return DVM_ECUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *partials = static_cast<double *>(scratch);
+  unsigned int *ticket = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + sizeof(double) * kMomMaxBlocks);
+  e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) {
+    moments_kernel<<<blocks, kMomBlock, 0, s>>>(h, mask, ncell, vt, dA_over_L, mom, Q, partials, ticket);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    set_moments_error(std::string("dvm_moments_noalloc: ") + cudaGetErrorString(e));
+    return DVM_ECUDA;
+  }
+  return DVM_OK;
 }

@@ -81,6 +81,7 @@ def lib():
         L.dvm_batch_kernels_per_sweep.restype = I
         L.dvm_batch_destroy.argtypes = [P]
         L.dvm_moments.argtypes = [ctypes.POINTER(Quad), P, P, I, D, P, P, P]
+        L.dvm_moments_noalloc.argtypes = [ctypes.POINTER(Quad), P, P, I, D, P, P, P]
         L.dvm_last_error.argtypes = [P]
         L.dvm_last_error.restype = ctypes.c_char_p
         L.dvm_status_string.argtypes = [I]
@@ -89,7 +90,8 @@ def lib():
         for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
-                     "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments"):
+                     "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
+                     "dvm_moments_noalloc"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -279,15 +281,15 @@ def velocity_grid(kind: str, n: int, vmax: float = 5.0):
     return x, w
 
 
-def moments(h_ptr, ncell, quad, mom_ptr, q_ptr, dA_over_L, mask_ptr=None, stream=None):
-    """dvm_moments on device pointers (ints, e.g. torch tensor data_ptr()): h [n*n][ncell] FP64 ->
-    mom [ncell][4], Q [1]."""
+def moments(h_ptr, ncell, quad, mom_ptr, q_ptr, dA_over_L, mask_ptr=None, stream=None, noalloc=False):
+    """dvm_moments (or dvm_moments_noalloc) on device pointers (ints, e.g. torch data_ptr()):
+    h [n*n][ncell] FP64 -> mom [ncell][4], Q [1]."""
     q = Quad(QUAD_KINDS[quad[0]], int(quad[1]), float(quad[2]) if len(quad) > 2 else 5.0)
-    st = lib().dvm_moments(ctypes.byref(q), ctypes.c_void_p(h_ptr), ctypes.c_void_p(mask_ptr or 0), int(ncell),
-                           float(dA_over_L), ctypes.c_void_p(mom_ptr), ctypes.c_void_p(q_ptr),
-                           ctypes.c_void_p(stream or 0))
+    fn = lib().dvm_moments_noalloc if noalloc else lib().dvm_moments
+    st = fn(ctypes.byref(q), ctypes.c_void_p(h_ptr), ctypes.c_void_p(mask_ptr or 0), int(ncell),
+            float(dA_over_L), ctypes.c_void_p(mom_ptr), ctypes.c_void_p(q_ptr), ctypes.c_void_p(stream or 0))
     if st != DVM_OK:
-        raise DvmError(st, "dvm_moments failed")
+        raise DvmError(st, lib().dvm_last_error(None).decode() or "dvm_moments failed")
 
 
 def kn_to_delta(kn: float) -> float:
