@@ -74,7 +74,9 @@ typedef struct {
   int precision;              /* dvm_precision */
   double force;               /* body-force source coefficient F along x1 (1 for the paper's Poiseuille flow) */
   int store_distribution;     /* 1 = also keep h in device memory (needed by dvm_distribution) */
-  int sweep_warps;            /* warps per sweep block, 1..32; 0 = choose automatically */
+  int sweep_warps;            /* upper bound on rows in flight (warps) per sweep block, 1..16;
+                                 0 = 16.  The chunk width is the smallest of 1, 2, 4, 8, 16 cells
+                                 with ceil(nx / width) rows within the bound; nx <= 256. */
 } dvm_params;
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,

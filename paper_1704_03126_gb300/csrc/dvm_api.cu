@@ -43,7 +43,7 @@ struct dvm_ctx {
   InstanceDesc hdesc{};
   InstanceDesc *d_desc = nullptr;
   int *d_sweep_map = nullptr, *d_fin_map = nullptr;
-  int warps = 0, cmax = 0;
+  int cw = 0;                      // sweep chunk width preferred by this context
   dvm_batch *self = nullptr;       // batch of this context alone (built on first use)
   DeviceState *h_state = nullptr;  // pinned
   std::string err;
@@ -53,7 +53,7 @@ struct dvm_ctx {
 struct dvm_batch {
   std::vector<dvm_ctx *> ctxs;
   bool fp64 = true, store_h = false, uniform = true;
-  int warps = 0, cmax = 0, nsweep = 0, nfin = 0;
+  int warps = 0, cw = 0, nsweep = 0, nfin = 0;
   InstanceDesc *d_descs = nullptr;
   int *d_smap = nullptr, *d_fmap = nullptr;
   cudaStream_t stream = nullptr;
@@ -87,7 +87,7 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
   const int half = c->half, gq = c->gq;
   const double dx = c->P.ly / c->ny;
   vel.assign((size_t)c->ngroups * kNumVelFields * kLanes, T(0));
-  inv.assign((size_t)c->ngroups * 9 * kLanes, T(0));
+  inv.assign((size_t)c->ngroups * kInvRows * kLanes, T(0));  // row 9 stays 0 (solid cells)
   const double kap[3] = {1.5, 1.0, 2.0};  // interior, second cell from a wall, next to a wall
   for (int g = 0; g < c->ngroups; ++g) {
     const int q = g / gq, gi = g % gq;
@@ -105,7 +105,7 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
       for (int k = 0; k < kNumVelFields; ++k) vel[((size_t)g * kNumVelFields + k) * kLanes + lane] = (T)f[k];
       for (int clx = 0; clx < 3; ++clx)
         for (int cly = 0; cly < 3; ++cly)
-          inv[((size_t)g * 9 + clx * 3 + cly) * kLanes + lane] = (T)(1.0 / (c->delta + cx * kap[clx] + cy * kap[cly]));
+          inv[((size_t)g * kInvRows + clx * 3 + cly) * kLanes + lane] = (T)(1.0 / (c->delta + cx * kap[clx] + cy * kap[cly]));
     }
   }
 }
@@ -160,11 +160,12 @@ bool table_sums(const dvm_ctx *c, const std::vector<T> &vel, InstanceDesc &D) {
   return true;
 }
 
-int auto_warps(int nx, int ny) {
-  int R = 16;
-  R = std::min(R, std::max(1, nx));
-  R = std::min(R, std::max(1, ny));
-  return R;
+// Sweep chunk width: the smallest of 1, 2, 4, 8, 16 cells that keeps ceil(nx / cw) rows in flight
+// within max_warps (each row in flight is one warp).
+int choose_cw(int nx, int max_warps) {
+  for (int cw : {1, 2, 4, 8, 16})
+    if ((nx + cw - 1) / cw <= max_warps) return cw;
+  return 16;
 }
 
 template <typename T>
@@ -222,28 +223,26 @@ dvm_status upload_desc(dvm_ctx *c) {
 }
 
 LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const int *fin_map, int ninst, int warps,
-                       int cmax, bool fp64) {
+                       int cw) {
   LaunchDesc L;
   L.inst = insts;
   L.sweep_map = sweep_map;
   L.fin_map = fin_map;
   L.ninst = ninst;
   L.warps = warps;
-  L.cmax = cmax;
-  L.stage_seams = fp64 ? 0 : 1;
+  L.cw = cw;
   return L;
 }
 
 // Capture `iters` sweeps of a launch into a graph: each the sweep kernel (when `sweep`) followed by
 // the two finalize kernels (when `fin`).
 dvm_status capture_graph(dvm_ctx *err_ctx, cudaStream_t cap, const LaunchDesc &L, int sweep_blocks, int fin_blocks,
-                         bool fp64, bool store_h, bool uniform, int iters, bool sweep, bool fin,
-                         cudaGraphExec_t *out) {
+                         bool fp64, bool uniform, int iters, bool sweep, bool fin, cudaGraphExec_t *out) {
   cudaGraph_t graph = nullptr;
   DVM_CUDA(err_ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    if (sweep) e = launch_sweep(fp64, store_h, uniform, L, sweep_blocks, cap);
+    if (sweep) e = launch_sweep(fp64, uniform, L, sweep_blocks, cap);
     if (e == cudaSuccess && fin) e = launch_finalize(L, fin_blocks, fp64, cap);
   }
   cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
@@ -297,18 +296,20 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
   b->fp64 = c0->fp64;
   b->store_h = c0->store_h;
   b->stream = c0->stream;
-  b->warps = kMaxWarps;
+  // one chunk width for the launch: the widest preferred by a member keeps every member within
+  // kMaxSweepWarps rows in flight; the block has as many warps as the widest member needs
+  b->cw = 1;
   for (int i = 0; i < n; ++i) {
-    b->warps = std::min(b->warps, ctxs[i]->warps);
+    b->cw = std::max(b->cw, ctxs[i]->cw);
     b->uniform = b->uniform && ctxs[i]->uniform;
   }
-  b->cmax = 1;
+  b->warps = 1;
   std::vector<InstanceDesc> descs(n);
   std::vector<int> smap, fmap;
   std::vector<double> work(n);
   double upd = 0.0;
   for (int i = 0; i < n; ++i) {
-    b->cmax = std::max(b->cmax, (ctxs[i]->nx + b->warps - 1) / b->warps);
+    b->warps = std::max(b->warps, (ctxs[i]->nx + b->cw - 1) / b->cw);
     descs[i] = ctxs[i]->hdesc;
     descs[i].uniform_delta = ctxs[i]->uniform ? 1 : 0;
     descs[i].delta_field = ctxs[i]->d_delta_field;
@@ -323,7 +324,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
   b->nfin = (int)fmap.size();
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c0->device);
-  if (sweep_smem_bytes(b->fp64, b->warps, b->cmax) > (size_t)smem_optin) {
+  if (b->warps > kMaxSweepWarps || sweep_smem_bytes(b->fp64, b->warps, b->cw) > (size_t)smem_optin) {
     batch_free(b);
     return fail(c0, DVM_EINVAL, "batched grids too wide for the sweep's shared memory");
   }
@@ -344,16 +345,14 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
   BATCH_CUDA(cudaStreamSynchronize(b->stream));
   for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
 #undef BATCH_CUDA
-  LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cmax, b->fp64);
+  LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw);
   b->m = iters_per_graph(upd);
-  dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, b->m,
-                                true, true, &b->g_many);
+  dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->uniform, b->m, true, true,
+                                &b->g_many);
   if (st == DVM_OK)
-    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, 1, true, false,
-                       &b->g_sweep);
+    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->uniform, 1, true, false, &b->g_sweep);
   if (st == DVM_OK)
-    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->store_h, b->uniform, 1, false, true,
-                       &b->g_fin);
+    st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->uniform, 1, false, true, &b->g_fin);
   if (st != DVM_OK) {
     batch_free(b);
     return st;
@@ -542,9 +541,14 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
     delete c;
     return fail(nullptr, DVM_EINVAL, "the mask has no gas cell");
   }
-  c->warps = P.sweep_warps > 0 ? P.sweep_warps : auto_warps(c->nx, c->ny);
-  c->cmax = (c->nx + c->warps - 1) / c->warps;
-  const size_t smem = sweep_smem_bytes(c->fp64, c->warps, c->cmax);
+  const int max_warps = P.sweep_warps > 0 ? std::min(P.sweep_warps, kMaxSweepWarps) : kMaxSweepWarps;
+  c->cw = choose_cw(c->nx, max_warps);
+  const int rows_in_flight = (c->nx + c->cw - 1) / c->cw;
+  if (rows_in_flight > kMaxSweepWarps) {
+    delete c;
+    return fail(nullptr, DVM_EINVAL, "grid too wide: nx must be at most 256 for the sweep's rows in flight");
+  }
+  const size_t smem = sweep_smem_bytes(c->fp64, rows_in_flight, c->cw);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -596,7 +600,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   const size_t recsz = c->fp64 ? sizeof(SweepRec<double>) : sizeof(SweepRec<float>);
   const size_t ncell = (size_t)c->ncell;
   CREATE_CUDA(cudaMalloc(&c->d_vel, ts * c->ngroups * kNumVelFields * kLanes));
-  CREATE_CUDA(cudaMalloc(&c->d_inv, ts * c->ngroups * 9 * kLanes));
+  CREATE_CUDA(cudaMalloc(&c->d_inv, ts * c->ngroups * kInvRows * kLanes));
   CREATE_CUDA(cudaMalloc(&c->d_rec, recsz * 4 * ncell));
   CREATE_CUDA(cudaMalloc(&c->d_code4, sizeof(uint32_t) * 4 * ncell));
   CREATE_CUDA(cudaMalloc(&c->d_hw_src, sizeof(int) * 8 * ncell));

@@ -13,6 +13,7 @@ namespace dvm {
 constexpr int kLanes = 32;       // velocities per group = warp width
 constexpr int kRingPad = 33;     // padded row stride (elements) of the shared-memory ring buffer
 constexpr int kMaxWarps = 32;
+constexpr int kMaxSweepWarps = 16;  // rows in flight per sweep block (512 threads, up to 128 registers)
 
 // Per-cell code bits for one quadrant (static geometry, see dvm_tables.cpp).
 enum : uint32_t {
@@ -22,32 +23,42 @@ enum : uint32_t {
   kClsYShift = 3,
   kIncX = 1u << 5, // the cell owns a wall face on its downstream x side (incident for this quadrant)
   kIncY = 1u << 6,
+  kInvShift = 8,   // 4 bits: row of the 1/denominator table, clx * 3 + cly, or 9 (solid: 0)
 };
 enum : int { kFull = 0, kNear = 1, kWall = 2 };
 // sides of a cell: the solid neighbour lies at -x (W), +x (E), -y (S), +y (N)
 enum : int { kW = 0, kE = 1, kS = 2, kN = 3 };
+constexpr int kInvRows = 10;
 
 // Sweep record: everything the sweep needs per cell and quadrant, rewritten every iteration by the
 // finalize kernel.  R_k = A + B v1 + C v2 + D (|v|^2 - 1) is the right-hand side of Eq. (iteration),
 // delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v1 with the collision coefficients a = G^{-1} m
-// (for an exact quadrature: delta (rho - c) + (2 delta u1 + F) v1 + 2 delta u2 v2 + delta tau (|v|^2 - 1));
-// hwx / hwy are the wall values used by the x / y upstream stencil; delta the cell's collision rate.
+// (for an exact quadrature: delta (rho - c) + (2 delta u1 + F) v1 + 2 delta u2 v2 + delta tau (|v|^2 - 1)).
+// The upwind combination along x is ax1 h(u1) + ax2 h(u2) + xw, with (ax1, ax2, xw) = (2, -1/2, 0)
+// inside, (1, 0, 0) at the second cell from a wall and (0, 0, 2 h_w) next to a wall; y likewise.
+// Solid cells carry all-zero coefficients (and the zero row of the 1/denominator table), so the
+// sweep computes h = 0 there without a branch.
 template <typename T> struct SweepRec;
 template <> struct alignas(16) SweepRec<float> {
   float A, B, C, D;
-  float hwx, hwy;
+  float ax1, ax2, xw, ay1;
+  float ay2, yw;
   uint32_t code;
   float delta;
 };
 template <> struct alignas(16) SweepRec<double> {
   double A, B, C, D;
-  double hwx, hwy;
-  uint32_t code;
+  double xw, yw;
+  uint32_t code;   // the FP64 record derives (ax1, ax2, ay1, ay2) from the class bits
   uint32_t pad;
   double delta;
 };
-static_assert(sizeof(SweepRec<float>) == 32, "record layout");
+static_assert(sizeof(SweepRec<float>) == 48, "record layout");
 static_assert(sizeof(SweepRec<double>) == 64, "record layout");
+
+// Upwind coefficients (a1, a2) of a stencil class: interior (2, -1/2), second cell (1, 0), wall (0, 0).
+__host__ __device__ inline float class_a1(int cls) { return cls == kFull ? 2.0f : (cls == kNear ? 1.0f : 0.0f); }
+__host__ __device__ inline float class_a2(int cls) { return cls == kFull ? -0.5f : 0.0f; }
 
 // Per-lane velocity table fields ([group][field][lane], in the sweep precision).
 enum : int {
@@ -65,6 +76,8 @@ struct DeviceState {
   int max_iter;    // stop with DVM_ENOCONV when iter reaches it
   int nan_flag;
   int iter_min;    // sweep of the smallest eps so far (FP32 stall test)
+  int err_flag;    // a bounded device-side wait gave up (reported as DVM_ETIMEOUT)
+  int pad0;
   unsigned int ticket1, ticket2;  // last-block counters of the two finalize kernels
   double tol;
   double c;        // accumulated mass shift (bordering unknown)
@@ -93,7 +106,7 @@ struct InstanceDesc {
   double ain[4];        // per side: sum_{v.n<0} |v.n| W  (incident weight of a constant)
   double nrm[4];        // per side: sum_{v.n>0} (v.n) W  (outgoing normaliser)
   const void *vel;      // [ngroups][kNumVelFields][32] T
-  const void *inv_den;  // [ngroups][9][32] T: 1 / (delta + cx kx + cy ky), uniform delta only
+  const void *inv_den;  // [ngroups][kInvRows][32] T: 1 / (delta + cx kx + cy ky), uniform delta only; row 9 = 0
   void *rec;            // [4][ncell] SweepRec<T>
   const uint32_t *code4;   // [ncell][4]
   const int *hw_src;       // [ncell][8]: (quadrant, axis) -> owner cell * 4 + side, or -1
@@ -114,9 +127,8 @@ struct LaunchDesc {
   const int *sweep_map;      // [sweep blocks]: instance << 16 | group
   const int *fin_map;        // [finalize blocks]: instance << 16 | block within instance
   int ninst;
-  int warps;                 // sweep warps per block (R)
-  int cmax;                  // max over instances of ceil(nx / R)
-  int stage_seams;           // shared-memory staging of periodic-y seam rows (FP32 path)
+  int warps;                 // sweep warps per block: max over instances of ceil(nx / cw)
+  int cw;                    // chunk width (cells per warp and step) of the sweep: 1, 2, 4, 8 or 16
 };
 
 }  // namespace dvm

@@ -64,18 +64,46 @@ __global__ void __launch_bounds__(kFinBlock) fin1_kernel(LaunchDesc L) {
   }
 }
 
+// Write the sweep record of one cell and quadrant: right-hand-side coefficients, the upwind
+// coefficients of the cell's stencil classes and the wall terms 2 h_w of wall-class axes.
 template <typename T>
 __device__ __forceinline__ void store_rec(SweepRec<T> *dst, double A, double B, double C, double Dd, double hwx,
-                                          double hwy, uint32_t code, double delta) {
-  SweepRec<T> r;
-  r.A = (T)A;
-  r.B = (T)B;
-  r.C = (T)C;
-  r.D = (T)Dd;
-  r.hwx = (T)hwx;
-  r.hwy = (T)hwy;
+                                          double hwy, uint32_t code, double delta);
+template <>
+__device__ __forceinline__ void store_rec<float>(SweepRec<float> *dst, double A, double B, double C, double Dd,
+                                                 double hwx, double hwy, uint32_t code, double delta) {
+  const int clx = (code >> kClsXShift) & 3, cly = (code >> kClsYShift) & 3;
+  const bool solid = (code & kSolid) != 0;
+  SweepRec<float> r;
+  r.A = solid ? 0.f : (float)A;
+  r.B = solid ? 0.f : (float)B;
+  r.C = solid ? 0.f : (float)C;
+  r.D = solid ? 0.f : (float)Dd;
+  r.ax1 = solid ? 0.f : class_a1(clx);
+  r.ax2 = solid ? 0.f : class_a2(clx);
+  r.xw = (!solid && clx == kWall) ? (float)(2.0 * hwx) : 0.f;
+  r.ay1 = solid ? 0.f : class_a1(cly);
+  r.ay2 = solid ? 0.f : class_a2(cly);
+  r.yw = (!solid && cly == kWall) ? (float)(2.0 * hwy) : 0.f;
   r.code = code;
-  r.delta = (T)delta;
+  r.delta = (float)delta;
+  *dst = r;
+}
+template <>
+__device__ __forceinline__ void store_rec<double>(SweepRec<double> *dst, double A, double B, double C, double Dd,
+                                                  double hwx, double hwy, uint32_t code, double delta) {
+  const int clx = (code >> kClsXShift) & 3, cly = (code >> kClsYShift) & 3;
+  const bool solid = (code & kSolid) != 0;
+  SweepRec<double> r;
+  r.A = solid ? 0.0 : A;
+  r.B = solid ? 0.0 : B;
+  r.C = solid ? 0.0 : C;
+  r.D = solid ? 0.0 : Dd;
+  r.xw = (!solid && clx == kWall) ? 2.0 * hwx : 0.0;
+  r.yw = (!solid && cly == kWall) ? 2.0 * hwy : 0.0;
+  r.code = code;
+  r.pad = 0u;
+  r.delta = delta;
   *dst = r;
 }
 
@@ -190,6 +218,10 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
         done = 1;
         status = 6;  // DVM_ENUMERIC
       }
+      if (atomicAdd(&st->err_flag, 0) != 0) {
+        done = 1;
+        status = 5;  // DVM_ETIMEOUT: a sweep block gave up waiting on another warp
+      }
       st->iter = n;
       st->c = c_new;
       st->s = s;
@@ -226,6 +258,7 @@ __global__ void reset_kernel(const InstanceDesc *D) {
     st->status = 0;
     st->max_iter = 0;
     st->nan_flag = 0;
+    st->err_flag = 0;
     st->ticket1 = st->ticket2 = 0u;
     st->tol = 0.0;
     st->c = st->s = st->s_new = 0.0;
@@ -244,6 +277,7 @@ __global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;
+  st->err_flag = 0;
   st->done = (st->iter >= max_iter_abs) ? 1 : 0;
   if (st->done) st->status = 4;
 }

@@ -7,42 +7,43 @@
 
 namespace dvm {
 
-// Shared-memory layout of the sweep kernel (bytes), identical on host and device.
+// Shared-memory layout of the sweep kernel (bytes), identical on host and device: the 3-deep ring of
+// R warps x CW cells x ring_stride, the record stages, the staged seam rows (FP32), the 1/denominator
+// table, the moment weights and the warps' progress words.
 struct SweepSmemLayout {
-  size_t ring, stage, seam, inv, wts, total;
+  size_t ring, stage, seam, inv, wts, prog, total;
 };
 
-__host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int C, int tsize, int recsize,
-                                                             int nstage, int stage_seams) {
+__host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int tsize, int recsize, int nstage,
+                                                             int stage_seams, int ring_stride) {
   SweepSmemLayout L;
   size_t off = 0;
+  auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   L.ring = off;
-  off += (size_t)R * 3 * C * kRingPad * tsize;
-  off = (off + 15) & ~(size_t)15;
+  off = align16(off + (size_t)R * 3 * cw * ring_stride * tsize);
   L.stage = off;
-  off += (size_t)R * nstage * C * recsize;
-  off = (off + 15) & ~(size_t)15;
+  off = align16(off + (size_t)R * nstage * cw * recsize);
   L.seam = off;
-  if (stage_seams) off += (size_t)2 * nstage * 2 * C * kLanes * tsize;
-  off = (off + 15) & ~(size_t)15;
+  if (stage_seams) off = align16(off + (size_t)2 * nstage * 2 * cw * kLanes * tsize);
   L.inv = off;
-  off += (size_t)9 * kLanes * tsize;
+  off = align16(off + (size_t)9 * kLanes * tsize);
   L.wts = off;
-  off += (size_t)4 * kRingPad * tsize;
-  off = (off + 15) & ~(size_t)15;
+  off = align16(off + (size_t)4 * ring_stride * tsize);
+  L.prog = off;
+  off = align16(off + (size_t)R * sizeof(int));
   L.total = off;
   return L;
 }
 
-// Sweep configuration of a precision: stage depth and seam staging.
-inline int sweep_nstage(bool fp64) { return fp64 ? 1 : 2; }
-inline int sweep_stage_seams(bool fp64) { return fp64 ? 0 : 1; }
-
-size_t sweep_smem_bytes(bool fp64, int warps, int cmax);
+size_t sweep_smem_bytes(bool fp64, int warps, int cw);
 
 // One source-iteration sweep of every instance in the launch (fused moments and wall fluxes).
-cudaError_t launch_sweep(bool fp64, bool store_h, bool uniform_delta, const LaunchDesc &L, int nblocks,
-                         cudaStream_t stream);
+cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+cudaError_t launch_sweep_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+size_t sweep_smem_bytes_f32(int warps, int cw);
+size_t sweep_smem_bytes_f64(int warps, int cw);
+
 // Finalize: mean-density projection, moments, residual, flow rate, next sweep records.
 cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream);
 // Reset an instance to h = 0 (records, accumulators and state; arrays are cleared by the caller).

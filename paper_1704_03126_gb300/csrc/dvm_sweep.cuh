@@ -1,0 +1,442 @@
+// dvm_sweep.cuh -- the transport sweep of one source iteration (the hot path), shared by the FP32
+// and FP64 translation units.
+//
+// For every discrete velocity, Eq. (iteration) of arXiv:1704.03126 (Sec. II.A) is solved over all
+// gas cells with upwind differences:
+//     (delta + sum_a |v_a|/dx kappa_a) h = R + sum_a |v_a|/dx combo_a,
+//     R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v1                     (Eq. BGK)
+// where along each axis (s = sign v_a, u1 = cell - s, u2 = cell - 2 s)
+//     interior            kappa = 3/2, combo = 2 h(u1) - h(u2)/2   (second order)
+//     u2 solid            kappa = 1,   combo = h(u1)               (first order)
+//     u1 solid            kappa = 2,   combo = 2 h_w(own face)     (linear through the wall value)
+// h_w is the diffuse wall value (Eq. diffuse2) of the previous iterate, and upstream cells across a
+// periodic seam also take the previous iterate (lagged).
+//
+// GB300 mapping.  One thread block sweeps one group of 32 velocities of one quadrant (a velocity per
+// lane: every lane walks the cells in the same order, so all branches are warp-uniform).  Its R
+// warps are rows in flight of a wavefront: row q (in sweep order) goes through column chunks of CW
+// cells, chunk c at "step" q + c, and warp w owns rows w, w + R, ...  A warp writes its rows into a
+// 3-deep shared-memory ring that the next two rows read.  There is no block-wide barrier: each warp
+// publishes the steps it has finished in a shared progress word and waits (bounded spins) only for
+//   - the warp of row q-1 to have finished the same chunk (then row q-2 has too), and
+//   - the warp of row q+2 to have read the ring slot this step overwrites.
+// Per-cell records (right-hand-side coefficients, wall values, stencil classes) are staged into
+// shared memory with cp.async one chunk ahead (FP32) or at the start of the chunk (FP64).  The
+// moments of each finished chunk are dot products over the 32 lanes read back from the ring (FP32
+// or FP64 sums) and are accumulated across groups with FP64 atomics; incident wall fluxes likewise.
+// h itself goes to HBM only at the periodic seams (and when the distribution is kept).
+#pragma once
+#include <climits>
+#include <cstdint>
+#include <type_traits>
+
+#include "dvm_device.cuh"
+#include "dvm_kernels.h"
+
+namespace dvm {
+namespace sweep {
+
+constexpr int kSpinLimit = 1 << 22;  // bounded waits: about 0.1-1 s before the kernel gives up
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.cta.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+// All lanes of the warp spin until *p >= need; false when the spin limit ran out.
+__device__ __forceinline__ bool wait_at_least(const int *p, int need) {
+  int spins = 0;
+  while (ld_acquire(p) < need) {
+    if (++spins > kSpinLimit) return false;
+    if (spins > 64) __nanosleep(32);
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T kappa_of(int cls) {
+  return cls == kFull ? T(1.5) : (cls == kNear ? T(1.0) : T(2.0));
+}
+
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  return T(1) / x;
+}
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  return __drcp_rn(x);
+}
+
+template <typename T>
+struct Traits;
+template <>
+struct Traits<float> {
+  static constexpr int kStages = 2;       // records staged one chunk ahead
+  static constexpr bool kStageSeams = true;
+  static constexpr int kRingStride = 36;  // 16-byte rows: vector loads in the moment dot products
+};
+template <>
+struct Traits<double> {
+  static constexpr int kStages = 1;       // shared memory is needed by the 8-byte ring
+  static constexpr bool kStageSeams = false;
+  static constexpr int kRingStride = 33;  // odd stride: conflict-free column reads
+};
+
+template <typename T>
+__host__ __device__ inline SweepSmemLayout layout(int warps, int cw) {
+  return sweep_smem_layout(warps, cw, (int)sizeof(T), (int)sizeof(SweepRec<T>), Traits<T>::kStages,
+                           Traits<T>::kStageSeams ? 1 : 0, Traits<T>::kRingStride);
+}
+
+template <typename T, bool UNIF, int CW>
+__global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(LaunchDesc L) {
+  constexpr int NSTAGE = Traits<T>::kStages;
+  constexpr bool STAGE_SEAM = Traits<T>::kStageSeams;
+  constexpr int RS = Traits<T>::kRingStride;
+  const int map = L.sweep_map[blockIdx.x];
+  const InstanceDesc *__restrict__ D = L.inst + (map >> 16);
+  const int g = map & 0xffff;
+  DeviceState *st = D->state;
+  if (*reinterpret_cast<volatile int *>(&st->done)) return;
+
+  const int nx = D->nx, ny = D->ny, ncell = D->ncell;
+  const bool px = D->periodic_x != 0, py = D->periodic_y != 0;
+  const int quad = g / D->groups_per_quadrant;
+  const bool xneg = (quad & 1) != 0, yneg = (quad & 2) != 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int Rb = blockDim.x >> 5;           // warps of the block (layout)
+  const int R = (nx + CW - 1) / CW;         // rows in flight of this instance (host ensures R <= Rb)
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SweepSmemLayout SL = layout<T>(Rb, CW);
+  T *ring = reinterpret_cast<T *>(smem + SL.ring);
+  SweepRec<T> *stage = reinterpret_cast<SweepRec<T> *>(smem + SL.stage);
+  T *seamst = reinterpret_cast<T *>(smem + SL.seam);
+  T *invt = reinterpret_cast<T *>(smem + SL.inv);
+  T *wts = reinterpret_cast<T *>(smem + SL.wts);
+  int *prog = reinterpret_cast<int *>(smem + SL.prog);
+
+  // zero the whole dynamic shared memory: ring slots and staged seam entries that are read before
+  // (or without) being written are multiplied by zero coefficients and must not hold NaN patterns
+  for (size_t b = threadIdx.x; b < SL.total / 16; b += blockDim.x)
+    reinterpret_cast<float4 *>(smem)[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes;
+  if (UNIF) {
+    const T *iv = static_cast<const T *>(D->inv_den) + (size_t)g * kInvRows * kLanes;
+    for (int i = threadIdx.x; i < kInvRows * kLanes; i += blockDim.x) invt[i] = iv[i];
+  }
+  for (int i = threadIdx.x; i < 4 * kLanes; i += blockDim.x) wts[(i >> 5) * RS + (i & 31)] = vt[(kW0 + (i >> 5)) * kLanes + (i & 31)];
+  // progress word of warp w = number of steps known finished; warp w starts at step w
+  for (int i = threadIdx.x; i < Rb; i += blockDim.x) prog[i] = i;
+  __syncthreads();
+  if (w >= R) return;
+
+  const T v1 = vt[kV1 * kLanes + lane], v2 = vt[kV2 * kLanes + lane], em1 = vt[kE2m1 * kLanes + lane];
+  const T cx = vt[kCx * kLanes + lane], cy = vt[kCy * kLanes + lane];
+  const T wnx = vt[kWnx * kLanes + lane], wny = vt[kWny * kLanes + lane];
+  const T sshift = static_cast<T>(st->s);
+  const SweepRec<T> *__restrict__ rec = static_cast<const SweepRec<T> *>(D->rec) + (size_t)quad * ncell;
+  T *seamx = static_cast<T *>(D->seam_x) + (size_t)g * ny * 2 * kLanes;
+  T *seamy = static_cast<T *>(D->seam_y) + (size_t)g * nx * 2 * kLanes;
+  T *hout = D->h ? static_cast<T *>(D->h) + (size_t)g * ncell * kLanes : nullptr;
+  double *acc = D->acc;
+  double *facc = D->facc + (size_t)((st->iter + 1) & 1) * ncell * 4;
+  const int sidex = xneg ? kW : kE;  // wall side hit by this quadrant's velocities along x
+  const int sidey = yneg ? kS : kN;
+  const int wprev = (w + R - 1) % R, wnext2 = (w + 2) % R;
+
+  // stage the records of chunk (q, c) into buffer `buf` (and, for rows 0 and 1 of a periodic y
+  // axis, the wrapped seam rows); x-seam values of a new row are loaded into registers
+  T pf_hp1 = T(0), pf_hp2 = T(0);
+  auto issue = [&](int q, int c, int buf) {
+    const int j = yneg ? ny - 1 - q : q;
+    SweepRec<T> *sdst = stage + ((size_t)w * NSTAGE + buf) * CW;
+    const int p0 = c * CW;
+    const int cnt = min(CW, nx - p0);
+    if (lane < cnt) {
+      const int p = p0 + lane;
+      const int i = xneg ? nx - 1 - p : p;
+      const char *src = reinterpret_cast<const char *>(rec + j * nx + i);
+      char *dst = reinterpret_cast<char *>(sdst + lane);
+#pragma unroll
+      for (int b = 0; b < (int)sizeof(SweepRec<T>); b += 16) cp_async16(dst + b, src + b);
+    } else if (lane < CW) {
+      // past the ragged end of the row: a solid record (zero coefficients) sweeps to h = 0
+      float4 *dst = reinterpret_cast<float4 *>(sdst + lane);
+#pragma unroll
+      for (int b = 0; b < (int)(sizeof(SweepRec<T>) / 16); ++b) dst[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+      sdst[lane].code = kSolid | (9u << kInvShift);
+    }
+    if (STAGE_SEAM && py && q < 2) {
+      // row 0 reads rows ny-1, ny-2 (seam slots 1, 0); row 1 reads row ny-1 (slot 1) as h(u2)
+      T *sd = seamst + ((size_t)(w & 1) * NSTAGE + buf) * 2 * CW * kLanes;
+#pragma unroll
+      for (int l = 0; l < CW; ++l) {
+        if (l < cnt) {
+          const int p = p0 + l;
+          const int i = xneg ? nx - 1 - p : p;
+          const T *s0 = seamy + i * 2 * kLanes + lane;
+          if (q == 0) {
+            cp_async_small<sizeof(T)>(sd + l * kLanes + lane, s0 + kLanes);
+            cp_async_small<sizeof(T)>(sd + (CW + l) * kLanes + lane, s0);
+          } else {
+            cp_async_small<sizeof(T)>(sd + (CW + l) * kLanes + lane, s0 + kLanes);
+          }
+        }
+      }
+    }
+    if (c == 0 && px) {
+      const T *sx = seamx + j * 2 * kLanes + lane;
+      pf_hp1 = sx[kLanes];  // column nx-1 in sweep order (before its mass shift)
+      pf_hp2 = sx[0];       // column nx-2
+    }
+    cp_async_commit();
+  };
+
+  // sweep one chunk.  MODE 0: upstream rows from shared memory (ring or staged seam rows);
+  // MODES 1 and 2 (FP64, rows 0 and 1 of a periodic y axis): the wrapped upstream rows come from
+  // the global seam buffer (pointers already offset by the lane)
+  T hp1 = T(0), hp2 = T(0);
+  T row_hp1 = T(0), row_hp2 = T(0);  // x-seam values of the current row, latched from pf_*
+  auto run_chunk = [&](auto mode_tag, int q, int c, const SweepRec<T> *rs, T *myr, const T *pr1, int ps1,
+                       const T *pr2, int ps2) {
+    constexpr int MODE = decltype(mode_tag)::value;
+    const int j = yneg ? ny - 1 - q : q;
+    if (c == 0) {
+      hp1 = px ? row_hp1 - sshift : T(0);
+      hp2 = px ? row_hp2 - sshift : T(0);
+    }
+    const int p0 = c * CW;
+    const int cnt = min(CW, nx - p0);
+    // the cell loop has no branches: stencil classes are coefficients in the records, solid cells
+    // and the cells past a ragged row end have zero coefficients and sweep to h = 0
+#pragma unroll
+    for (int l = 0; l < CW; ++l) {
+      const SweepRec<T> r = rs[l];
+      T hq1, hq2;
+      if (MODE == 0) {
+        hq1 = pr1[l * ps1 + lane];
+        hq2 = pr2[l * ps2 + lane];
+      } else if (MODE == 1) {
+        hq1 = l < cnt ? pr1[l * ps1] - sshift : T(0);
+        hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
+      } else {
+        hq1 = pr1[l * ps1 + lane];
+        hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
+      }
+      T ax1, ax2, ay1, ay2;
+      if constexpr (sizeof(T) == 4) {
+        ax1 = r.ax1;
+        ax2 = r.ax2;
+        ay1 = r.ay1;
+        ay2 = r.ay2;
+      } else {
+        const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
+        const bool solid = (r.code & kSolid) != 0;
+        ax1 = solid ? T(0) : T(class_a1(clx));
+        ax2 = solid ? T(0) : T(class_a2(clx));
+        ay1 = solid ? T(0) : T(class_a1(cly));
+        ay2 = solid ? T(0) : T(class_a2(cly));
+      }
+      const T Rk = fma(r.D, em1, fma(r.C, v2, fma(r.B, v1, r.A)));
+      const T by = fma(ay1, hq1, fma(ay2, hq2, r.yw));
+      const T base = fma(cy, by, Rk);
+      T inv;
+      if (UNIF) {
+        inv = invt[((r.code >> kInvShift) & 15) * kLanes + lane];
+      } else {
+        const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
+        inv = recip<T>(r.delta + cx * kappa_of<T>(clx) + cy * kappa_of<T>(cly));
+      }
+      const T bx = fma(ax1, hp1, fma(ax2, hp2, r.xw));
+      const T h = fma(cx, bx, base) * inv;
+      hp2 = hp1;
+      hp1 = h;
+      myr[l * RS + lane] = h;
+    }
+    __syncwarp();
+    // per-chunk passes over the ring: stored distribution, seams, incident wall fluxes, moments
+    if (hout) {
+      for (int l = 0; l < cnt; ++l) {
+        const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
+        hout[(size_t)(j * nx + i) * kLanes + lane] = myr[l * RS + lane];
+      }
+    }
+    if (px && p0 + cnt > nx - 2) {
+      for (int p = max(p0, nx - 2); p < p0 + cnt; ++p)
+        seamx[(j * 2 + (p - (nx - 2))) * kLanes + lane] = myr[(p - p0) * RS + lane];
+    }
+    if (py && q >= ny - 2) {
+      for (int l = 0; l < cnt; ++l) {
+        const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
+        seamy[(i * 2 + (q - (ny - 2))) * kLanes + lane] = myr[l * RS + lane];
+      }
+    }
+    {
+      const uint32_t mycode = lane < cnt ? rs[lane].code : 0u;
+      unsigned incx = __ballot_sync(0xffffffffu, (mycode & kIncX) != 0);
+      unsigned incy = __ballot_sync(0xffffffffu, (mycode & kIncY) != 0);
+      while (incx | incy) {
+        const bool is_x = incx != 0;
+        const int l = __ffs(is_x ? incx : incy) - 1;
+        if (is_x) incx &= incx - 1;
+        else incy &= incy - 1;
+        const T f = warp_sum<T>((is_x ? wnx : wny) * myr[l * RS + lane]);
+        if (lane == 0) {
+          const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
+          atomicAdd(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
+        }
+      }
+    }
+    // moments of the chunk: one (cell, moment) pair per lane and pass, dot product over the lanes
+#pragma unroll
+    for (int pass = 0; pass < (CW * 4 + kLanes - 1) / kLanes; ++pass) {
+      const int pr = pass * kLanes + lane;
+      const int l = pr >> 2, m = pr & 3;
+      if (pr < CW * 4 && l < cnt && !(rs[l].code & kSolid)) {
+        const T *hr = myr + l * RS;
+        const T *wr = wts + m * RS;
+        T sum = T(0);
+        if constexpr (RS % 4 == 0 && sizeof(T) == 4) {
+#pragma unroll
+          for (int k = 0; k < kLanes; k += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(hr + k);
+            const float4 b = *reinterpret_cast<const float4 *>(wr + k);
+            sum = fma(a.x, b.x, sum);
+            sum = fma(a.y, b.y, sum);
+            sum = fma(a.z, b.z, sum);
+            sum = fma(a.w, b.w, sum);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < kLanes; ++k) sum = fma(wr[k], hr[k], sum);
+        }
+        const int p = p0 + l;
+        const int i = xneg ? nx - 1 - p : p;
+        atomicAdd(&acc[(j * nx + i) * 4 + m], static_cast<double>(sum));
+      }
+    }
+  };
+
+  auto give_up = [&]() {
+    cp_async_wait<0>();
+    atomicExch(&st->err_flag, 1);
+  };
+
+  int item = 0;
+  if (NSTAGE == 2) issue(w, 0, 0);
+  for (int q = w; q < ny; q += R) {
+    for (int c = 0; c < R; ++c, ++item) {
+      const int t = q + c;
+      const int buf = (NSTAGE == 2) ? (item & 1) : 0;
+      if (NSTAGE == 2) {
+        // pf_* hold this row's x-seam values (loaded when this chunk was staged); latch them before
+        // staging the next chunk, which may belong to the next row (one chunk per row when R = 1)
+        if (c == 0) {
+          row_hp1 = pf_hp1;
+          row_hp2 = pf_hp2;
+        }
+        const int nq = (c + 1 < R) ? q : q + R, nc = (c + 1 < R) ? c + 1 : 0;
+        if (nq < ny) issue(nq, nc, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        issue(q, c, 0);
+        cp_async_wait<0>();
+        if (c == 0) {
+          row_hp1 = pf_hp1;
+          row_hp2 = pf_hp2;
+        }
+      }
+      __syncwarp();
+      // row q-1 finished this chunk, and row q+2 has read the ring slot written three steps ago
+      if (R > 1 && !wait_at_least(&prog[wprev], t)) return give_up();
+      if (R > 2 && !wait_at_least(&prog[wnext2], t)) return give_up();
+      const SweepRec<T> *rs = stage + ((size_t)w * NSTAGE + buf) * CW;
+      T *myr = ring + ((size_t)w * 3 + (t % 3)) * CW * RS;
+      const T *pr1 = ring + ((size_t)wprev * 3 + ((t + 2) % 3)) * CW * RS;
+      const T *pr2 = ring + ((size_t)((w + 2 * R - 2) % R) * 3 + ((t + 1) % 3)) * CW * RS;
+      if (py && q < 2) {
+        if (STAGE_SEAM) {
+          T *sd = seamst + ((size_t)(w & 1) * NSTAGE + buf) * 2 * CW * kLanes;
+          const int cnt = min(CW, nx - c * CW);
+          // the staged seam values are the previous iterate before its mass shift (own lane only)
+          for (int l = 0; l < cnt; ++l) {
+            if (q == 0) sd[l * kLanes + lane] -= sshift;
+            sd[(CW + l) * kLanes + lane] -= sshift;
+          }
+          if (q == 0)
+            run_chunk(std::integral_constant<int, 0>(), q, c, rs, myr, sd, kLanes, sd + CW * kLanes, kLanes);
+          else
+            run_chunk(std::integral_constant<int, 0>(), q, c, rs, myr, pr1, RS, sd + CW * kLanes, kLanes);
+        } else {
+          const int p0 = c * CW;
+          const int i0 = xneg ? nx - 1 - p0 : p0;
+          const int stride = xneg ? -2 * kLanes : 2 * kLanes;
+          const T *s0 = seamy + i0 * 2 * kLanes + lane;
+          if (q == 0)
+            run_chunk(std::integral_constant<int, 1>(), q, c, rs, myr, s0 + kLanes, stride, s0, stride);
+          else
+            run_chunk(std::integral_constant<int, 2>(), q, c, rs, myr, pr1, RS, s0 + kLanes, stride);
+        }
+      } else {
+        run_chunk(std::integral_constant<int, 0>(), q, c, rs, myr, pr1, RS, pr2, RS);
+      }
+      __syncwarp();
+      if (lane == 0) st_release(&prog[w], t + 1);
+    }
+  }
+  if (lane == 0) st_release(&prog[w], INT_MAX / 2);  // no more rows: never wait on this warp again
+}
+
+template <typename T, bool UNIF, int CW>
+cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  auto kern = sweep_kernel<T, UNIF, CW>;
+  const size_t smem = layout<T>(L.warps, CW).total;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nblocks, L.warps * kLanes, smem, stream>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename T, bool UNIF>
+cudaError_t launch_cw(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  switch (L.cw) {
+    case 1: return launch<T, UNIF, 1>(L, nblocks, stream);
+    case 2: return launch<T, UNIF, 2>(L, nblocks, stream);
+    case 4: return launch<T, UNIF, 4>(L, nblocks, stream);
+    case 8: return launch<T, UNIF, 8>(L, nblocks, stream);
+    case 16: return launch<T, UNIF, 16>(L, nblocks, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sweep
+}  // namespace dvm

@@ -1,0 +1,13 @@
+// dvm_sweep_f32.cu -- FP32-storage instantiations of the sweep kernel (see dvm_sweep.cuh).
+#include "dvm_sweep.cuh"
+
+namespace dvm {
+
+size_t sweep_smem_bytes_f32(int warps, int cw) { return sweep::layout<float>(warps, cw).total; }
+
+cudaError_t launch_sweep_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  return uniform_delta ? sweep::launch_cw<float, true>(L, nblocks, stream)
+                       : sweep::launch_cw<float, false>(L, nblocks, stream);
+}
+
+}  // namespace dvm

@@ -1,0 +1,21 @@
+// dvm_sweep_f64.cu -- FP64 instantiations of the sweep kernel (see dvm_sweep.cuh).
+#include "dvm_sweep.cuh"
+
+namespace dvm {
+
+size_t sweep_smem_bytes_f64(int warps, int cw) { return sweep::layout<double>(warps, cw).total; }
+
+cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  return uniform_delta ? sweep::launch_cw<double, true>(L, nblocks, stream)
+                       : sweep::launch_cw<double, false>(L, nblocks, stream);
+}
+
+size_t sweep_smem_bytes(bool fp64, int warps, int cw) {
+  return fp64 ? sweep_smem_bytes_f64(warps, cw) : sweep_smem_bytes_f32(warps, cw);
+}
+
+cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  return fp64 ? launch_sweep_f64(uniform_delta, L, nblocks, stream) : launch_sweep_f32(uniform_delta, L, nblocks, stream);
+}
+
+}  // namespace dvm

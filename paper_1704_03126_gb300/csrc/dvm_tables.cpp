@@ -136,7 +136,7 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
     for (int i = 0; i < nx; ++i) {
       const int cell = j * nx + i;
       if (mask[cell]) {
-        for (int q = 0; q < 4; ++q) G.code4[(size_t)cell * 4 + q] = kSolid;
+        for (int q = 0; q < 4; ++q) G.code4[(size_t)cell * 4 + q] = kSolid | (9u << kInvShift);
         continue;
       }
       ++G.n_gas;
@@ -170,6 +170,8 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
           G.hw_src[(size_t)cell * 8 + q * 2 + 1] = src;
           if (solid(i, j + sy)) code |= kIncY;
         }
+        const uint32_t clx = (code >> kClsXShift) & 3u, cly = (code >> kClsYShift) & 3u;
+        code |= (clx * 3u + cly) << kInvShift;
         G.code4[(size_t)cell * 4 + q] = code;
       }
     }
