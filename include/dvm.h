@@ -132,6 +132,19 @@ typedef struct {
 } dvm_info;
 dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info);
 
+/* Gradient of the flow rate with respect to the per-cell collision rate, dQ/d delta_c, at the current
+ * (converged) forward state, by the adjoint of the projected source iteration: transposed sweeps
+ * (velocities visited in the reverse order, pulling from their forward-downstream cells) until the
+ * stopping test of dvm_solve, applied to the relative change of sum_k v1_k z_k, passes.  This is the
+ * field a wall-distance-dependent relaxation time would change (the paper's MRT-LBM comparison
+ * alters exactly this coefficient).
+ *   dQ_ddelta   host double [ny][nx] (output; 0 in solid cells).
+ *   q_identity  host, may be NULL: F sum z v1, equal to Q at convergence (a consistency check).
+ *   iters       host, may be NULL: adjoint sweeps run.
+ * Needs store_distribution = 1 and at least one forward sweep (DVM_ESTATE otherwise).  Allocates the
+ * adjoint state (about as much as the forward state plus one more distribution) on first use. */
+dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta, double *q_identity, int *iters);
+
 /* Distribution h of selected velocities (needs store_distribution = 1).  ks: host int [nk] with
  * k = a * n + b for v = (x_a, x_b) on the 1D nodes in ascending order.  out: host double
  * [nk][ny][nx]; solid cells 0. */

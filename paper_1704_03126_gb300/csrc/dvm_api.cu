@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/dvm.h"
+#include "dvm.h"
 #include "dvm_device.cuh"
 #include "dvm_kernels.h"
 #include "dvm_tables.h"
@@ -47,6 +47,13 @@ struct dvm_ctx {
   dvm_batch *self = nullptr;       // batch of this context alone (built on first use)
   DeviceState *h_state = nullptr;  // pinned
   std::string err;
+  // adjoint (allocated by the first dvm_adjoint)
+  void *a_rec = nullptr, *a_seamx = nullptr, *a_seamy = nullptr, *a_z = nullptr;
+  double *a_acc = nullptr, *a_flux = nullptr, *a_alpha = nullptr, *a_z1prev = nullptr, *a_grad = nullptr;
+  DeviceState *a_state = nullptr;
+  InstanceDesc *a_desc = nullptr;
+  cudaGraphExec_t a_graph = nullptr;
+  int a_graph_iters = 0;
 };
 
 // A set of contexts advanced together: one launch of each kernel per sweep, replayed as CUDA graphs.
@@ -100,8 +107,10 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
       const double W = valid ? c->w1[half + a] * c->w1[half + b] : 0.0;
       const double e = v1 * v1 + v2 * v2 - 1.0;
       const double cx = std::fabs(v1) / dx, cy = std::fabs(v2) / dx;
+      const double z = valid ? 1.0 : 0.0;
       const double f[kNumVelFields] = {v1, v2, e, cx, cy, W, W * v1, W * v2, W * (v1 * v1 + v2 * v2),
-                                       std::fabs(v1) * W, std::fabs(v2) * W};
+                                       std::fabs(v1) * W, std::fabs(v2) * W,
+                                       z, z * v1, z * v2, z * (v1 * v1 + v2 * v2)};
       for (int k = 0; k < kNumVelFields; ++k) vel[((size_t)g * kNumVelFields + k) * kLanes + lane] = (T)f[k];
       for (int clx = 0; clx < 3; ++clx)
         for (int cly = 0; cly < 3; ++cly)
@@ -198,6 +207,19 @@ void release_device(dvm_ctx *c) {
   free_dev(c->d_fin_map);
   if (c->h_state) cudaFreeHost(c->h_state);
   c->h_state = nullptr;
+  if (c->a_graph) cudaGraphExecDestroy(c->a_graph);
+  c->a_graph = nullptr;
+  free_dev(c->a_rec);
+  free_dev(c->a_seamx);
+  free_dev(c->a_seamy);
+  free_dev(c->a_z);
+  free_dev(c->a_acc);
+  free_dev(c->a_flux);
+  free_dev(c->a_alpha);
+  free_dev(c->a_z1prev);
+  free_dev(c->a_grad);
+  free_dev(c->a_state);
+  free_dev(c->a_desc);
 }
 
 dvm_status reset_state(dvm_ctx *c) {
@@ -711,6 +733,10 @@ dvm_status dvm_set_delta_field(dvm_ctx *ctx, const double *delta_c) {
     batch_free(ctx->self);
     ctx->self = nullptr;
   }
+  if (ctx->a_graph) {
+    cudaGraphExecDestroy(ctx->a_graph);
+    ctx->a_graph = nullptr;
+  }
   dvm_status st = upload_desc(ctx);
   if (st != DVM_OK) return st;
   return reset_state(ctx);
@@ -828,6 +854,118 @@ dvm_status dvm_velocity_grid(const dvm_quad *q, double *nodes, double *weights) 
     weights[a] = w[a];
   }
   return DVM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Adjoint: gradient of Q with respect to the per-cell collision rate (dvm_adjoint).
+
+namespace {
+
+dvm_status adjoint_setup(dvm_ctx *c) {
+  const size_t ts = c->fp64 ? 8 : 4;
+  const size_t recsz = c->fp64 ? sizeof(SweepRec<double>) : sizeof(SweepRec<float>);
+  const size_t ncell = (size_t)c->ncell;
+  if (!c->a_state) {
+    DVM_CUDA(c, cudaMalloc(&c->a_rec, recsz * 4 * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_seamx, ts * c->ngroups * c->ny * 2 * kLanes));
+    DVM_CUDA(c, cudaMalloc(&c->a_seamy, ts * c->ngroups * c->nx * 2 * kLanes));
+    DVM_CUDA(c, cudaMalloc(&c->a_z, ts * c->ngroups * ncell * kLanes));
+    DVM_CUDA(c, cudaMalloc(&c->a_acc, sizeof(double) * 4 * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_flux, sizeof(double) * 8 * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_alpha, sizeof(double) * 4 * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_z1prev, sizeof(double) * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_grad, sizeof(double) * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_state, sizeof(DeviceState)));
+    DVM_CUDA(c, cudaMalloc(&c->a_desc, sizeof(InstanceDesc)));
+  }
+  // the adjoint view: the forward instance with the adjoint buffers in place of the forward ones
+  InstanceDesc A = c->hdesc;
+  A.uniform_delta = c->uniform ? 1 : 0;
+  A.delta_field = c->d_delta_field;
+  A.rec = c->a_rec;
+  A.acc = c->a_acc;
+  A.facc = c->a_flux;
+  A.mom = c->a_alpha;
+  A.u1prev = c->a_z1prev;
+  A.seam_x = c->a_seamx;
+  A.seam_y = c->a_seamy;
+  A.h = c->a_z;
+  A.state = c->a_state;
+  A.h_fwd = c->d_h;
+  A.mom_fwd = c->d_mom;
+  A.state_fwd = c->d_state;
+  A.grad = c->a_grad;
+  DVM_CUDA(c, cudaMemcpyAsync(c->a_desc, &A, sizeof(InstanceDesc), cudaMemcpyHostToDevice, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_acc, 0, sizeof(double) * 4 * ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_flux, 0, sizeof(double) * 8 * ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_alpha, 0, sizeof(double) * 4 * ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_z1prev, 0, sizeof(double) * ncell, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_seamx, 0, ts * c->ngroups * c->ny * 2 * kLanes, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_seamy, 0, ts * c->ngroups * c->nx * 2 * kLanes, c->stream));
+  DVM_CUDA(c, cudaMemsetAsync(c->a_z, 0, ts * c->ngroups * ncell * kLanes, c->stream));
+  DVM_CUDA(c, launch_adjoint_reset(c->a_desc, c->ncell, c->fp64, c->stream));
+  if (!c->a_graph) {
+    const int rows = (c->nx + c->cw - 1) / c->cw;
+    LaunchDesc L = make_launch(c->a_desc, c->d_sweep_map, c->d_fin_map, 1, rows, c->cw);
+    const int fin_blocks = c->hdesc.fin_nblocks;
+    const int lines = (c->hdesc.periodic_x ? c->ngroups * c->ny : 0) + (c->hdesc.periodic_y ? c->ngroups * c->nx : 0);
+    const int seam_blocks = (lines * 32 + 255) / 256;
+    const double upd = (double)c->geo.n_gas * c->nv * c->nv;
+    c->a_graph_iters = iters_per_graph(upd);
+    cudaGraph_t graph = nullptr;
+    DVM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < c->a_graph_iters && e == cudaSuccess; ++it) {
+      e = launch_sweep_adjoint(c->fp64, c->uniform, L, c->ngroups, c->cap_stream);
+      if (e == cudaSuccess) e = launch_adjoint_finalize(L, fin_blocks, seam_blocks, c->fp64, c->cap_stream);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(c, DVM_ECUDA, std::string("adjoint graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&c->a_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, DVM_ECUDA, std::string("adjoint graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return DVM_OK;
+}
+
+}  // namespace
+
+dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta, double *q_identity, int *iters) {
+  if (!ctx || !dQ_ddelta) return DVM_EINVAL;
+  dvm_ctx *c = ctx;
+  if (!(tol > 0.0) || max_iter < 1) return fail(c, DVM_EINVAL, "tol must be > 0 and max_iter >= 1");
+  if (!c->d_h) return fail(c, DVM_ESTATE, "dvm_adjoint needs the forward distribution (store_distribution = 1)");
+  DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
+  DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->h_state->iter < 1) return fail(c, DVM_ESTATE, "dvm_adjoint needs a forward solve first");
+  dvm_status st = adjoint_setup(c);
+  if (st != DVM_OK) return st;
+  DVM_CUDA(c, launch_arm(c->a_state, tol, max_iter, c->stream));
+  const long long max_replays = (long long)max_iter / c->a_graph_iters + 3;
+  for (long long replay = 0;; ++replay) {
+    if (replay >= max_replays) return fail(c, DVM_ETIMEOUT, "adjoint stop flag not set after max_iter sweeps");
+    DVM_CUDA(c, cudaGraphLaunch(c->a_graph, c->stream));
+    DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->a_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
+    DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_state->done) break;
+  }
+  const dvm_status status = (dvm_status)c->h_state->status;
+  const int n = c->h_state->iter;
+  if (status != DVM_OK && status != DVM_ENOCONV) return fail(c, status, "adjoint iteration failed");
+  DVM_CUDA(c, cudaMemsetAsync(&c->a_state->Q, 0, sizeof(double), c->stream));
+  DVM_CUDA(c, launch_adjoint_gradient(c->a_desc, c->ncell, c->fp64, c->stream));
+  std::vector<double> g((size_t)c->ncell);
+  DVM_CUDA(c, cudaMemcpyAsync(g.data(), c->a_grad, sizeof(double) * c->ncell, cudaMemcpyDeviceToHost, c->stream));
+  DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->a_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
+  DVM_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int cell = 0; cell < c->ncell; ++cell)
+    dQ_ddelta[cell] = (c->geo.code4[(size_t)cell * 4] & kSolid) ? 0.0 : g[cell];
+  if (q_identity) *q_identity = c->h_state->Q;
+  if (iters) *iters = n;
+  return status;
 }
 
 dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out) {

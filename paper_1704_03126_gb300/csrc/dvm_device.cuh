@@ -24,6 +24,13 @@ enum : uint32_t {
   kIncX = 1u << 5, // the cell owns a wall face on its downstream x side (incident for this quadrant)
   kIncY = 1u << 6,
   kInvShift = 8,   // 4 bits: row of the 1/denominator table, clx * 3 + cly, or 9 (solid: 0)
+  // Transposed stencil (adjoint sweep): the forward-downstream cells d1 = c + s and d2 = c + 2 s
+  // read c with weights t1 in {0, 1, 2} (d1 solid / second cell from a wall / interior) and
+  // t2 in {0, -1/2} (d1 or d2 solid / interior).
+  kAdjT1XShift = 12,  // 2 bits: t1 along x
+  kAdjT2X = 1u << 14, // t2 = -1/2 along x
+  kAdjT1YShift = 15,  // 2 bits: t1 along y
+  kAdjT2Y = 1u << 17,
 };
 enum : int { kFull = 0, kNear = 1, kWall = 2 };
 // sides of a cell: the solid neighbour lies at -x (W), +x (E), -y (S), +y (N)
@@ -65,6 +72,7 @@ enum : int {
   kV1 = 0, kV2, kE2m1, kCx, kCy,   // v1, v2, |v|^2 - 1, |v1|/dx, |v2|/dx
   kW0, kW1, kW2, kW3,              // W, W v1, W v2, W |v|^2 (moment weights; W = 0 on padded lanes)
   kWnx, kWny,                      // |v1| W, |v2| W (incident wall flux weights)
+  kZ0, kZ1, kZ2, kZ3,              // 1, v1, v2, |v|^2 (adjoint moments; 0 on padded lanes)
   kNumVelFields
 };
 
@@ -87,6 +95,10 @@ struct DeviceState {
   double eps_ring[4];
   double eps_min;  // smallest eps so far
   double mass_acc, du_acc, u_acc, q_acc;
+  // adjoint iteration only
+  double mu;       // bordering multiplier of the transposed system
+  double kappa;    // (mu - sum lambda) / (n_gas sum W), added to the next right-hand side
+  double lam_acc, dz_acc, seam_acc;
 };
 
 struct InstanceDesc {
@@ -119,6 +131,11 @@ struct InstanceDesc {
   void *seam_y;         // [ngroups][nx][2][32] T: last two rows of the previous sweep
   void *h;              // [ngroups][ncell][32] T, or nullptr
   DeviceState *state;
+  // adjoint view only: the forward state the gradient is taken at
+  const void *h_fwd;           // forward h, [ngroups][ncell][32] T
+  const double *mom_fwd;       // forward moments [ncell][4]
+  const DeviceState *state_fwd;
+  double *grad;                // [ncell] dQ / d delta_c
 };
 
 // Launch descriptor shared by the kernels of one (possibly batched) iteration.

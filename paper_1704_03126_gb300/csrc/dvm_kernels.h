@@ -43,6 +43,15 @@ cudaError_t launch_sweep_f32(bool uniform_delta, const LaunchDesc &L, int nblock
 cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 size_t sweep_smem_bytes_f32(int warps, int cw);
 size_t sweep_smem_bytes_f64(int warps, int cw);
+// The transposed sweep of the adjoint iteration (launch over adjoint views of the instances).
+cudaError_t launch_sweep_adjoint(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+cudaError_t launch_sweep_adjoint_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+cudaError_t launch_sweep_adjoint_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+// Adjoint bookkeeping: lagged seam sums, adjoint moments -> next right-hand sides, stopping test;
+// records of h = 0; the gradient from the stored forward and adjoint distributions.
+cudaError_t launch_adjoint_finalize(const LaunchDesc &L, int fin_blocks, int seam_blocks, bool fp64, cudaStream_t stream);
+cudaError_t launch_adjoint_reset(const InstanceDesc *adj_dev, int ncell, bool fp64, cudaStream_t stream);
+cudaError_t launch_adjoint_gradient(const InstanceDesc *adj_dev, int ncell, bool fp64, cudaStream_t stream);
 
 // Finalize: mean-density projection, moments, residual, flow rate, next sweep records.
 cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream);

@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/dvm.h"
+#include "dvm.h"
 #include "dvm_tables.h"
 
 namespace dvm {

@@ -114,7 +114,12 @@ __host__ __device__ inline SweepSmemLayout layout(int warps, int cw) {
                            Traits<T>::kStageSeams ? 1 : 0, Traits<T>::kRingStride);
 }
 
-template <typename T, bool UNIF, int CW>
+// ADJ = false: the forward sweep.  ADJ = true: the transposed sweep of the adjoint iteration --
+// cells are visited in the reverse order (the forward order of the opposite quadrant), each pulls
+// from its forward-downstream cells with the transposed weights t1, t2, the right-hand side is
+// W (A + B v1 + C v2 + D (|v|^2 - 1)) + |v1| W TX + |v2| W TY, the moments are the unweighted sums
+// of (1, v1, v2, |v|^2) z, and cells next to a wall add 2 |v_a|/dx z to that wall's adjoint flux.
+template <typename T, bool UNIF, int CW, bool ADJ>
 __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(LaunchDesc L) {
   constexpr int NSTAGE = Traits<T>::kStages;
   constexpr bool STAGE_SEAM = Traits<T>::kStageSeams;
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
   const int nx = D->nx, ny = D->ny, ncell = D->ncell;
   const bool px = D->periodic_x != 0, py = D->periodic_y != 0;
   const int quad = g / D->groups_per_quadrant;
-  const bool xneg = (quad & 1) != 0, yneg = (quad & 2) != 0;
+  const bool xneg = ((quad & 1) != 0) != ADJ, yneg = ((quad & 2) != 0) != ADJ;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int Rb = blockDim.x >> 5;           // warps of the block (layout)
   const int R = (nx + CW - 1) / CW;         // rows in flight of this instance (host ensures R <= Rb)
@@ -152,7 +157,8 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
     const T *iv = static_cast<const T *>(D->inv_den) + (size_t)g * kInvRows * kLanes;
     for (int i = threadIdx.x; i < kInvRows * kLanes; i += blockDim.x) invt[i] = iv[i];
   }
-  for (int i = threadIdx.x; i < 4 * kLanes; i += blockDim.x) wts[(i >> 5) * RS + (i & 31)] = vt[(kW0 + (i >> 5)) * kLanes + (i & 31)];
+  constexpr int kMom0 = ADJ ? kZ0 : kW0;  // moment weights: (W, W v1, W v2, W |v|^2) or (1, v1, v2, |v|^2)
+  for (int i = threadIdx.x; i < 4 * kLanes; i += blockDim.x) wts[(i >> 5) * RS + (i & 31)] = vt[(kMom0 + (i >> 5)) * kLanes + (i & 31)];
   // progress word of warp w = number of steps known finished; warp w starts at step w
   for (int i = threadIdx.x; i < Rb; i += blockDim.x) prog[i] = i;
   __syncthreads();
@@ -161,7 +167,8 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
   const T v1 = vt[kV1 * kLanes + lane], v2 = vt[kV2 * kLanes + lane], em1 = vt[kE2m1 * kLanes + lane];
   const T cx = vt[kCx * kLanes + lane], cy = vt[kCy * kLanes + lane];
   const T wnx = vt[kWnx * kLanes + lane], wny = vt[kWny * kLanes + lane];
-  const T sshift = static_cast<T>(st->s);
+  const T wl = vt[kW0 * kLanes + lane];
+  const T sshift = ADJ ? T(0) : static_cast<T>(st->s);
   const SweepRec<T> *__restrict__ rec = static_cast<const SweepRec<T> *>(D->rec) + (size_t)quad * ncell;
   T *seamx = static_cast<T *>(D->seam_x) + (size_t)g * ny * 2 * kLanes;
   T *seamy = static_cast<T *>(D->seam_y) + (size_t)g * nx * 2 * kLanes;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
   // the global seam buffer (pointers already offset by the lane)
   T hp1 = T(0), hp2 = T(0);
   T row_hp1 = T(0), row_hp2 = T(0);  // x-seam values of the current row, latched from pf_*
-  auto run_chunk = [&](auto mode_tag, int q, int c, const SweepRec<T> *rs, T *myr, const T *pr1, int ps1,
+  auto run_chunk = [&](auto mode_tag, int q, int c, int t, const SweepRec<T> *rs, T *myr, const T *pr1, int ps1,
                        const T *pr2, int ps2) {
     constexpr int MODE = decltype(mode_tag)::value;
     const int j = yneg ? ny - 1 - q : q;
@@ -235,52 +242,82 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
     }
     const int p0 = c * CW;
     const int cnt = min(CW, nx - p0);
-    // the cell loop has no branches: stencil classes are coefficients in the records, solid cells
-    // and the cells past a ragged row end have zero coefficients and sweep to h = 0
+    // The cell loop has no branches: stencil classes are coefficients in the records; solid cells
+    // and the cells past a ragged row end have zero coefficients and sweep to h = 0.  Sub-chunks of
+    // SUB cells run in two phases: first everything that does not depend on this row's x-recurrence
+    // (records, the two upstream rows, the right-hand side, the y combination, 1/denominator) for all
+    // SUB cells, so their shared-memory loads overlap; then the recurrence itself and the ring stores.
+    constexpr int SUB = (sizeof(T) == 4) ? (CW < 8 ? CW : 8) : (CW < 2 ? CW : 2);
 #pragma unroll
-    for (int l = 0; l < CW; ++l) {
-      const SweepRec<T> r = rs[l];
-      T hq1, hq2;
-      if (MODE == 0) {
-        hq1 = pr1[l * ps1 + lane];
-        hq2 = pr2[l * ps2 + lane];
-      } else if (MODE == 1) {
-        hq1 = l < cnt ? pr1[l * ps1] - sshift : T(0);
-        hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
-      } else {
-        hq1 = pr1[l * ps1 + lane];
-        hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
+    for (int l0 = 0; l0 < CW; l0 += SUB) {
+      T base[SUB], invv[SUB], cax1[SUB], cax2[SUB], cxw[SUB];
+#pragma unroll
+      for (int u = 0; u < SUB; ++u) {
+        const int l = l0 + u;
+        const SweepRec<T> r = rs[l];
+        T hq1, hq2;
+        if (MODE == 0) {
+          hq1 = pr1[l * ps1 + lane];
+          hq2 = pr2[l * ps2 + lane];
+        } else if (MODE == 1) {
+          hq1 = l < cnt ? pr1[l * ps1] - sshift : T(0);
+          hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
+        } else {
+          hq1 = pr1[l * ps1 + lane];
+          hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
+        }
+        T ay1, ay2;
+        if constexpr (sizeof(T) == 4) {
+          cax1[u] = r.ax1;
+          cax2[u] = r.ax2;
+          ay1 = r.ay1;
+          ay2 = r.ay2;
+        } else if constexpr (!ADJ) {
+          const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
+          const bool solid = (r.code & kSolid) != 0;
+          cax1[u] = solid ? T(0) : T(class_a1(clx));
+          cax2[u] = solid ? T(0) : T(class_a2(clx));
+          ay1 = solid ? T(0) : T(class_a1(cly));
+          ay2 = solid ? T(0) : T(class_a2(cly));
+        } else {
+          cax1[u] = T((r.code >> kAdjT1XShift) & 3);
+          cax2[u] = (r.code & kAdjT2X) ? T(-0.5) : T(0);
+          ay1 = T((r.code >> kAdjT1YShift) & 3);
+          ay2 = (r.code & kAdjT2Y) ? T(-0.5) : T(0);
+        }
+        T Rk = fma(r.D, em1, fma(r.C, v2, fma(r.B, v1, r.A)));
+        T by;
+        if constexpr (ADJ) {
+          // the incident-wall terms ride in the xw / yw slots of adjoint records
+          Rk = fma(wnx, r.xw, fma(wny, r.yw, wl * Rk));
+          cxw[u] = T(0);
+          by = fma(ay1, hq1, ay2 * hq2);
+        } else {
+          cxw[u] = r.xw;
+          by = fma(ay1, hq1, fma(ay2, hq2, r.yw));
+        }
+        base[u] = fma(cy, by, Rk);
+        if (UNIF) {
+          invv[u] = invt[((r.code >> kInvShift) & 15) * kLanes + lane];
+        } else {
+          const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
+          invv[u] = recip<T>(r.delta + cx * kappa_of<T>(clx) + cy * kappa_of<T>(cly));
+        }
       }
-      T ax1, ax2, ay1, ay2;
-      if constexpr (sizeof(T) == 4) {
-        ax1 = r.ax1;
-        ax2 = r.ax2;
-        ay1 = r.ay1;
-        ay2 = r.ay2;
-      } else {
-        const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
-        const bool solid = (r.code & kSolid) != 0;
-        ax1 = solid ? T(0) : T(class_a1(clx));
-        ax2 = solid ? T(0) : T(class_a2(clx));
-        ay1 = solid ? T(0) : T(class_a1(cly));
-        ay2 = solid ? T(0) : T(class_a2(cly));
+#pragma unroll
+      for (int u = 0; u < SUB; ++u) {
+        const T bx = fma(cax1[u], hp1, fma(cax2[u], hp2, cxw[u]));
+        const T h = fma(cx, bx, base[u]) * invv[u];
+        hp2 = hp1;
+        hp1 = h;
+        myr[(l0 + u) * RS + lane] = h;
       }
-      const T Rk = fma(r.D, em1, fma(r.C, v2, fma(r.B, v1, r.A)));
-      const T by = fma(ay1, hq1, fma(ay2, hq2, r.yw));
-      const T base = fma(cy, by, Rk);
-      T inv;
-      if (UNIF) {
-        inv = invt[((r.code >> kInvShift) & 15) * kLanes + lane];
-      } else {
-        const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
-        inv = recip<T>(r.delta + cx * kappa_of<T>(clx) + cy * kappa_of<T>(cly));
-      }
-      const T bx = fma(ax1, hp1, fma(ax2, hp2, r.xw));
-      const T h = fma(cx, bx, base) * inv;
-      hp2 = hp1;
-      hp1 = h;
-      myr[l * RS + lane] = h;
     }
+    // The next rows need only the ring: publish this step now, so that the per-chunk passes below
+    // (stored h, seams, wall fluxes, moments) stay off the wavefront's critical path.  The ring slot
+    // is not rewritten before the consumer two rows down has read it (checked at step t + 3).
+    __syncwarp();
+    if (lane == 0) st_release(&prog[w], t + 1);
     __syncwarp();
     // per-chunk passes over the ring: stored distribution, seams, incident wall fluxes, moments
     if (hout) {
@@ -300,15 +337,20 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
       }
     }
     {
+      // forward: incident flux sum |v_n| W h at cells owning a downstream wall face; adjoint: the
+      // transposed wall reads, sum 2 |v_a|/dx z at cells whose upstream neighbour is solid
       const uint32_t mycode = lane < cnt ? rs[lane].code : 0u;
-      unsigned incx = __ballot_sync(0xffffffffu, (mycode & kIncX) != 0);
-      unsigned incy = __ballot_sync(0xffffffffu, (mycode & kIncY) != 0);
+      const bool fx = ADJ ? (((mycode >> kClsXShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncX) != 0;
+      const bool fy = ADJ ? (((mycode >> kClsYShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncY) != 0;
+      unsigned incx = __ballot_sync(0xffffffffu, fx);
+      unsigned incy = __ballot_sync(0xffffffffu, fy);
+      const T weight_x = ADJ ? T(2) * cx : wnx, weight_y = ADJ ? T(2) * cy : wny;
       while (incx | incy) {
         const bool is_x = incx != 0;
         const int l = __ffs(is_x ? incx : incy) - 1;
         if (is_x) incx &= incx - 1;
         else incy &= incy - 1;
-        const T f = warp_sum<T>((is_x ? wnx : wny) * myr[l * RS + lane]);
+        const T f = warp_sum<T>((is_x ? weight_x : weight_y) * myr[l * RS + lane]);
         if (lane == 0) {
           const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
           atomicAdd(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
@@ -325,15 +367,16 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
         const T *wr = wts + m * RS;
         T sum = T(0);
         if constexpr (RS % 4 == 0 && sizeof(T) == 4) {
+          // packed FP32x2 FMAs: two interleaved partial sums
+          float2 s2a = make_float2(0.f, 0.f), s2b = make_float2(0.f, 0.f);
 #pragma unroll
           for (int k = 0; k < kLanes; k += 4) {
             const float4 a = *reinterpret_cast<const float4 *>(hr + k);
             const float4 b = *reinterpret_cast<const float4 *>(wr + k);
-            sum = fma(a.x, b.x, sum);
-            sum = fma(a.y, b.y, sum);
-            sum = fma(a.z, b.z, sum);
-            sum = fma(a.w, b.w, sum);
+            s2a = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), s2a);
+            s2b = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), s2b);
           }
+          sum = (s2a.x + s2b.x) + (s2a.y + s2b.y);
         } else {
 #pragma unroll
           for (int k = 0; k < kLanes; ++k) sum = fma(wr[k], hr[k], sum);
@@ -393,32 +436,31 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
             sd[(CW + l) * kLanes + lane] -= sshift;
           }
           if (q == 0)
-            run_chunk(std::integral_constant<int, 0>(), q, c, rs, myr, sd, kLanes, sd + CW * kLanes, kLanes);
+            run_chunk(std::integral_constant<int, 0>(), q, c, t, rs, myr, sd, kLanes, sd + CW * kLanes, kLanes);
           else
-            run_chunk(std::integral_constant<int, 0>(), q, c, rs, myr, pr1, RS, sd + CW * kLanes, kLanes);
+            run_chunk(std::integral_constant<int, 0>(), q, c, t, rs, myr, pr1, RS, sd + CW * kLanes, kLanes);
         } else {
           const int p0 = c * CW;
           const int i0 = xneg ? nx - 1 - p0 : p0;
           const int stride = xneg ? -2 * kLanes : 2 * kLanes;
           const T *s0 = seamy + i0 * 2 * kLanes + lane;
           if (q == 0)
-            run_chunk(std::integral_constant<int, 1>(), q, c, rs, myr, s0 + kLanes, stride, s0, stride);
+            run_chunk(std::integral_constant<int, 1>(), q, c, t, rs, myr, s0 + kLanes, stride, s0, stride);
           else
-            run_chunk(std::integral_constant<int, 2>(), q, c, rs, myr, pr1, RS, s0 + kLanes, stride);
+            run_chunk(std::integral_constant<int, 2>(), q, c, t, rs, myr, pr1, RS, s0 + kLanes, stride);
         }
       } else {
-        run_chunk(std::integral_constant<int, 0>(), q, c, rs, myr, pr1, RS, pr2, RS);
+        run_chunk(std::integral_constant<int, 0>(), q, c, t, rs, myr, pr1, RS, pr2, RS);
       }
       __syncwarp();
-      if (lane == 0) st_release(&prog[w], t + 1);
     }
   }
   if (lane == 0) st_release(&prog[w], INT_MAX / 2);  // no more rows: never wait on this warp again
 }
 
-template <typename T, bool UNIF, int CW>
+template <typename T, bool UNIF, int CW, bool ADJ>
 cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
-  auto kern = sweep_kernel<T, UNIF, CW>;
+  auto kern = sweep_kernel<T, UNIF, CW, ADJ>;
   const size_t smem = layout<T>(L.warps, CW).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -426,14 +468,14 @@ cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-template <typename T, bool UNIF>
+template <typename T, bool UNIF, bool ADJ>
 cudaError_t launch_cw(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   switch (L.cw) {
-    case 1: return launch<T, UNIF, 1>(L, nblocks, stream);
-    case 2: return launch<T, UNIF, 2>(L, nblocks, stream);
-    case 4: return launch<T, UNIF, 4>(L, nblocks, stream);
-    case 8: return launch<T, UNIF, 8>(L, nblocks, stream);
-    case 16: return launch<T, UNIF, 16>(L, nblocks, stream);
+    case 1: return launch<T, UNIF, 1, ADJ>(L, nblocks, stream);
+    case 2: return launch<T, UNIF, 2, ADJ>(L, nblocks, stream);
+    case 4: return launch<T, UNIF, 4, ADJ>(L, nblocks, stream);
+    case 8: return launch<T, UNIF, 8, ADJ>(L, nblocks, stream);
+    case 16: return launch<T, UNIF, 16, ADJ>(L, nblocks, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -6,8 +6,13 @@ namespace dvm {
 size_t sweep_smem_bytes_f64(int warps, int cw) { return sweep::layout<double>(warps, cw).total; }
 
 cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
-  return uniform_delta ? sweep::launch_cw<double, true>(L, nblocks, stream)
-                       : sweep::launch_cw<double, false>(L, nblocks, stream);
+  return uniform_delta ? sweep::launch_cw<double, true, false>(L, nblocks, stream)
+                       : sweep::launch_cw<double, false, false>(L, nblocks, stream);
+}
+
+cudaError_t launch_sweep_adjoint_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  return uniform_delta ? sweep::launch_cw<double, true, true>(L, nblocks, stream)
+                       : sweep::launch_cw<double, false, true>(L, nblocks, stream);
 }
 
 size_t sweep_smem_bytes(bool fp64, int warps, int cw) {
@@ -16,6 +21,11 @@ size_t sweep_smem_bytes(bool fp64, int warps, int cw) {
 
 cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   return fp64 ? launch_sweep_f64(uniform_delta, L, nblocks, stream) : launch_sweep_f32(uniform_delta, L, nblocks, stream);
+}
+
+cudaError_t launch_sweep_adjoint(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  return fp64 ? launch_sweep_adjoint_f64(uniform_delta, L, nblocks, stream)
+              : launch_sweep_adjoint_f32(uniform_delta, L, nblocks, stream);
 }
 
 }  // namespace dvm

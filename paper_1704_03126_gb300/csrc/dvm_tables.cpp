@@ -172,6 +172,19 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
         }
         const uint32_t clx = (code >> kClsXShift) & 3u, cly = (code >> kClsYShift) & 3u;
         code |= (clx * 3u + cly) << kInvShift;
+        // transposed stencil: which forward-downstream cells read this one, and with what weight
+        {
+          const uint32_t t1 = solid(i + sx, j) ? 0u : (solid(i - sx, j) ? 1u : 2u);
+          const bool t2 = !solid(i + sx, j) && !solid(i + 2 * sx, j);
+          code |= t1 << kAdjT1XShift;
+          if (t2) code |= kAdjT2X;
+        }
+        {
+          const uint32_t t1 = solid(i, j + sy) ? 0u : (solid(i, j - sy) ? 1u : 2u);
+          const bool t2 = !solid(i, j + sy) && !solid(i, j + 2 * sy);
+          code |= t1 << kAdjT1YShift;
+          if (t2) code |= kAdjT2Y;
+        }
         G.code4[(size_t)cell * 4 + q] = code;
       }
     }

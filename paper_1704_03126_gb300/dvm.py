@@ -81,6 +81,7 @@ def lib():
         L.dvm_batch_kernels_per_sweep.restype = I
         L.dvm_batch_destroy.argtypes = [P]
         L.dvm_moments.argtypes = [ctypes.POINTER(Quad), P, P, I, D, P, P, P]
+        L.dvm_adjoint.argtypes = [P, D, I, P, ctypes.POINTER(D), ctypes.POINTER(I)]
         L.dvm_moments_noalloc.argtypes = [ctypes.POINTER(Quad), P, P, I, D, P, P, P]
         L.dvm_last_error.argtypes = [P]
         L.dvm_last_error.restype = ctypes.c_char_p
@@ -91,7 +92,7 @@ def lib():
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
                      "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
-                     "dvm_moments_noalloc"):
+                     "dvm_moments_noalloc", "dvm_adjoint"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -184,6 +185,15 @@ class Solver:
         self._check(lib().dvm_get_info(self._ctx, ctypes.byref(inf)))
         return dict(iterations=inf.iterations, eps=inf.eps, est=inf.est, mass_shift=inf.mass_shift, Q=inf.Q,
                     status=inf.status)
+
+    def adjoint(self, tol=1e-10, max_iter=100000):
+        """dQ/d delta_c at the current forward state: (grad [ny][nx], F sum z v1, adjoint sweeps)."""
+        g = np.empty(self.shape)
+        qid = ctypes.c_double()
+        it = ctypes.c_int()
+        st = lib().dvm_adjoint(self._ctx, float(tol), int(max_iter), _ptr(g), ctypes.byref(qid), ctypes.byref(it))
+        self._check(st, (DVM_OK, DVM_ENOCONV))
+        return g, qid.value, it.value
 
     def distribution(self, ks):
         ks = np.ascontiguousarray(ks, dtype=np.int32)

@@ -1,0 +1,87 @@
+"""GPU adjoint (dvm_adjoint, transposed sweeps through the C ABI) against the FP64 oracle's adjoint of
+the same projected iteration, the forward/adjoint identity Q = F sum z v1, and central differences of
+GPU forward solves."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_03126_gb300 import build as dvm_build
+from paper_1704_03126_gb300 import dvm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    dvm_build.build()
+    return dvm.lib()
+
+
+def _block(nx, ny):
+    m = np.zeros((ny, nx), np.uint8)
+    m[ny // 3: ny // 3 + 3, nx // 2: nx // 2 + 4] = 1
+    return m
+
+
+CASES = [
+    ("plates_gh8", inputs.plates_mask(4, 16), True, False, 0.7, ("gh", 8, 0.0)),
+    ("rough24_nc8", inputs.rough_channel_mask(24), True, False, 1.5, ("nc", 8, 4.0)),
+    ("block_periodic_cubic10", _block(20, 16), True, True, 1.0, ("cubic", 10, 4.0)),
+    ("porous40_cubic12", inputs.porous_disks_mask(40, 0.6, 4, 6, seed=5)[0], True, True, 2.0, ("cubic", 12, 4.0)),
+    ("closed_box_nc8", _block(12, 12), False, False, 1.0, ("nc", 8, 4.0)),
+]
+
+
+def _delta_field(mask, base, seed):
+    rng = np.random.default_rng(seed)
+    return base * rng.uniform(0.5, 1.5, size=mask.shape)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_gradient_matches_oracle(case):
+    name, mask, px, py, delta, quad = case
+    d = _delta_field(mask, delta, 3)
+    sol = dvm.Solver(mask, px, py, delta=delta, quad=quad, precision="fp64", store_distribution=True)
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=200000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=200000)
+    p = oracle.Problem.make(mask, px, py, d, quad)
+    ref = oracle.solve(p, tol=1e-13, max_iter=200000)
+    g_ref, q_ref_id, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=200000)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale, np.abs(grad - g_ref).max() / scale
+    q, _ = sol.flowrate()
+    assert abs(q_id - q) < 1e-9 * abs(q)
+    assert np.all(grad[mask == 1] == 0.0)
+
+
+def test_adjoint_matches_central_differences_of_gpu_solves():
+    mask = inputs.rough_channel_mask(16)
+    quad = ("nc", 8, 4.0)
+    d = _delta_field(mask, 1.0, 9)
+    sol = dvm.Solver(mask, True, False, delta=1.0, quad=quad, precision="fp64", store_distribution=True)
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-14, max_iter=200000)
+    grad, _, _ = sol.adjoint(tol=1e-13, max_iter=200000)
+    gas = np.flatnonzero(mask.ravel() == 0)
+    for cell in gas[[0, 17, 60, len(gas) - 1]]:
+        step = 1e-4 * d.ravel()[cell]
+        qs = []
+        for sgn in (1, -1):
+            dd = d.copy().ravel()
+            dd[cell] += sgn * step
+            s = dvm.Solver(mask, True, False, delta=1.0, quad=quad, precision="fp64")
+            s.set_delta_field(dd.reshape(mask.shape))
+            s.solve(tol=1e-14, max_iter=200000)
+            qs.append(s.flowrate()[0])
+        fd = (qs[0] - qs[1]) / (2 * step)
+        assert abs(fd - grad.ravel()[cell]) < 1e-6 * np.abs(grad).max()
+
+
+def test_adjoint_requires_stored_distribution():
+    sol = dvm.Solver(inputs.plates_mask(4, 8), True, False, kn=1.0, quad=("gh", 4, 0.0))
+    sol.solve(tol=1e-10)
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.adjoint()
+    assert ei.value.status == dvm.DVM_ESTATE

