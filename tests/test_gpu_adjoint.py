@@ -85,3 +85,31 @@ def test_adjoint_requires_stored_distribution():
     with pytest.raises(dvm.DvmError) as ei:
         sol.adjoint()
     assert ei.value.status == dvm.DVM_ESTATE
+
+
+def test_autograd_flow_rate_backward():
+    import torch
+
+    from paper_1704_03126_gb300.autograd import flow_rate
+
+    mask = inputs.porous_disks_mask(32, 0.65, 3, 5, seed=4)[0]
+    quad = ("cubic", 8, 4.0)
+    sol = dvm.Solver(mask, True, True, delta=1.0, quad=quad, precision="fp64", store_distribution=True)
+    d0 = _delta_field(mask, 1.2, 11)
+    delta = torch.tensor(d0, dtype=torch.float64, device="cuda", requires_grad=True)
+    q = flow_rate(delta, sol, tol=1e-13)
+    q.backward()
+    g_auto = delta.grad.cpu().numpy()
+    # the same gradient from the oracle's adjoint
+    p = oracle.Problem.make(mask, True, True, d0, quad)
+    ref = oracle.solve(p, tol=1e-13, max_iter=200000)
+    g_ref, _, _, _ = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=200000)
+    assert abs(q.item() - ref["Q"]) < 1e-10 * abs(ref["Q"])
+    assert np.abs(g_auto - g_ref).max() < 1e-8 * np.abs(g_ref).max()
+    # one directional derivative along a random direction
+    rng = np.random.default_rng(2)
+    dirn = rng.standard_normal(mask.shape) * (mask == 0)
+    eps = 1e-5
+    qp = flow_rate(torch.tensor(d0 + eps * dirn, device="cuda"), sol, tol=1e-14).item()
+    qm = flow_rate(torch.tensor(d0 - eps * dirn, device="cuda"), sol, tol=1e-14).item()
+    assert abs((qp - qm) / (2 * eps) - float((g_auto * dirn).sum())) < 1e-6 * np.abs(g_auto).sum()
