@@ -1,12 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the DVM source iteration (linearized BGK, arXiv:1704.03126 Sec. II.A) on GB300.
 
-Workload: force-driven flow through the rough channel -- 128 x 128 cells, periodic along x1, diffuse
-plates with one 26 x 32 block per wall, 32 x 32 trapezoid velocities on [-5, 5]^2 -- at Kn = 0.1, 1
-and 10, the three instances advanced together.  One step = one source iteration of all three
-(transport sweep with fused moments and wall fluxes, mass projection, residual, flow rate), i.e.
-3 x 14720 gas cells x 1024 velocities = 45.2 M cell-velocity updates.
+Default workload (--workload rough): force-driven flow through the rough channel -- 128 x 128 cells,
+periodic along x1, diffuse plates with one 26 x 32 block per wall, 32 x 32 trapezoid velocities on
+[-5, 5]^2 -- at Kn = 0.1, 1 and 10, the three instances advanced together.  One step = one source
+iteration of all three (transport sweep with fused moments and wall fluxes, mass projection,
+residual, flow rate), i.e. 3 x 14720 gas cells x 1024 velocities = 45.2 M cell-velocity updates.
 
+Other workloads, one JSON line each:
+  porous   periodic disk medium 256 x 256 (porosity 0.6, radii 8-20), cubic 48 x 48 velocities,
+           Kn = 0.05, 0.5, 5 advanced together (FP32 storage).
+  batched  64 mixed instances (sides 64-256, rough or porous, Kn log-uniform in [0.01, 10], cubic
+           16-48 velocities) in one launch per kernel, sweep kernel picked by the autotuner;
+           compared with 64 plain solves.
+  adjoint  porous 256 x 256 (porosity 0.5), cubic 32 x 32, Kn = 1, FP64: one step = one transposed
+           (adjoint) sweep; gradient checked against central differences of forward solves.
+
+The sweep kernel of every launch is chosen by the library's autotuner before the timed region.
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
 """
 from __future__ import annotations
@@ -27,7 +37,14 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 KNS = (0.1, 1.0, 10.0)
-METRIC = "DVM cell-velocity updates/s (rough channel 128x128, 32x32 velocities, Kn 0.1/1/10)"
+POROUS_KNS = (0.05, 0.5, 5.0)
+METRICS = {
+    "rough": "DVM cell-velocity updates/s (rough channel 128x128, 32x32 velocities, Kn 0.1/1/10)",
+    "porous": "DVM cell-velocity updates/s (porous 256x256 phi 0.6, cubic 48x48 velocities, Kn 0.05/0.5/5)",
+    "batched": "DVM cell-velocity updates/s (64 mixed instances, one batched launch per kernel)",
+    "adjoint": "adjoint sweep cell-velocity updates/s (porous 256x256 phi 0.5, cubic 32x32, Kn 1, FP64)",
+}
+METRIC = METRICS["rough"]
 UNIT = "updates/s"
 # FP32 / FP64 operations per interior cell-velocity update of the sweep kernel:
 # right-hand side 3 FMA, two upwind combinations 2 x (FMA + MUL), update 2 FMA + MUL, moments 4 FMA
@@ -46,23 +63,63 @@ def parse():
     ap.add_argument("--single", action="store_true", help="time only the selected precision")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
                     help="keep warming up for at least this long (clock sampling); 0 for profiling")
+    ap.add_argument("--workload", default="rough", choices=sorted(METRICS))
+    ap.add_argument("--schedule", default="autotune",
+                    help="sweep kernel: autotune, rows, columns1, columns2, columns4")
+    ap.add_argument("--fd-cells", type=int, default=64, help="adjoint workload: cells checked by central differences")
     return ap.parse_args()
 
 
-def workload_config(precision):
+WORKLOAD_TEXT = {
+    "rough": "rough channel 128x128 (blocks 26x32 on both walls, x1 periodic), 32x32 trapezoid velocities "
+             "|v|<=5, Kn 0.1/1/10 batched; force-driven (F=1)",
+    "porous": "periodic disk medium 256x256 (seeded non-overlapping disks, radii 8-20, porosity 0.6), cubic "
+              "48x48 velocities |v|<=4, Kn 0.05/0.5/5 batched; force-driven (F=1)",
+    "batched": "64 seeded instances: side 64-256, rough or porous, Kn log-uniform 0.01-10, cubic 16-48 "
+               "velocities; one launch per kernel per sweep",
+    "adjoint": "periodic disk medium 256x256 (porosity 0.5, seed 1), cubic 32x32 velocities, Kn 1, FP64; "
+               "transposed sweeps of the adjoint iteration at the converged forward state",
+}
+
+
+def workload_config(precision, workload="rough"):
     return {
-        "workload": "rough channel 128x128 (blocks 26x32 on both walls, x1 periodic), 32x32 trapezoid "
-                    "velocities |v|<=5, Kn 0.1/1/10 batched; force-driven (F=1)",
-        "instances_per_step": len(KNS),
+        "workload": WORKLOAD_TEXT[workload],
+        "instances_per_step": len(instances(workload)),
         "precision": "fp32 store / fp64 accumulate" if precision == "fp32" else "fp64",
         "l2": "flushed between timed steps (256 MiB write)",
         "data": "synthetic staircase geometry",
     }
 
 
-def instances():
+_INSTANCES = {}
+
+
+def instances(workload="rough"):
     from paper_1704_03126_gb300 import inputs
-    return [inputs.rough_instance(kn) for kn in KNS]
+    if workload not in _INSTANCES:
+        if workload == "rough":
+            _INSTANCES[workload] = [inputs.rough_instance(kn) for kn in KNS]
+        elif workload == "porous":
+            _INSTANCES[workload] = [inputs.porous_instance(kn) for kn in POROUS_KNS]
+        elif workload == "batched":
+            _INSTANCES[workload] = inputs.batched_instances(64)
+        else:
+            _INSTANCES[workload] = [inputs.porous_instance(1.0, nv=32, porosity=0.5, seed=1)]
+    return _INSTANCES[workload]
+
+
+def apply_schedule(batch, spec):
+    """Pick the batch's sweep kernel: the library autotuner (5 timed sweeps per candidate) or a fixed one."""
+    if spec == "autotune":
+        kind, v, ms = batch.autotune(5)
+        return {"kernel": kind, "threads_per_column": v, "tuned_sweep_ms": ms, "by": "autotuner"}
+    if spec == "rows":
+        batch.set_schedule("rows", 0)
+    else:
+        batch.set_schedule("columns", int(spec[len("columns"):]))
+    kind, v = batch.schedule()
+    return {"kernel": kind, "threads_per_column": v, "by": "fixed"}
 
 
 def updates_per_step(insts):
@@ -125,12 +182,12 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
-    insts = instances()
+    insts = instances(args.workload)
     upd = updates_per_step(insts)
 
     def make(precision):
-        return [dvm.Solver(inst.mask, True, False, kn=inst.kn, quad=inst.quad, precision=precision,
-                           stream=stream.cuda_stream) for inst in insts]
+        return [dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, kn=inst.kn, quad=inst.quad,
+                           precision=precision, stream=stream.cuda_stream) for inst in insts]
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -165,10 +222,13 @@ def run_ours(args, rank, world, local_rank):
     results = {}
     sampler = ClockSampler(local_rank)
     sampler.start()
-    precisions = [args.precision] + ([] if args.single else ["fp64" if args.precision == "fp32" else "fp32"])
+    single = args.single or args.workload != "rough"
+    precisions = [args.precision] + ([] if single else ["fp64" if args.precision == "fp32" else "fp32"])
+    schedules = {}
     for precision in precisions:
         solvers = make(precision)
         batch = dvm.Batch(solvers)
+        schedules[precision] = apply_schedule(batch, args.schedule)
         total_ms, sweep_ms, fin_ms, wsteps = timed_steps(batch, args.steps, args.warmup)
         if world > 1:
             t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -195,21 +255,25 @@ def run_ours(args, rank, world, local_rank):
     def roofline(prec):
         r = results[prec]
         achieved = FLOPS_PER_UPDATE * upd / (r["sweep_ms"] / 1e3) / 1e12
+        sc = schedules[prec]
+        kname = ("sweep_kernel" if sc["kernel"] == "rows"
+                 else f"cols_kernel, {sc['threads_per_column']} thread(s) per column")
         return {"bound": "alu", "achieved": achieved, "peak": peak[prec], "unit": "TFLOP/s",
                 "frac": achieved / peak[prec], "traffic": None,
-                "kernel": f"sweep_kernel ({prec})", "flops_per_update": FLOPS_PER_UPDATE,
+                "kernel": f"{kname} ({prec})", "schedule": sc, "flops_per_update": FLOPS_PER_UPDATE,
                 "peak_note": ("FP32 FMA units x max SM clock" if prec == "fp32"
                               else "FP64 units (2 FMA/SM/clk) x max SM clock") + ", derived (of unit counts)",
                 "sweep_ms": r["sweep_ms"], "finalize_ms": r["fin_ms"]}
 
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic", "config": workload_config(args.precision),
+        "data": "synthetic", "config": workload_config(args.precision, args.workload),
         "roofline": roofline(args.precision),
         "clocks": clocks,
-        "gpu_launches": args.steps * (main["kernels_per_step"] + len(KNS)),
+        # per step: the sweep and two finalize kernels, and one arming kernel per instance
+        "gpu_launches": args.steps * (main["kernels_per_step"] + len(insts)),
     }
     other = "fp64" if args.precision == "fp32" else "fp32"
     if other in results:
@@ -223,10 +287,11 @@ def run_ours(args, rank, world, local_rank):
     }
 
     if not args.skip_extras:
-        out["e2e"] = e2e(args, insts, stream, dvm, torch)
-        out["converge"] = converge(results, insts, torch)
+        big = args.workload == "batched"
+        out["e2e"] = e2e(args, insts, stream, dvm, torch, sweeps=10 if big else 50, reps=1 if big else 3)
+        out["converge"] = converge(results, insts, torch, max_iter=20000 if big else 200000)
     if rank == 0 and not args.skip_extras:
-        out["cpu_baseline"] = cpu_baseline(insts)
+        out["cpu_baseline"] = cpu_baseline(insts, args.workload)
     for r in results.values():
         r["batch"].close()
         for s in r["solvers"]:
@@ -242,8 +307,8 @@ def e2e(args, insts, stream, dvm, torch, sweeps=50, reps=3):
     h2d = d2h = 0
     for _ in range(reps):
         for inst in insts:
-            s = dvm.Solver(inst.mask, True, False, kn=inst.kn, quad=inst.quad, precision=args.precision,
-                           stream=stream.cuda_stream)
+            s = dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, kn=inst.kn, quad=inst.quad,
+                           precision=args.precision, stream=stream.cuda_stream)
             s.iterate(sweeps)
             q, _ = s.flowrate()
             f = s.fields()
@@ -259,8 +324,9 @@ def e2e(args, insts, stream, dvm, torch, sweeps=50, reps=3):
                     f"dvm_destroy; {reps} repetitions"}
 
 
-def converge(results, insts, torch, tol=None):
-    """Time to converge: each instance alone (plain) vs the three batched, from h = 0."""
+def converge(results, insts, torch, max_iter=200000):
+    """Time to converge: each instance alone (plain, automatic sweep kernel) vs all of them batched
+    (the timed launch), from h = 0, to the same tolerance."""
     out = {}
     for prec, r in results.items():
         t = 1e-10 if prec == "fp64" else 1e-6
@@ -270,27 +336,35 @@ def converge(results, insts, torch, tol=None):
             s.reset()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st, iters, est = s.solve(tol=t, max_iter=200000, raise_on_noconv=False)
+            st, iters, est = s.solve(tol=t, max_iter=max_iter, raise_on_noconv=False)
             dt = time.perf_counter() - t0
             t_plain += dt
-            per[f"kn{inst.kn:g}"] = {"iterations": iters, "seconds": dt, "Q": s.flowrate()[0], "status": int(st)}
+            per[inst.name] = {"iterations": iters, "seconds": dt, "Q": s.flowrate()[0], "status": int(st)}
         for s in r["solvers"]:
             s.reset()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r["batch"].run(tol=t, max_iter=200000)
+        status = r["batch"].run(tol=t, max_iter=max_iter)
         t_batch = time.perf_counter() - t0
-        out[prec] = {"tol": t, "plain": per, "plain_total_s": t_plain, "batched_total_s": t_batch,
-                     "batched_Q": [s.flowrate()[0] for s in r["solvers"]]}
+        bq = [s.flowrate()[0] for s in r["solvers"]]
+        pq = [v["Q"] for v in per.values()]
+        out[prec] = {"tol": t, "max_iter": max_iter, "plain_total_s": t_plain, "batched_total_s": t_batch,
+                     "converged_plain": sum(v["status"] == 0 for v in per.values()),
+                     "converged_batched": int((np.asarray(status) == 0).sum()), "instances": len(insts),
+                     "max_rel_dQ_batched_vs_plain": max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(bq, pq))}
+        if len(insts) <= 4:
+            out[prec]["plain"] = per
+            out[prec]["batched_Q"] = bq
     return out
 
 
-def cpu_baseline(insts, budget_s=12.0):
-    """The FP64 oracle as it stands, on the host cores: sweeps of the Kn = 1 instance."""
+def cpu_baseline(insts, workload="rough", budget_s=12.0):
+    """The FP64 oracle as it stands, on the host cores: sweeps of one instance of the workload (the
+    middle Knudsen number, or the first batched instance)."""
     import oracle
 
-    inst = insts[1]
-    p = oracle.Problem.make(inst.mask, True, False, oracle.delta_from_kn(inst.kn), inst.quad)
+    inst = insts[1] if len(insts) == 3 else insts[0]
+    p = oracle.Problem.make(inst.mask, inst.periodic_x, inst.periodic_y, oracle.delta_from_kn(inst.kn), inst.quad)
     K = inst.quad[1] ** 2
     h = np.zeros((K, p.ny, p.nx))
     t0 = time.perf_counter()
@@ -303,8 +377,120 @@ def cpu_baseline(insts, budget_s=12.0):
     upd = int((inst.mask == 0).sum()) * K * n
     return {"value": upd / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
             "kind": "oracle",
-            "sample": f"{n} source-iteration sweeps of the Kn=1 rough-channel instance (FP64, C + OpenMP), "
-                      f"{dt:.1f} s"}
+            "sample": f"{n} source-iteration sweeps of instance {inst.name} (FP64, C + OpenMP), {dt:.1f} s"}
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """Adjoint workload: converged FP64 forward state, then the adjoint iteration (transposed sweeps)
+    timed with CUDA events on the solver's stream; checked against central differences of forward
+    solves (cells drawn with SplitMix64 seed 7, step 1e-4 delta) and one directional difference over
+    all sampled cells at once."""
+    import torch
+
+    from paper_1704_03126_gb300 import dvm, inputs
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    inst = instances("adjoint")[0]
+    upd = updates_per_step([inst])
+    delta = dvm.kn_to_delta(inst.kn)
+    tol = 1e-12
+
+    def solver(store):
+        s = dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, delta=delta, quad=inst.quad,
+                       precision="fp64", store_distribution=store, stream=stream.cuda_stream)
+        if args.schedule != "autotune":
+            s.set_schedule(*(("rows", 0) if args.schedule == "rows" else ("columns", int(args.schedule[7:]))))
+        return s
+
+    sol = solver(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sol.solve(tol=tol, max_iter=100000)  # warm-up (graphs, clocks)
+    sol.reset()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st, f_iters, _ = sol.solve(tol=tol, max_iter=100000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    q0 = sol.flowrate()[0]
+    sol.adjoint(tol=tol, max_iter=100000)  # warm-up of the adjoint graph
+    torch.cuda.synchronize()
+    e0.record(stream)
+    grad, q_id, a_iters = sol.adjoint(tol=tol, max_iter=100000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    sched = sol.schedule()
+
+    # central differences: all perturbed solves in one batch
+    cells = inputs.sample_gas_cells(inst.mask, args.fd_cells, seed=7)
+    base = np.where(inst.mask == 0, delta, 0.0)
+    rng = np.random.default_rng(7)
+    dirn = np.zeros(inst.mask.size)
+    dirn[cells] = rng.standard_normal(len(cells))
+    fields = []
+    for c in cells:
+        for sgn in (1.0, -1.0):
+            d = base.copy().ravel()
+            d[c] += sgn * 1e-4 * delta
+            fields.append(d.reshape(inst.mask.shape))
+    eps_dir = 1e-4
+    for sgn in (1.0, -1.0):
+        fields.append((base.ravel() * (1.0 + sgn * eps_dir * dirn)).reshape(inst.mask.shape))
+    qs = []
+    t0 = time.perf_counter()
+    chunk = 32
+    for k in range(0, len(fields), chunk):
+        sols = [solver(False) for _ in fields[k:k + chunk]]
+        for s, f in zip(sols, fields[k:k + chunk]):
+            s.set_delta_field(f)
+        dvm.batch_solve(sols, tol=1e-14, max_iter=100000)
+        qs.extend(s.flowrate()[0] for s in sols)
+        for s in sols:
+            s.close()
+    fd_s = time.perf_counter() - t0
+    qs = np.array(qs)
+    fd = (qs[0:2 * len(cells):2] - qs[1:2 * len(cells):2]) / (2e-4 * delta)
+    g = grad.ravel()[cells]
+    gscale = np.abs(grad).max()
+    dir_fd = (qs[-2] - qs[-1]) / (2 * eps_dir)
+    dir_adj = float((grad.ravel() * base.ravel() * dirn).sum())
+    value = a_iters * upd / (adj_ms / 1e3)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak64 = 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_UPDATE * value / 1e12
+    out = {
+        "metric": METRICS["adjoint"], "value": value, "unit": UNIT, "n_gpus": world, "steps": a_iters,
+        "warmup": 1, "ms_per_step": adj_ms / a_iters, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config("fp64", "adjoint"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                     "frac": achieved / peak64, "traffic": None,
+                     "kernel": f"transposed sweep, {sched[0]} kernel (fp64), whole adjoint iteration incl. bookkeeping",
+                     "flops_per_update": FLOPS_PER_UPDATE},
+        "clocks": clocks,
+        # per adjoint sweep: transposed sweep, seam sums, two finalize kernels; plus arm, reset, gradient
+        "gpu_launches": 4 * a_iters + 3,
+        "adjoint_vs_plain": {"tol": tol, "forward_iterations": f_iters, "forward_ms": fwd_ms,
+                             "adjoint_iterations": a_iters, "adjoint_ms": adj_ms,
+                             "forward_updates_per_s": f_iters * upd / (fwd_ms / 1e3),
+                             "Q": q0, "Q_identity_rel_err": abs(q_id - q0) / abs(q0)},
+        "fd_check": {"cells": int(len(cells)), "step": "1e-4 delta", "forward_tol": 1e-14,
+                     "max_abs_err_over_max_grad": float(np.abs(fd - g).max() / gscale),
+                     "median_rel_err": float(np.median(np.abs(fd - g) / np.maximum(np.abs(g), 1e-300))),
+                     "directional_rel_err": abs(dir_fd - dir_adj) / abs(dir_adj), "seconds": fd_s,
+                     "solves": len(fields)},
+    }
+    sol.close()
+    return out
 
 
 # ------------------------------------------------------------------------------ reference arm
@@ -313,8 +499,8 @@ def run_reference(args):
     """The oracle timed as it stands on the host cores: one step = one sweep of each instance."""
     import oracle
 
-    insts = instances()
-    probs = [oracle.Problem.make(i.mask, True, False, oracle.delta_from_kn(i.kn), i.quad) for i in insts]
+    insts = instances(args.workload if args.workload != "adjoint" else "rough")
+    probs = [oracle.Problem.make(i.mask, i.periodic_x, i.periodic_y, oracle.delta_from_kn(i.kn), i.quad) for i in insts]
     states = [np.zeros((i.quad[1] ** 2, p.ny, p.nx)) for i, p in zip(insts, probs)]
     upd = updates_per_step(insts)
     for _ in range(args.warmup):
@@ -328,12 +514,14 @@ def run_reference(args):
     value = args.steps * upd / dt
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "metric": METRICS[args.workload if args.workload != "adjoint" else "rough"], "value": value,
+        "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config("fp64"), "impl": "reference",
+        "config": workload_config("fp64", args.workload if args.workload != "adjoint" else "rough"),
+        "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} steps, each one FP64 oracle sweep of all three instances"},
+                         "sample": f"{args.steps} steps, each one FP64 oracle sweep of every instance"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -360,7 +548,7 @@ def main():
     if world > 1:
         import torch
         torch.distributed.barrier()
-    out = run_ours(args, rank, world, local_rank)
+    out = (run_adjoint if args.workload == "adjoint" else run_ours)(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

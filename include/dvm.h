@@ -74,10 +74,20 @@ typedef struct {
   int precision;              /* dvm_precision */
   double force;               /* body-force source coefficient F along x1 (1 for the paper's Poiseuille flow) */
   int store_distribution;     /* 1 = also keep h in device memory (needed by dvm_distribution) */
-  int sweep_warps;            /* upper bound on rows in flight (warps) per sweep block, 1..16;
-                                 0 = 16.  The chunk width is the smallest of 1, 2, 4, 8, 16 cells
-                                 with ceil(nx / width) rows within the bound; nx <= 256. */
+  int sweep_warps;            /* row sweep only: upper bound on rows in flight (warps) per sweep block,
+                                 1..16; 0 = 16.  The chunk width is the smallest of 1, 2, 4, 8, 16
+                                 cells with ceil(nx / width) rows within the bound. */
 } dvm_params;
+
+/* The transport sweep kernel (both compute the same update; see dvm_set_schedule):
+ *   DVM_SWEEP_ROWS     a thread block per group of 32 velocities, lanes = velocities, warps = rows in
+ *                      flight of a row wavefront; nx <= 256.
+ *   DVM_SWEEP_COLUMNS  threads = grid columns walking an anti-diagonal wavefront, each with 8 (FP32)
+ *                      or 4 (FP64) velocities; `threads_per_column` (1, 2 or 4) threads share a
+ *                      column, so a block holds 8, 16 or 32 (FP32) velocities; nx * threads_per_column
+ *                      <= 512.
+ *   DVM_SWEEP_AUTO     columns, with the most threads per column that fit. */
+typedef enum { DVM_SWEEP_AUTO = 0, DVM_SWEEP_ROWS = 1, DVM_SWEEP_COLUMNS = 2 } dvm_sweep_kind;
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
  * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape. */
@@ -145,6 +155,14 @@ dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info);
  * adjoint state (about as much as the forward state plus one more distribution) on first use. */
 dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta, double *q_identity, int *iters);
 
+/* Choose the sweep kernel of the context's own solves and adjoint (dvm_sweep_kind; threads_per_column
+ * 0 = automatic, used by DVM_SWEEP_COLUMNS only).  DVM_EINVAL if the grid does not fit the choice.
+ * Results agree to rounding; speed differs with the grid width and the number of velocity groups.
+ * Default: DVM_SWEEP_AUTO.  Batches created later start from the first member's choice. */
+dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column);
+/* The resolved choice (kind is never DVM_SWEEP_AUTO; threads_per_column 0 for rows). */
+dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_column);
+
 /* Distribution h of selected velocities (needs store_distribution = 1).  ks: host int [nk] with
  * k = a * n + b for v = (x_a, x_b) on the 1D nodes in ascending order.  out: host double
  * [nk][ny][nx]; solid cells 0. */
@@ -174,6 +192,14 @@ dvm_status dvm_batch_iterate(dvm_batch *batch, int n);
 /* Device time of the last single sweep run by dvm_batch_iterate(batch, 1): the sweep kernel and the
  * two finalize kernels, in milliseconds (CUDA events recorded around them on the batch stream). */
 dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms);
+/* Re-plan the batch's sweep launch for another kernel (see dvm_set_schedule); state is kept. */
+dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_column);
+dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *threads_per_column);
+/* Autotuner: time every sweep kernel that fits the batch's grids (rows; columns with 1, 2, 4 threads
+ * per column) over `sweeps` single sweeps each (CUDA events, median), keep the fastest and return it
+ * (any output may be NULL; sweep_ms is its median sweep time).  The trial sweeps are ordinary source
+ * iterations: they advance every member's state. */
+dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *threads_per_column, float *sweep_ms);
 /* Kernel launches issued per sweep of the batch (sweep + finalize kernels). */
 int dvm_batch_kernels_per_sweep(const dvm_batch *batch);
 void dvm_batch_destroy(dvm_batch *batch);

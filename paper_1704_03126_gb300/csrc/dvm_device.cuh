@@ -1,9 +1,10 @@
 // dvm_device.cuh -- device-side data layout of libdvm (internal; not part of the C ABI).
 //
 // One "instance" is one geometry + Knudsen number + velocity grid.  The distribution h of an
-// instance is split into velocity groups of 32 velocities of one quadrant (sign(v1), sign(v2));
-// one thread block sweeps one group over the whole grid (lanes = velocities, warps = rows in
-// flight).  Several instances can share a launch (batched solves).
+// instance is split into velocity groups of 32 velocities of one quadrant (sign(v1), sign(v2)).
+// The row-wavefront sweep gives one thread block a group (lanes = velocities, warps = rows in
+// flight); the column sweep gives a block a group or a part of one (threads = grid columns, each
+// with a few velocities).  Several instances can share a launch (batched solves).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -141,11 +142,21 @@ struct InstanceDesc {
 // Launch descriptor shared by the kernels of one (possibly batched) iteration.
 struct LaunchDesc {
   const InstanceDesc *inst;  // device array [ninst]
-  const int *sweep_map;      // [sweep blocks]: instance << 16 | group
+  const int *sweep_map;      // [sweep blocks]: instance << 16 | part << 12 | group
   const int *fin_map;        // [finalize blocks]: instance << 16 | block within instance
   int ninst;
   int warps;                 // sweep warps per block: max over instances of ceil(nx / cw)
   int cw;                    // chunk width (cells per warp and step) of the sweep: 1, 2, 4, 8 or 16
+  int cols_v;                // 0: row-wavefront sweep; 1, 2, 4: column sweep with that many threads per
+                             // column (the block's velocity set is split among them)
 };
+
+#ifdef __CUDACC__
+// FP64 reduction into global memory without a return value (PTX red): the warp does not wait for the
+// L2 round trip that atomicAdd's returned old value would cost.
+__device__ __forceinline__ void red_add(double *addr, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;\n" ::"l"(__cvta_generic_to_global(addr)), "d"(v) : "memory");
+}
+#endif
 
 }  // namespace dvm

@@ -37,12 +37,49 @@ __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int 
 
 size_t sweep_smem_bytes(bool fp64, int warps, int cw);
 
+// Column sweep (dvm_sweep_cols.cuh): shared-memory layout -- per-pair velocity constants, the
+// 1/denominator table of the block's velocities and the 3-deep ring of column results.
+constexpr int kColsMaxThreads = 512;
+struct ColsSmemLayout {
+  size_t cst, inv, ring, recs, xseam, yseam, total;
+};
+// cell records are staged `depth` steps ahead: 5 (FP32, 48-byte records) or 4 (FP64, 64 bytes); the
+// x-seam values of a row sit in a ring of kColsSeamRows rows, the y-seam values of every column are
+// staged once at the start
+__host__ __device__ inline int cols_depth(int tsize) { return tsize == 4 ? 5 : 4; }
+constexpr int kColsSeamRows = 8;
+__host__ __device__ inline ColsSmemLayout cols_smem_layout(int V, int G, int ncol, int tsize) {
+  ColsSmemLayout L;
+  size_t off = 0;
+  auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const int VB = V * G;
+  L.cst = off;
+  off = align16(off + (size_t)VB * 8 * tsize);
+  L.inv = off;
+  off = align16(off + (size_t)kInvRows * VB * tsize);
+  L.ring = off;
+  off = align16(off + (size_t)3 * V * G * tsize * ncol);
+  L.recs = off;
+  off = align16(off + (size_t)cols_depth(tsize) * ncol * (tsize == 4 ? 48 : 64));
+  L.xseam = off;
+  off = align16(off + (size_t)kColsSeamRows * V * 2 * G * tsize);
+  L.yseam = off;
+  off = align16(off + (size_t)V * ncol * 2 * G * tsize);
+  L.total = off;
+  return L;
+}
+// velocities per thread of the column sweep
+inline int cols_g(bool fp64) { return fp64 ? 4 : 8; }
+size_t cols_smem_bytes(bool fp64, int v, int warps);
+
 // One source-iteration sweep of every instance in the launch (fused moments and wall fluxes).
 cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 cudaError_t launch_sweep_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 size_t sweep_smem_bytes_f32(int warps, int cw);
 size_t sweep_smem_bytes_f64(int warps, int cw);
+cudaError_t launch_sweep_cols_f32(bool uniform_delta, bool adjoint, const LaunchDesc &L, int nblocks, cudaStream_t stream);
+cudaError_t launch_sweep_cols_f64(bool uniform_delta, bool adjoint, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 // The transposed sweep of the adjoint iteration (launch over adjoint views of the instances).
 cudaError_t launch_sweep_adjoint(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 cudaError_t launch_sweep_adjoint_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);

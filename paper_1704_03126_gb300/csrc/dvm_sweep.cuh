@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
   constexpr int RS = Traits<T>::kRingStride;
   const int map = L.sweep_map[blockIdx.x];
   const InstanceDesc *__restrict__ D = L.inst + (map >> 16);
-  const int g = map & 0xffff;
+  const int g = map & 0xfff;
   DeviceState *st = D->state;
   if (*reinterpret_cast<volatile int *>(&st->done)) return;
 
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
         const T f = warp_sum<T>((is_x ? weight_x : weight_y) * myr[l * RS + lane]);
         if (lane == 0) {
           const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
-          atomicAdd(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
+          red_add(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
         }
       }
     }
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
         }
         const int p = p0 + l;
         const int i = xneg ? nx - 1 - p : p;
-        atomicAdd(&acc[(j * nx + i) * 4 + m], static_cast<double>(sum));
+        red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(sum));
       }
     }
   };

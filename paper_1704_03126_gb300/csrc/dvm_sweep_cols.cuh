@@ -1,0 +1,437 @@
+// dvm_sweep_cols.cuh -- the transport sweep with one thread per grid column (the "column" sweep),
+// shared by the FP32 and FP64, forward and adjoint translation units.
+//
+// It computes exactly the update of the row-wavefront sweep (dvm_sweep.cuh): Eq. (iteration) of
+// arXiv:1704.03126 (Sec. II.A) with second-order upwind differences, lagged periodic seams and the
+// diffuse wall values of the previous iterate, fused with the moments and incident wall fluxes.
+// Only the mapping differs.  A thread owns one column p of the grid (in the quadrant's sweep order)
+// and G velocities of the block's velocity set, and walks down its column one row per step: at step S
+// it updates cell (p, S - p), so the block advances along the anti-diagonals of the quadrant.  Every
+// upstream value is one or two steps old:
+//   y: h(p, q-1) and h(p, q-2) are the thread's own last two results (registers);
+//   x: h(p-1, q) and h(p-2, q) were written one and two steps ago by threads p-1 and p-2 into a
+//      3-deep shared-memory ring; one block barrier per step orders them.
+// The G velocities of a thread are independent, so the arithmetic runs on velocity pairs (packed
+// FP32x2 FMAs in FP32), and the cell's record is read once for G updates.  The V threads of a block
+// that share a column hold different velocities; their moment and wall-flux sums are combined with
+// warp shuffles and added to the FP64 accumulators with one atomic per value.  There are no
+// spin-waits: the only synchronisation is the per-step barrier, which every thread reaches.
+#pragma once
+#include <cstdint>
+
+#include "dvm_device.cuh"
+#include "dvm_kernels.h"
+
+namespace dvm {
+namespace cols {
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using T2 = float2;
+  using V16 = float4;  // 16-byte shared-memory vector: two velocity pairs
+  __device__ static __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+  __device__ static __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  __device__ static __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  __device__ static __forceinline__ float2 splat(float x) { return make_float2(x, x); }
+  __device__ static __forceinline__ float2 rcp2(float2 d) { return make_float2(1.0f / d.x, 1.0f / d.y); }
+  __device__ static __forceinline__ float2 pair(const float4 &v, int i) {
+    return i ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+  }
+  __device__ static __forceinline__ float4 pack(const float2 *p) { return make_float4(p[0].x, p[0].y, p[1].x, p[1].y); }
+};
+template <>
+struct Vec<double> {
+  using T2 = double2;
+  using V16 = double2;  // one velocity pair
+  __device__ static __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+  }
+  __device__ static __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+  __device__ static __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+  __device__ static __forceinline__ double2 splat(double x) { return make_double2(x, x); }
+  __device__ static __forceinline__ double2 rcp2(double2 d) { return make_double2(1.0 / d.x, 1.0 / d.y); }
+  __device__ static __forceinline__ double2 pair(const double2 &v, int) { return v; }
+  __device__ static __forceinline__ double2 pack(const double2 *p) { return p[0]; }
+};
+
+// velocities per thread: 8 in FP32 (4 packed pairs), 4 in FP64
+template <typename T>
+struct ColsG {
+  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
+};
+
+// per-pair constant fields in shared memory ([VB / 2][kCstFields] pairs)
+enum : int { kCV1 = 0, kCV2, kCE, kCCx, kCCy, kCWm, kCWr, kCPad, kCstFields };
+
+template <typename T>
+__host__ __device__ inline ColsSmemLayout layout(int V, int ncol) {
+  constexpr int G = ColsG<T>::value;
+  return cols_smem_layout(V, G, ncol, (int)sizeof(T));
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ADJ = false: the forward sweep.  ADJ = true: the transposed sweep of the adjoint iteration (see
+// dvm_sweep.cuh): reversed traversal, transposed weights t1, t2 from the record, right-hand side
+// W (A + B v1 + C v2 + D (|v|^2 - 1)) + |v1| W TX + |v2| W TY, unweighted moments, and
+// 2 |v_a|/dx z added to the wall adjoint flux of cells whose upstream neighbour is solid.
+template <typename T, bool ADJ, bool UNIF, int V>
+__global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) {
+  using Q = Vec<T>;
+  using T2 = typename Q::T2;
+  using V16 = typename Q::V16;
+  constexpr int G = ColsG<T>::value;
+  constexpr int CPW = kLanes / V;                 // columns per warp
+  constexpr int NP = G / 2;                       // velocity pairs per thread
+  constexpr int VB = V * G;                       // velocities per block
+  constexpr int NQ = G * (int)sizeof(T) / 16;     // 16-byte vectors per thread and column
+  constexpr int PPQ = 16 / (2 * (int)sizeof(T));  // pairs per 16-byte vector
+  constexpr int DEPTH = sizeof(T) == 4 ? 5 : 4;    // = cols_depth: record stages in flight
+  constexpr int SR = kColsSeamRows;                // rows of the staged x-seam ring (> DEPTH + 1)
+  static_assert(SR >= DEPTH + 2, "a staged seam row must outlive the two steps that read it");
+  static_assert(4 % V == 0, "V divides the four moments");
+
+  const int map = L.sweep_map[blockIdx.x];
+  const InstanceDesc *__restrict__ D = L.inst + (map >> 16);
+  const int g = map & 0xfff, sub = (map >> 12) & 0xf;
+  DeviceState *st = D->state;
+  if (*reinterpret_cast<volatile int *>(&st->done)) return;
+
+  const int nx = D->nx, ny = D->ny, ncell = D->ncell;
+  const bool px = D->periodic_x != 0, py = D->periodic_y != 0;
+  const int quad = g / D->groups_per_quadrant;
+  const bool xneg = ((quad & 1) != 0) != ADJ, yneg = ((quad & 2) != 0) != ADJ;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int v = lane / CPW;                       // velocity subset of this thread
+  const int p = w * CPW + (lane % CPW);           // column in sweep order
+  const int ncol = (blockDim.x >> 5) * CPW;
+  const int l0 = sub * VB + v * G;                // first velocity lane (within the group)
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ColsSmemLayout SL = layout<T>(V, ncol);
+  T *cstT = reinterpret_cast<T *>(smem + SL.cst);
+  const T2 *cst = reinterpret_cast<const T2 *>(smem + SL.cst);
+  T *invt = reinterpret_cast<T *>(smem + SL.inv);
+  V16 *ring = reinterpret_cast<V16 *>(smem + SL.ring);
+  SweepRec<T> *recs = reinterpret_cast<SweepRec<T> *>(smem + SL.recs);  // [DEPTH][ncol]
+  T *xsr = reinterpret_cast<T *>(smem + SL.xseam);  // [SR][V][2][G]: seam columns (nx-2, nx-1) of row q
+  T *ysr = reinterpret_cast<T *>(smem + SL.yseam);  // [V][ncol][2][G]: seam rows (ny-2, ny-1) of column p
+
+  for (size_t b = threadIdx.x; b < SL.total / 16; b += blockDim.x)
+    reinterpret_cast<float4 *>(smem)[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  {
+    const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes + sub * VB;
+    for (int t = threadIdx.x; t < VB * kCstFields; t += blockDim.x) {
+      const int vl = t % VB, f = t / VB;
+      const int fld = f == kCV1 ? kV1 : f == kCV2 ? kV2 : f == kCE ? kE2m1 : f == kCCx ? kCx : f == kCCy ? kCy
+                    : f == kCWm ? (ADJ ? kZ0 : kW0) : kW0;
+      cstT[((vl >> 1) * kCstFields + f) * 2 + (vl & 1)] = f == kCPad ? T(0) : vt[fld * kLanes + vl];
+    }
+    if (UNIF) {
+      const T *iv = static_cast<const T *>(D->inv_den) + (size_t)g * kInvRows * kLanes + sub * VB;
+      for (int t = threadIdx.x; t < kInvRows * VB; t += blockDim.x) invt[t] = iv[(t / VB) * kLanes + t % VB];
+    }
+  }
+  __syncthreads();
+
+  const T sshift = ADJ ? T(0) : static_cast<T>(st->s);
+  const T dx = static_cast<T>(D->dx);
+  const SweepRec<T> *__restrict__ rec = static_cast<const SweepRec<T> *>(D->rec) + (size_t)quad * ncell;
+  T *seamx = static_cast<T *>(D->seam_x) + (size_t)g * ny * 2 * kLanes + l0;
+  T *seamy = static_cast<T *>(D->seam_y) + (size_t)g * nx * 2 * kLanes + l0;
+  T *hout = D->h ? static_cast<T *>(D->h) + (size_t)g * ncell * kLanes + l0 : nullptr;
+  double *acc = D->acc;
+  double *facc = D->facc + (size_t)((st->iter + 1) & 1) * ncell * 4;
+  const int sidex = xneg ? kW : kE;
+  const int sidey = yneg ? kS : kN;
+  const int nsteps = nx + ny - 1;
+  const T2 zero2 = Q::splat(T(0));
+
+  auto ring_at = [&](int slot, int col, int kq) -> V16 * {
+    return ring + ((size_t)(slot * V + v) * NQ + kq) * ncol + col;
+  };
+  auto load_vec = [&](const T *src, T2 (&dst)[NP], T shift) {
+#pragma unroll
+    for (int kq = 0; kq < NQ; ++kq) {
+      const V16 x = *reinterpret_cast<const V16 *>(src + kq * (16 / (int)sizeof(T)));
+#pragma unroll
+      for (int u = 0; u < PPQ; ++u) dst[kq * PPQ + u] = Q::add2(Q::pair(x, u), Q::splat(-shift));
+    }
+  };
+  auto store_vec = [&](T *dst, const T2 (&src)[NP]) {
+#pragma unroll
+    for (int kq = 0; kq < NQ; ++kq) *reinterpret_cast<V16 *>(dst + kq * (16 / (int)sizeof(T))) = Q::pack(src + kq * PPQ);
+  };
+
+  // Nothing a step reads comes straight from global memory: the record of the cell a column reaches
+  // at step S is copied (cp.async, by the column's first thread) into stage S % DEPTH during step
+  // S - DEPTH + 1, and with it, for column 0, the previous sweep's x-seam values of that row; the
+  // y-seam values of every column are copied before the first step.  Every thread commits one group
+  // per step; waiting for all but DEPTH - 2 groups before the step's barrier makes stage S + 1
+  // visible to the whole block at step S + 1.
+  constexpr int SEGS = G * (int)sizeof(T) / 16;  // 16-byte pieces of one thread's G values
+  auto stage = [&](int S, int slot) {
+    const int q = S - p;
+    if (S < nsteps && p < nx && q >= 0 && q < ny) {
+      const int j = yneg ? ny - 1 - q : q, i = xneg ? nx - 1 - p : p;
+      if (v == 0) {
+        const char *src = reinterpret_cast<const char *>(rec + (size_t)j * nx + i);
+        char *dst = reinterpret_cast<char *>(recs + (size_t)slot * ncol + p);
+#pragma unroll
+        for (int b = 0; b < (int)sizeof(SweepRec<T>); b += 16) cp_async16(dst + b, src + b);
+      }
+      if (px && p == 0) {
+        T *dst = xsr + (size_t)((q % SR) * V + v) * 2 * G;
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+          for (int b = 0; b < SEGS; ++b)
+            cp_async16(dst + sl * G + b * (16 / (int)sizeof(T)),
+                       seamx + (size_t)(j * 2 + sl) * kLanes + b * (16 / (int)sizeof(T)));
+      }
+    }
+    cp_async_commit();
+  };
+  if (py && p < nx) {
+    const int i = xneg ? nx - 1 - p : p;
+    T *dst = ysr + (size_t)(v * ncol + p) * 2 * G;
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+      for (int b = 0; b < SEGS; ++b)
+        cp_async16(dst + sl * G + b * (16 / (int)sizeof(T)),
+                   seamy + (size_t)(i * 2 + sl) * kLanes + b * (16 / (int)sizeof(T)));
+  }
+#pragma unroll
+  for (int s = 0; s < DEPTH - 1; ++s) stage(s, s);
+  cp_async_wait<DEPTH - 2>();
+  __syncthreads();
+
+  // one step: hy1 holds h(p, q-1), hy2 holds h(p, q-2); the new h(p, q) replaces hy2
+  // ring slots of steps S, S-1, S-2 and the record stage of step S (rotated, not recomputed)
+  int r0 = 0, r1 = 2, r2 = 1, sd = 0;
+  auto step = [&](T2 (&hy1)[NP], T2 (&hy2)[NP], const int S) {
+    const int q = S - p;
+    const bool active = p < nx && q >= 0 && q < ny;
+    stage(S + DEPTH - 1, sd == 0 ? DEPTH - 1 : sd - 1);  // the stage of step S - 1, read before the last barrier
+    if (__any_sync(0xffffffffu, active)) {
+      const int j = yneg ? ny - 1 - q : q, i = xneg ? nx - 1 - p : p;
+      const int cell = j * nx + i;
+      uint32_t code = kSolid;
+      T m0 = T(0), m1 = T(0), m2 = T(0), m3 = T(0);
+      if (active) {
+        const SweepRec<T> r = recs[sd * ncol + p];
+        code = r.code;
+        T ax1, ax2, ay1, ay2, xw = T(0), yw = T(0);
+        if constexpr (sizeof(T) == 4) {
+          ax1 = r.ax1;
+          ax2 = r.ax2;
+          ay1 = r.ay1;
+          ay2 = r.ay2;
+        } else if constexpr (!ADJ) {
+          const int clx = (code >> kClsXShift) & 3, cly = (code >> kClsYShift) & 3;
+          const bool solid = (code & kSolid) != 0;
+          ax1 = solid ? T(0) : T(class_a1(clx));
+          ax2 = solid ? T(0) : T(class_a2(clx));
+          ay1 = solid ? T(0) : T(class_a1(cly));
+          ay2 = solid ? T(0) : T(class_a2(cly));
+        } else {
+          ax1 = T((code >> kAdjT1XShift) & 3);
+          ax2 = (code & kAdjT2X) ? T(-0.5) : T(0);
+          ay1 = T((code >> kAdjT1YShift) & 3);
+          ay2 = (code & kAdjT2Y) ? T(-0.5) : T(0);
+        }
+        if (!ADJ) {
+          xw = r.xw;
+          yw = r.yw;
+        }
+        if (q == 0) {
+          if (py) {
+            const T *ys = ysr + (size_t)(v * ncol + p) * 2 * G;
+            load_vec(ys + G, hy1, sshift);
+            load_vec(ys, hy2, sshift);
+          } else {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) hy1[k] = hy2[k] = zero2;
+          }
+        }
+        T2 u1[NP], u2[NP];
+        const int s0 = r0, s1 = r1, s2 = r2;
+        const T *xs = xsr + (size_t)((q % SR) * V + v) * 2 * G;  // staged seam of this row (column 0's)
+        if (p >= 2) {
+#pragma unroll
+          for (int kq = 0; kq < NQ; ++kq) {
+            const V16 a = *ring_at(s1, p - 1, kq), b = *ring_at(s2, p - 2, kq);
+#pragma unroll
+            for (int u = 0; u < PPQ; ++u) {
+              u1[kq * PPQ + u] = Q::pair(a, u);
+              u2[kq * PPQ + u] = Q::pair(b, u);
+            }
+          }
+        } else {
+          // column 0 reads the previous sweep's columns nx-1, nx-2 (slots 1, 0); column 1 reads
+          // column 0 of this sweep and slot 1
+          if (p == 1) {
+#pragma unroll
+            for (int kq = 0; kq < NQ; ++kq) {
+              const V16 a = *ring_at(s1, 0, kq);
+#pragma unroll
+              for (int u = 0; u < PPQ; ++u) u1[kq * PPQ + u] = Q::pair(a, u);
+            }
+          } else if (px) {
+            load_vec(xs + G, u1, sshift);
+          } else {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) u1[k] = zero2;
+          }
+          if (px) {
+            load_vec(xs + p * G, u2, sshift);
+          } else {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) u2[k] = zero2;
+          }
+        }
+        const T2 sA = Q::splat(r.A), sB = Q::splat(r.B), sC = Q::splat(r.C), sD = Q::splat(r.D);
+        const T2 sax1 = Q::splat(ax1), sax2 = Q::splat(ax2), say1 = Q::splat(ay1), say2 = Q::splat(ay2);
+        const T2 sxw = Q::splat(xw), syw = Q::splat(yw);
+        const T2 stx = Q::splat(ADJ ? T(r.xw) * dx : T(0)), sty = Q::splat(ADJ ? T(r.yw) * dx : T(0));
+        const int irow = (code >> kInvShift) & 15;
+        T2 skx = zero2, sky = zero2, sdl = zero2;
+        if (!UNIF) {
+          const int clx = (code >> kClsXShift) & 3, cly = (code >> kClsYShift) & 3;
+          skx = Q::splat(clx == kFull ? T(1.5) : (clx == kNear ? T(1.0) : T(2.0)));
+          sky = Q::splat(cly == kFull ? T(1.5) : (cly == kNear ? T(1.0) : T(2.0)));
+          sdl = Q::splat(T(r.delta));
+        }
+        T2 M0 = zero2, M1 = zero2, M2 = zero2, M3 = zero2;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const T2 *c = cst + (size_t)((v * NP + k) * kCstFields);
+          const T2 cv1 = c[kCV1], cv2 = c[kCV2], ce = c[kCE], ccx = c[kCCx], ccy = c[kCCy], cwm = c[kCWm];
+          T2 Rk = Q::fma2(sD, ce, Q::fma2(sC, cv2, Q::fma2(sB, cv1, sA)));
+          if (ADJ) Rk = Q::mul2(c[kCWr], Q::fma2(ccx, stx, Q::fma2(ccy, sty, Rk)));
+          const T2 by = Q::fma2(say1, hy1[k], Q::fma2(say2, hy2[k], syw));
+          const T2 bx = Q::fma2(sax1, u1[k], Q::fma2(sax2, u2[k], sxw));
+          T2 iv;
+          if (UNIF) iv = *reinterpret_cast<const T2 *>(invt + irow * VB + v * G + 2 * k);
+          else iv = Q::rcp2(Q::fma2(ccx, skx, Q::fma2(ccy, sky, sdl)));
+          const T2 h = Q::mul2(Q::fma2(ccx, bx, Q::fma2(ccy, by, Rk)), iv);
+          hy2[k] = h;
+          const T2 wh = Q::mul2(cwm, h);
+          M0 = Q::add2(M0, wh);
+          M1 = Q::fma2(cv1, wh, M1);
+          M2 = Q::fma2(cv2, wh, M2);
+          M3 = Q::fma2(ce, wh, M3);
+        }
+#pragma unroll
+        for (int kq = 0; kq < NQ; ++kq) *ring_at(s0, p, kq) = Q::pack(hy2 + kq * PPQ);
+        m0 = M0.x + M0.y;
+        m1 = M1.x + M1.y;
+        m2 = M2.x + M2.y;
+        m3 = (M3.x + M3.y) + m0;  // sum w |v|^2 h = sum w (|v|^2 - 1) h + sum w h
+        if (hout) store_vec(hout + (size_t)cell * kLanes, hy2);
+        if (px && p >= nx - 2) store_vec(seamx + (size_t)(j * 2 + (p - (nx - 2))) * kLanes, hy2);
+        if (py && q >= ny - 2) store_vec(seamy + (size_t)(i * 2 + (q - (ny - 2))) * kLanes, hy2);
+      }
+#pragma unroll
+      for (int off = CPW; off < kLanes; off <<= 1) {
+        m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+        m1 += __shfl_xor_sync(0xffffffffu, m1, off);
+        m2 += __shfl_xor_sync(0xffffffffu, m2, off);
+        m3 += __shfl_xor_sync(0xffffffffu, m3, off);
+      }
+      if (active && !(code & kSolid)) {
+#pragma unroll
+        for (int t = 0; t < 4 / V; ++t) {
+          const int mi = v + t * V;
+          const T val = mi == 0 ? m0 : (mi == 1 ? m1 : (mi == 2 ? m2 : m3));
+          red_add(&acc[(size_t)cell * 4 + mi], static_cast<double>(val));
+        }
+      }
+      // forward: incident flux sum |v_n| W h at cells owning a downstream wall face; adjoint: the
+      // transposed wall reads, sum 2 |v_a|/dx z at cells whose upstream neighbour is solid
+      bool fxf, fyf;
+      if (ADJ) {
+        fxf = active && !(code & kSolid) && ((code >> kClsXShift) & 3u) == (uint32_t)kWall;
+        fyf = active && !(code & kSolid) && ((code >> kClsYShift) & 3u) == (uint32_t)kWall;
+      } else {
+        fxf = active && (code & kIncX) != 0;
+        fyf = active && (code & kIncY) != 0;
+      }
+      if (__any_sync(0xffffffffu, fxf || fyf)) {
+        T fx = T(0), fy = T(0);
+        if (fxf || fyf) {
+          T2 ax = zero2, ay = zero2;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const T2 *c = cst + (size_t)((v * NP + k) * kCstFields);
+            const T2 wh = ADJ ? hy2[k] : Q::mul2(c[kCWm], hy2[k]);
+            ax = Q::fma2(c[kCCx], wh, ax);
+            ay = Q::fma2(c[kCCy], wh, ay);
+          }
+          fx = fxf ? (ax.x + ax.y) : T(0);
+          fy = fyf ? (ay.x + ay.y) : T(0);
+        }
+#pragma unroll
+        for (int off = CPW; off < kLanes; off <<= 1) {
+          fx += __shfl_xor_sync(0xffffffffu, fx, off);
+          fy += __shfl_xor_sync(0xffffffffu, fy, off);
+        }
+        const T scale = ADJ ? T(2) : dx;
+        if (v == 0 && fxf) red_add(&facc[(size_t)cell * 4 + sidex], static_cast<double>(fx * scale));
+        if (v == 0 && fyf) red_add(&facc[(size_t)cell * 4 + sidey], static_cast<double>(fy * scale));
+      }
+    }
+    cp_async_wait<DEPTH - 2>();
+    __syncthreads();
+    const int t = r2;
+    r2 = r1;
+    r1 = r0;
+    r0 = t;
+    sd = sd + 1 == DEPTH ? 0 : sd + 1;
+  };
+
+  T2 ha[NP], hb[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) ha[k] = hb[k] = zero2;
+  for (int S = 0; S < nsteps; S += 2) {
+    step(ha, hb, S);  // h -> hb
+    if (S + 1 < nsteps) step(hb, ha, S + 1);
+  }
+}
+
+template <typename T, bool ADJ, bool UNIF, int V>
+cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  auto kern = cols_kernel<T, ADJ, UNIF, V>;
+  const int ncol = L.warps * (kLanes / V);
+  const size_t smem = layout<T>(V, ncol).total;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nblocks, L.warps * kLanes, smem, stream>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename T, bool ADJ, bool UNIF>
+cudaError_t launch_v(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  switch (L.cols_v) {
+    case 1: return launch<T, ADJ, UNIF, 1>(L, nblocks, stream);
+    case 2: return launch<T, ADJ, UNIF, 2>(L, nblocks, stream);
+    case 4: return launch<T, ADJ, UNIF, 4>(L, nblocks, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cols
+}  // namespace dvm

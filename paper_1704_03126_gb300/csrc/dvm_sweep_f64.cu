@@ -20,10 +20,16 @@ size_t sweep_smem_bytes(bool fp64, int warps, int cw) {
 }
 
 cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  if (L.cols_v > 0)
+    return fp64 ? launch_sweep_cols_f64(uniform_delta, false, L, nblocks, stream)
+                : launch_sweep_cols_f32(uniform_delta, false, L, nblocks, stream);
   return fp64 ? launch_sweep_f64(uniform_delta, L, nblocks, stream) : launch_sweep_f32(uniform_delta, L, nblocks, stream);
 }
 
 cudaError_t launch_sweep_adjoint(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  if (L.cols_v > 0)
+    return fp64 ? launch_sweep_cols_f64(uniform_delta, true, L, nblocks, stream)
+                : launch_sweep_cols_f32(uniform_delta, true, L, nblocks, stream);
   return fp64 ? launch_sweep_adjoint_f64(uniform_delta, L, nblocks, stream)
               : launch_sweep_adjoint_f32(uniform_delta, L, nblocks, stream);
 }

@@ -88,11 +88,17 @@ def lib():
         L.dvm_status_string.argtypes = [I]
         L.dvm_status_string.restype = ctypes.c_char_p
         L.dvm_destroy.argtypes = [P]
+        L.dvm_set_schedule.argtypes = [P, I, I]
+        L.dvm_get_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.dvm_batch_set_schedule.argtypes = [P, I, I]
+        L.dvm_batch_get_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.dvm_batch_autotune.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
         for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
                      "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
-                     "dvm_moments_noalloc", "dvm_adjoint"):
+                     "dvm_moments_noalloc", "dvm_adjoint", "dvm_set_schedule", "dvm_get_schedule",
+                     "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -107,11 +113,13 @@ class Solver:
 
     mask: uint8 [ny][nx] (1 = solid); quad = (kind, n, vmax) with kind in {"gh", "nc", "cubic"};
     exactly one of kn (> 0, inf allowed) and delta (>= 0).  stream: a cudaStream_t as int (e.g.
-    torch.cuda.current_stream().cuda_stream) or None.
+    torch.cuda.current_stream().cuda_stream) or None.  schedule: None (automatic), or (kind,
+    threads_per_column) for set_schedule.
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
-                 precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None):
+                 precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
+                 schedule=None):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -138,6 +146,8 @@ class Solver:
         st = L.dvm_create(_ptr(mask), ctypes.byref(p), ctypes.c_void_p(stream or 0), ctypes.byref(self._ctx))
         if st != DVM_OK:
             raise DvmError(st, L.dvm_last_error(None).decode())
+        if schedule is not None:
+            self.set_schedule(*schedule)
 
     def _check(self, st, allow=(DVM_OK,)):
         if st not in allow:
@@ -157,6 +167,15 @@ class Solver:
 
     def reset(self):
         return self._check(lib().dvm_reset(self._ctx))
+
+    def set_schedule(self, kind="auto", threads_per_column=0):
+        """Sweep kernel of this solver: "rows", "columns" (threads_per_column 1, 2, 4 or 0 = auto) or "auto"."""
+        return self._check(lib().dvm_set_schedule(self._ctx, SWEEP_KINDS[kind], int(threads_per_column)))
+
+    def schedule(self):
+        k, v = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().dvm_get_schedule(self._ctx, ctypes.byref(k), ctypes.byref(v)))
+        return SWEEP_NAMES[k.value], v.value
 
     def solve(self, tol=1e-10, max_iter=100000, raise_on_noconv=True):
         """Returns (status, sweeps run, error estimate)."""
@@ -219,6 +238,10 @@ class Solver:
             pass
 
 
+SWEEP_KINDS = {"auto": 0, "rows": 1, "columns": 2}
+SWEEP_NAMES = {v: k for k, v in SWEEP_KINDS.items()}
+
+
 class Batch:
     """Several Solvers advanced by one launch of each kernel per sweep (dvm_batch_*)."""
 
@@ -256,6 +279,27 @@ class Batch:
 
     def kernels_per_sweep(self):
         return lib().dvm_batch_kernels_per_sweep(self._b)
+
+    def set_schedule(self, kind="auto", threads_per_column=0):
+        st = lib().dvm_batch_set_schedule(self._b, SWEEP_KINDS[kind], int(threads_per_column))
+        if st != DVM_OK:
+            self._err(st)
+
+    def schedule(self):
+        k, v = ctypes.c_int(), ctypes.c_int()
+        st = lib().dvm_batch_get_schedule(self._b, ctypes.byref(k), ctypes.byref(v))
+        if st != DVM_OK:
+            self._err(st)
+        return SWEEP_NAMES[k.value], v.value
+
+    def autotune(self, sweeps=5):
+        """Time every fitting sweep kernel (the trial sweeps advance the state); keeps the fastest.
+        Returns (kind, threads_per_column, median sweep ms)."""
+        k, v, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        st = lib().dvm_batch_autotune(self._b, int(sweeps), ctypes.byref(k), ctypes.byref(v), ctypes.byref(ms))
+        if st != DVM_OK:
+            self._err(st)
+        return SWEEP_NAMES[k.value], v.value, ms.value
 
     def close(self):
         if self._b:

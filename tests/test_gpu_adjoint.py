@@ -1,6 +1,8 @@
 """GPU adjoint (dvm_adjoint, transposed sweeps through the C ABI) against the FP64 oracle's adjoint of
 the same projected iteration, the forward/adjoint identity Q = F sum z v1, and central differences of
 GPU forward solves."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -37,17 +39,29 @@ def _delta_field(mask, base, seed):
     return base * rng.uniform(0.5, 1.5, size=mask.shape)
 
 
+SCHEDULES = [("rows", 0), ("columns", 1), ("columns", 2), ("columns", 4)]
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_gradient(name):
+    _, mask, px, py, delta, quad = next(c for c in CASES if c[0] == name)
+    d = _delta_field(mask, delta, 3)
+    p = oracle.Problem.make(mask, px, py, d, quad)
+    ref = oracle.solve(p, tol=1e-13, max_iter=200000)
+    return oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=200000)
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=["rows", "cols1", "cols2", "cols4"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_adjoint_gradient_matches_oracle(case):
+def test_adjoint_gradient_matches_oracle(case, schedule):
     name, mask, px, py, delta, quad = case
     d = _delta_field(mask, delta, 3)
-    sol = dvm.Solver(mask, px, py, delta=delta, quad=quad, precision="fp64", store_distribution=True)
+    sol = dvm.Solver(mask, px, py, delta=delta, quad=quad, precision="fp64", store_distribution=True,
+                     schedule=schedule)
     sol.set_delta_field(d)
     sol.solve(tol=1e-13, max_iter=200000)
     grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=200000)
-    p = oracle.Problem.make(mask, px, py, d, quad)
-    ref = oracle.solve(p, tol=1e-13, max_iter=200000)
-    g_ref, q_ref_id, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=200000)
+    g_ref, q_ref_id, _, ok = _oracle_gradient(name)
     assert ok
     scale = np.abs(g_ref).max()
     assert np.abs(grad - g_ref).max() < 1e-8 * scale, np.abs(grad - g_ref).max() / scale

@@ -5,8 +5,11 @@ Tolerances (stated in the test, from the target accuracy of the two storage prec
   FP32 storage / FP64 accumulation: |Q - Q_oracle| / S < 1e-5, fields within 1e-4 absolute.
 S = sum |u1| dA / Lx, which is |Q_oracle| for every through-flow case; closed boxes have no net flow.
 Both sides run the same discrete iteration (same stopping rule); parity is judged on converged fixed
-points, so iteration counts may differ by a sweep or two at the stopping knife edge.
+points, so iteration counts may differ by a sweep or two at the stopping knife edge.  Every case runs
+on both sweep kernels: the row wavefront and the column sweep with 1, 2 and 4 threads per column.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -48,11 +51,25 @@ def _compare(sol, orc, mask, precision):
         assert np.all(np.isnan(f[name][~gas]))
 
 
-def _solve_both(mask, px, py, kn, quad, precision, gpu_tol, orc_tol=1e-12, **kw):
-    delta = dvm.kn_to_delta(kn)
-    sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision=precision, **kw)
+SCHEDULES = [("rows", 0), ("columns", 1), ("columns", 2), ("columns", 4)]
+SCHED_IDS = ["rows", "cols1", "cols2", "cols4"]
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_cached(key):
+    mask, px, py, kn, quad, orc_tol = _ORACLE_ARGS[key]
+    return oracle.solve(_oracle_problem(mask, px, py, dvm.kn_to_delta(kn), quad), tol=orc_tol, max_iter=200000)
+
+
+_ORACLE_ARGS = {}
+
+
+def _solve_both(mask, px, py, kn, quad, precision, gpu_tol, orc_tol=1e-12, schedule=None, **kw):
+    sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision=precision, schedule=schedule, **kw)
     st, iters, est = sol.solve(tol=gpu_tol, max_iter=200000)
-    orc = oracle.solve(_oracle_problem(mask, px, py, delta, quad), tol=orc_tol, max_iter=200000)
+    key = (mask.tobytes(), mask.shape, px, py, kn, quad, orc_tol)
+    _ORACLE_ARGS[key] = (mask, px, py, kn, quad, orc_tol)
+    orc = _oracle_cached(key)
     assert orc["converged"]
     return sol, orc, iters
 
@@ -100,26 +117,30 @@ CASES = [
 FP32_SLOW = {"ragged37x29_block_gh8", "ragged37x29_warps5", "narrow3x40_nonperiodic_y", "periodic_y_only"}
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_small_geometries_match_oracle_fp64(case):
+def test_small_geometries_match_oracle_fp64(case, schedule):
     name, mask, px, py, kn, quad, warps = case
-    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp64", 1e-12, sweep_warps=warps)
+    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp64", 1e-12, schedule=schedule, sweep_warps=warps)
+    assert sol.schedule() == schedule
     _compare(sol, orc, mask, "fp64")
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] not in FP32_SLOW], ids=lambda c: c[0])
-def test_small_geometries_match_oracle_fp32(case):
+def test_small_geometries_match_oracle_fp32(case, schedule):
     name, mask, px, py, kn, quad, warps = case
-    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp32", 1e-6, sweep_warps=warps)
+    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp32", 1e-6, schedule=schedule, sweep_warps=warps)
     _compare(sol, orc, mask, "fp32")
 
 
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] in FP32_SLOW], ids=lambda c: c[0])
-def test_fp32_error_on_slowly_converging_cases(case):
+def test_fp32_error_on_slowly_converging_cases(case, schedule):
     """Slow source-iteration convergence amplifies FP32 rounding: the stated bound is 1e-4 on Q and
     1e-3 on the fields (measured: 1e-5 to 4e-5 on Q)."""
     name, mask, px, py, kn, quad, warps = case
-    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp32", 1e-6, sweep_warps=warps)
+    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp32", 1e-6, schedule=schedule, sweep_warps=warps)
     q, _ = sol.flowrate()
     assert abs(q - orc["Q"]) < 1e-4 * _flow_scale(orc, mask)
     f = sol.fields()
@@ -127,26 +148,30 @@ def test_fp32_error_on_slowly_converging_cases(case):
     assert np.abs(f["u1"][gas] - orc["u1"][gas]).max() < 1e-3
 
 
-def test_delta_field_matches_oracle():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
+def test_delta_field_matches_oracle(schedule, precision):
     mask = _block_mask(20, 16)
     rng = np.random.default_rng(5)
     d = rng.uniform(0.3, 3.0, size=mask.shape)
     quad = ("cubic", 10, 4.0)
-    sol = dvm.Solver(mask, True, True, delta=1.0, quad=quad, precision="fp64")
+    sol = dvm.Solver(mask, True, True, delta=1.0, quad=quad, precision=precision, schedule=schedule)
     sol.set_delta_field(d)
-    sol.solve(tol=1e-12, max_iter=100000)
+    sol.solve(tol=1e-12 if precision == "fp64" else 1e-6, max_iter=100000)
     orc = oracle.solve(_oracle_problem(mask, True, True, d, quad), tol=1e-12, max_iter=100000)
-    _compare(sol, orc, mask, "fp64")
+    _compare(sol, orc, mask, precision)
     q, ka = sol.flowrate()
     assert np.isnan(ka)
 
 
-def test_one_sweep_matches_oracle_velocity_by_velocity():
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
+def test_one_sweep_matches_oracle_velocity_by_velocity(schedule):
     """From the GPU's stored state h^n, the oracle sweeps selected velocities once; the GPU's h^{n+1}
     must agree (after the same mass shift)."""
     mask = inputs.rough_channel_mask(24)
     quad = ("nc", 8, 4.0)
-    sol = dvm.Solver(mask, True, False, kn=0.5, quad=quad, precision="fp64", store_distribution=True)
+    sol = dvm.Solver(mask, True, False, kn=0.5, quad=quad, precision="fp64", store_distribution=True,
+                     schedule=schedule)
     sol.iterate(3)
     K = quad[1] ** 2
     h_n = sol.distribution(np.arange(K))
@@ -162,7 +187,8 @@ def test_one_sweep_matches_oracle_velocity_by_velocity():
     assert err < 1e-12 * max(1.0, np.abs(ref).max()), err
 
 
-def test_batch_matches_single_solves():
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
+def test_batch_matches_single_solves(schedule):
     specs = [
         (inputs.rough_channel_mask(32), True, False, 1.0, ("nc", 8, 4.0)),
         (inputs.porous_disks_mask(40, 0.65, 4, 6, seed=2)[0], True, True, 0.2, ("cubic", 12, 4.0)),
@@ -173,7 +199,7 @@ def test_batch_matches_single_solves():
         s = dvm.Solver(m, px, py, kn=kn, quad=quad, precision="fp64")
         s.solve(tol=1e-12, max_iter=100000)
         singles.append(s.flowrate()[0])
-        batch.append(dvm.Solver(m, px, py, kn=kn, quad=quad, precision="fp64"))
+        batch.append(dvm.Solver(m, px, py, kn=kn, quad=quad, precision="fp64", schedule=schedule))
     per = dvm.batch_solve(batch, tol=1e-12, max_iter=100000)
     assert list(per) == [0, 0, 0]
     for s, q in zip(batch, singles):
@@ -196,6 +222,38 @@ def test_max_iter_reports_noconv():
     ref = dvm.Solver(inputs.plates_mask(4, 16), True, False, kn=0.1, quad=("gh", 8, 0.0))
     ref.solve(tol=1e-12, max_iter=100000)
     assert abs(sol.flowrate()[0] - ref.flowrate()[0]) < 1e-10 * abs(ref.flowrate()[0])
+
+
+def test_autotune_picks_a_fitting_kernel_and_keeps_the_state():
+    specs = [(inputs.rough_channel_mask(64), ("cubic", 16, 4.0), 0.5),
+             (inputs.porous_disks_mask(96, 0.65, 4, 8, seed=4)[0], ("cubic", 24, 4.0), 2.0)]
+    sols = [dvm.Solver(m, True, False, kn=kn, quad=q, precision="fp32") for m, q, kn in specs]
+    refs = [dvm.Solver(m, True, False, kn=kn, quad=q, precision="fp32") for m, q, kn in specs]
+    b = dvm.Batch(sols)
+    kind, v, ms = b.autotune(sweeps=3)
+    assert (kind, v) in SCHEDULES and ms > 0
+    assert b.schedule() == (kind, v)
+    done = sols[0].info()["iterations"]
+    assert done == 4 * (1 + 3)  # rows + three column variants, each 1 warm-up + 3 timed sweeps
+    b.iterate(10)
+    for r in refs:
+        r.iterate(done + 10)
+    for s, r in zip(sols, refs):
+        assert abs(s.flowrate()[0] - r.flowrate()[0]) < 1e-5 * abs(r.flowrate()[0])
+    with pytest.raises(dvm.DvmError):
+        b.set_schedule("columns", 3)
+
+
+def test_wide_grid_runs_on_the_column_sweep_only():
+    mask = inputs.rough_channel_mask(384)[:64].copy()  # 384 columns: beyond the row sweep's 256
+    sol = dvm.Solver(mask, True, False, kn=1.0, quad=("cubic", 8, 4.0), precision="fp32")
+    assert sol.schedule() == ("columns", 1)
+    with pytest.raises(dvm.DvmError):
+        sol.set_schedule("rows")
+    with pytest.raises(dvm.DvmError):
+        sol.set_schedule("columns", 2)
+    sol.iterate(5)
+    assert np.isfinite(sol.flowrate()[0])
 
 
 # ------------------------------------------------------------------ full-size workloads
