@@ -26,7 +26,7 @@ __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int 
   L.seam = off;
   if (stage_seams) off = align16(off + (size_t)2 * nstage * 2 * cw * kLanes * tsize);
   L.inv = off;
-  off = align16(off + (size_t)9 * kLanes * tsize);
+  off = align16(off + (size_t)kInvRows * kLanes * tsize);  // rows 0-8: stencil classes, row 9: solid (0)
   L.wts = off;
   off = align16(off + (size_t)4 * ring_stride * tsize);
   L.prog = off;

@@ -278,3 +278,60 @@ def test_rough_channel_full_size_fixed_point():
     u1 = f["u1"]
     assert np.nanmax(np.abs(u1 - u1[:, ::-1])) < 1e-4
     assert np.nanmax(np.abs(u1 - u1[::-1, :])) < 1e-4
+
+
+# ------------------------------------------------------------------ wide grids (256 columns)
+
+def _wide_porous_slice():
+    """24 rows of the 256 x 256 disk medium, periodic in both directions: the row kernel's widest
+    chunk (16 cells, 16 rows in flight) and the column kernel's widest blocks."""
+    return inputs.porous_disks_mask(256, 0.6, 8, 20, seed=1)[0][:24].copy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("schedule", SCHEDULES[:3], ids=SCHED_IDS[:3])
+def test_one_sweep_on_a_256_column_periodic_grid(schedule, precision):
+    mask = _wide_porous_slice()
+    quad = ("cubic", 8, 4.0)
+    sol = dvm.Solver(mask, True, True, kn=0.5, quad=quad, precision=precision, store_distribution=True,
+                     schedule=schedule)
+    sol.iterate(3)
+    K = quad[1] ** 2
+    h_n = sol.distribution(np.arange(K))
+    c_n = sol.info()["mass_shift"]
+    sol.iterate(1)
+    c_np1 = sol.info()["mass_shift"]
+    ks = [0, 5, 18, 27, 36, 45, 63]
+    h_np1 = sol.distribution(ks)
+    p = _oracle_problem(mask, True, True, dvm.kn_to_delta(0.5), quad)
+    ref = oracle.sweep_selected(p, h_n, c_n, ks) - (c_np1 - c_n)
+    gas = mask == 0
+    err = np.abs((ref - h_np1)[:, gas]).max()
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert err < tol * max(1.0, np.abs(ref).max()), err
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES[:3], ids=SCHED_IDS[:3])
+def test_256_column_periodic_grid_fixed_point(schedule):
+    mask = _wide_porous_slice()
+    quad = ("cubic", 8, 4.0)
+    sol, orc, iters = _solve_both(mask, True, True, 0.5, quad, "fp64", 1e-11, orc_tol=1e-11, schedule=schedule)
+    _compare(sol, orc, mask, "fp64")
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES[:3], ids=SCHED_IDS[:3])
+def test_multi_instance_batch_is_reproducible(schedule):
+    """Identical runs of a batch must agree to the rounding of the FP64 accumulation order.  (The row
+    kernel once sized its 1/denominator table one row short in shared memory; the spare row then
+    raced with the moment weights, visible only as run-to-run scatter in multi-instance batches.)"""
+    insts = [inputs.porous_instance(kn, nv=16) for kn in (0.05, 0.5, 5.0)]
+    qs = []
+    for _ in range(3):
+        sols = [dvm.Solver(i.mask, True, True, kn=i.kn, quad=i.quad, precision="fp32", schedule=schedule)
+                for i in insts]
+        b = dvm.Batch(sols)
+        b.iterate(200)
+        qs.append([s.flowrate()[0] for s in sols])
+        b.close()
+    qs = np.array(qs)
+    assert np.all((qs.max(0) - qs.min(0)) < 1e-9 * np.abs(qs).mean(0)), qs
