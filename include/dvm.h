@@ -189,8 +189,16 @@ dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out);
 dvm_status dvm_batch_run(dvm_batch *batch, double tol, int max_iter, dvm_status *per);
 /* Exactly n sweeps of every member, no stopping test.  Synchronises the stream. */
 dvm_status dvm_batch_iterate(dvm_batch *batch, int n);
-/* Device time of the last single sweep run by dvm_batch_iterate(batch, 1): the sweep kernel and the
- * two finalize kernels, in milliseconds (CUDA events recorded around them on the batch stream). */
+/* Exactly n sweeps of every member, enqueued on the batch stream without waiting (one arming kernel,
+ * then the sweep graphs); nothing is read back.  Call dvm_batch_check (or synchronise the stream)
+ * before reading results.  Errors of the sweeps themselves surface in dvm_batch_check. */
+dvm_status dvm_batch_enqueue(dvm_batch *batch, int n);
+/* Wait for the batch stream and report the first failing member status (DVM_ENOCONV is not a failure
+ * here: an enqueued run has no stopping test). */
+dvm_status dvm_batch_check(dvm_batch *batch);
+/* Device time of the last single sweep run by dvm_batch_iterate(batch, 1) or dvm_batch_enqueue(batch,
+ * 1): the sweep kernel and the two finalize kernels, in milliseconds (CUDA events recorded around them
+ * on the batch stream); read it after the stream has reached them. */
 dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms);
 /* Re-plan the batch's sweep launch for another kernel (see dvm_set_schedule); state is kept. */
 dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_column);

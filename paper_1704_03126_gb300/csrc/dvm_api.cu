@@ -1080,6 +1080,42 @@ dvm_status dvm_batch_iterate(dvm_batch *batch, int n) {
   return batch_iterate(batch, n);
 }
 
+dvm_status dvm_batch_enqueue(dvm_batch *batch, int n) {
+  if (!batch) return DVM_EINVAL;
+  dvm_batch *b = batch;
+  dvm_ctx *c0 = b->ctxs[0];
+  if (n < 1 || n > 1000000) return fail(c0, DVM_EINVAL, "n must be in 1..1000000");
+  for (dvm_ctx *c : b->ctxs)
+    if (c->stream != b->stream) DVM_CUDA(c0, cudaStreamSynchronize(c->stream));
+  DVM_CUDA(c0, launch_arm_all(b->d_descs, (int)b->ctxs.size(), -1.0, n, b->stream));
+  int left = n;
+  while (left >= b->m && b->m > 1) {
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_many, b->stream));
+    left -= b->m;
+  }
+  for (; left > 0; --left) {
+    DVM_CUDA(c0, cudaEventRecord(b->ev[0], b->stream));
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_sweep, b->stream));
+    DVM_CUDA(c0, cudaEventRecord(b->ev[1], b->stream));
+    DVM_CUDA(c0, cudaGraphLaunch(b->g_fin, b->stream));
+    DVM_CUDA(c0, cudaEventRecord(b->ev[2], b->stream));
+  }
+  b->timed = (n == 1) || (n % b->m != 0) || b->m == 1;
+  return DVM_OK;
+}
+
+dvm_status dvm_batch_check(dvm_batch *batch) {
+  if (!batch) return DVM_EINVAL;
+  bool all = false;
+  dvm_status st = batch_poll(batch, &all);
+  if (st != DVM_OK) return st;
+  for (dvm_ctx *c : batch->ctxs) {
+    const int s = c->h_state->status;
+    if (s != DVM_OK && s != DVM_ENOCONV) return fail(batch->ctxs[0], (dvm_status)s, "a batch member failed");
+  }
+  return DVM_OK;
+}
+
 dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms) {
   if (!batch) return DVM_EINVAL;
   if (!batch->timed) return fail(batch->ctxs[0], DVM_ESTATE, "no timed single sweep has run on this batch");

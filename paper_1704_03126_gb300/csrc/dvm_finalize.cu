@@ -282,7 +282,31 @@ __global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
   if (st->done) st->status = 4;
 }
 
+// Arm every instance of a launch for `count` more sweeps, relative to its device-side sweep count
+// (no host read of the state: used by asynchronous batch sweeps).
+__global__ void arm_all_kernel(const InstanceDesc *descs, int n, double tol, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  DeviceState *st = descs[i].state;
+  const long long lim = (long long)st->iter + count;
+  const int max_iter_abs = lim > 2000000000LL ? 2000000000 : (int)lim;
+  st->tol = tol;
+  st->eps_min = INFINITY;
+  st->iter_min = st->iter;
+  st->max_iter = max_iter_abs;
+  st->status = 0;
+  st->nan_flag = 0;
+  st->err_flag = 0;
+  st->done = (st->iter >= max_iter_abs) ? 1 : 0;
+  if (st->done) st->status = 4;
+}
+
 }  // namespace
+
+cudaError_t launch_arm_all(const InstanceDesc *descs, int n, double tol, int count, cudaStream_t stream) {
+  arm_all_kernel<<<(n + 127) / 128, 128, 0, stream>>>(descs, n, tol, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream) {
   fin1_kernel<<<nblocks, kFinBlock, 0, stream>>>(L);

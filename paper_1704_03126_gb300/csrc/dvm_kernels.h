@@ -94,6 +94,8 @@ cudaError_t launch_adjoint_gradient(const InstanceDesc *adj_dev, int ncell, bool
 cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream);
 // Reset an instance to h = 0 (records, accumulators and state; arrays are cleared by the caller).
 cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
+// Arm every instance of a launch for `count` more sweeps (device-relative; one launch).
+cudaError_t launch_arm_all(const InstanceDesc *descs, int n, double tol, int count, cudaStream_t stream);
 // Arm the stopping test of an instance: tol, absolute sweep limit; clears done and status.
 cudaError_t launch_arm(DeviceState *st, double tol, int max_iter_abs, cudaStream_t stream);
 

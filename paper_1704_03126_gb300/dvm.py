@@ -88,6 +88,8 @@ def lib():
         L.dvm_status_string.argtypes = [I]
         L.dvm_status_string.restype = ctypes.c_char_p
         L.dvm_destroy.argtypes = [P]
+        L.dvm_batch_enqueue.argtypes = [P, I]
+        L.dvm_batch_check.argtypes = [P]
         L.dvm_set_schedule.argtypes = [P, I, I]
         L.dvm_get_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         L.dvm_batch_set_schedule.argtypes = [P, I, I]
@@ -98,7 +100,8 @@ def lib():
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
                      "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
                      "dvm_moments_noalloc", "dvm_adjoint", "dvm_set_schedule", "dvm_get_schedule",
-                     "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune"):
+                     "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune",
+                     "dvm_batch_enqueue", "dvm_batch_check"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -265,6 +268,18 @@ class Batch:
 
     def iterate(self, n=1):
         st = lib().dvm_batch_iterate(self._b, int(n))
+        if st != DVM_OK:
+            self._err(st)
+
+    def enqueue(self, n=1):
+        """n sweeps of every member, enqueued without waiting (see check)."""
+        st = lib().dvm_batch_enqueue(self._b, int(n))
+        if st != DVM_OK:
+            self._err(st)
+
+    def check(self):
+        """Wait for the enqueued sweeps; raises on a failed member."""
+        st = lib().dvm_batch_check(self._b)
         if st != DVM_OK:
             self._err(st)
 

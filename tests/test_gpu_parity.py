@@ -335,3 +335,19 @@ def test_multi_instance_batch_is_reproducible(schedule):
         b.close()
     qs = np.array(qs)
     assert np.all((qs.max(0) - qs.min(0)) < 1e-9 * np.abs(qs).mean(0)), qs
+
+
+def test_enqueued_sweeps_match_iterate():
+    insts = [inputs.rough_instance(kn, n=32, nv=8) for kn in (0.1, 1.0)]
+    a = [dvm.Solver(i.mask, True, False, kn=i.kn, quad=i.quad, precision="fp64") for i in insts]
+    b = [dvm.Solver(i.mask, True, False, kn=i.kn, quad=i.quad, precision="fp64") for i in insts]
+    ba, bb = dvm.Batch(a), dvm.Batch(b)
+    ba.iterate(7)
+    for n in (1, 4, 2):
+        bb.enqueue(n)
+    bb.check()
+    for x, y in zip(a, b):
+        assert y.info()["iterations"] == 7
+        assert abs(x.flowrate()[0] - y.flowrate()[0]) < 1e-13 * abs(x.flowrate()[0])
+    s_ms, f_ms = bb.timing()
+    assert s_ms > 0 and f_ms > 0
