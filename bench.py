@@ -196,7 +196,10 @@ def run_ours(args, rank, world, local_rank):
     from paper_1704_03126_gb300 import dvm
 
     torch.cuda.set_device(local_rank)
-    stream = torch.cuda.current_stream()
+    # a stream of our own (the default stream's handle is 0, which the library would replace by a
+    # private stream): the solvers, the L2 flush and the CUDA events all run on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     insts = instances(args.workload)
     upd = updates_per_step(insts)
 
@@ -407,7 +410,8 @@ def run_adjoint(args, rank, world, local_rank):
     from paper_1704_03126_gb300 import dvm, inputs
 
     torch.cuda.set_device(local_rank)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     inst = instances("adjoint")[0]
     upd = updates_per_step([inst])
     delta = dvm.kn_to_delta(inst.kn)

@@ -255,6 +255,11 @@ __global__ void __launch_bounds__(kBlock) afin2_kernel(const InstanceDesc *D) {
     const double tx = (code & kIncX) ? fcur[(size_t)cell * 4 + sx] / D->nrm[sx] : 0.0;
     const double ty = (code & kIncY) ? fcur[(size_t)cell * 4 + sy] / D->nrm[sy] : 0.0;
     store_adj_rec<T>(rec + (size_t)q * ncell + cell, al, kappa, tx, ty, code, d);
+    // the transposed sweep visits cells in the opposite order of the quadrant
+    if (D->rec_diag)
+      store_adj_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
+                           diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) == 0, (q & 2) == 0),
+                       al, kappa, tx, ty, code, d);
   }
   reinterpret_cast<Dbl4 *>(fnext)[cell] = Dbl4{0.0, 0.0, 0.0, 0.0};
 }
@@ -268,8 +273,13 @@ __global__ void areset_kernel(const InstanceDesc *D) {
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncell; cell += gridDim.x * blockDim.x) {
     const bool solid = (D->code4[(size_t)cell * 4] & kSolid) != 0;
     const double d = solid ? 0.0 : (D->uniform_delta ? D->delta : D->delta_field[cell]);
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q) {
       store_adj_rec<T>(rec + (size_t)q * ncell + cell, zero, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+      if (D->rec_diag)
+        store_adj_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
+                             diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) == 0, (q & 2) == 0),
+                         zero, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DeviceState *st = D->state;

@@ -34,7 +34,7 @@ struct dvm_ctx {
   bool own_stream = false;
   int device = 0;
   // device memory
-  void *d_vel = nullptr, *d_inv = nullptr, *d_rec = nullptr;
+  void *d_vel = nullptr, *d_inv = nullptr, *d_rec = nullptr, *d_rec_diag = nullptr;
   uint32_t *d_code4 = nullptr;
   int *d_hw_src = nullptr;
   double *d_delta_field = nullptr, *d_acc = nullptr, *d_facc = nullptr, *d_mom = nullptr, *d_u1prev = nullptr;
@@ -50,7 +50,7 @@ struct dvm_ctx {
   DeviceState *h_state = nullptr;  // pinned
   std::string err;
   // adjoint (allocated by the first dvm_adjoint)
-  void *a_rec = nullptr, *a_seamx = nullptr, *a_seamy = nullptr, *a_z = nullptr;
+  void *a_rec = nullptr, *a_rec_diag = nullptr, *a_seamx = nullptr, *a_seamy = nullptr, *a_z = nullptr;
   double *a_acc = nullptr, *a_flux = nullptr, *a_alpha = nullptr, *a_z1prev = nullptr, *a_grad = nullptr;
   DeviceState *a_state = nullptr;
   InstanceDesc *a_desc = nullptr;
@@ -238,6 +238,7 @@ void release_device(dvm_ctx *c) {
   free_dev(c->d_vel);
   free_dev(c->d_inv);
   free_dev(c->d_rec);
+  free_dev(c->d_rec_diag);
   free_dev(c->d_code4);
   free_dev(c->d_hw_src);
   free_dev(c->d_delta_field);
@@ -257,6 +258,7 @@ void release_device(dvm_ctx *c) {
   if (c->a_graph) cudaGraphExecDestroy(c->a_graph);
   c->a_graph = nullptr;
   free_dev(c->a_rec);
+  free_dev(c->a_rec_diag);
   free_dev(c->a_seamx);
   free_dev(c->a_seamy);
   free_dev(c->a_z);
@@ -707,6 +709,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   CREATE_CUDA(cudaMalloc(&c->d_vel, ts * c->ngroups * kNumVelFields * kLanes));
   CREATE_CUDA(cudaMalloc(&c->d_inv, ts * c->ngroups * kInvRows * kLanes));
   CREATE_CUDA(cudaMalloc(&c->d_rec, recsz * 4 * ncell));
+  CREATE_CUDA(cudaMalloc(&c->d_rec_diag, recsz * 4 * diag_quadrant_size(c->nx, c->ny)));
   CREATE_CUDA(cudaMalloc(&c->d_code4, sizeof(uint32_t) * 4 * ncell));
   CREATE_CUDA(cudaMalloc(&c->d_hw_src, sizeof(int) * 8 * ncell));
   CREATE_CUDA(cudaMalloc(&c->d_delta_field, sizeof(double) * ncell));
@@ -772,6 +775,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   D.vel = c->d_vel;
   D.inv_den = c->d_inv;
   D.rec = c->d_rec;
+  D.rec_diag = c->d_rec_diag;
   D.code4 = c->d_code4;
   D.hw_src = c->d_hw_src;
   D.acc = c->d_acc;
@@ -950,6 +954,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   const size_t ncell = (size_t)c->ncell;
   if (!c->a_state) {
     DVM_CUDA(c, cudaMalloc(&c->a_rec, recsz * 4 * ncell));
+    DVM_CUDA(c, cudaMalloc(&c->a_rec_diag, recsz * 4 * diag_quadrant_size(c->nx, c->ny)));
     DVM_CUDA(c, cudaMalloc(&c->a_seamx, ts * c->ngroups * c->ny * 2 * kLanes));
     DVM_CUDA(c, cudaMalloc(&c->a_seamy, ts * c->ngroups * c->nx * 2 * kLanes));
     DVM_CUDA(c, cudaMalloc(&c->a_z, ts * c->ngroups * ncell * kLanes));
@@ -966,6 +971,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   A.uniform_delta = c->uniform ? 1 : 0;
   A.delta_field = c->d_delta_field;
   A.rec = c->a_rec;
+  A.rec_diag = c->a_rec_diag;
   A.acc = c->a_acc;
   A.facc = c->a_flux;
   A.mom = c->a_alpha;

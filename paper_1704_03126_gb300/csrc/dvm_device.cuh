@@ -64,6 +64,14 @@ template <> struct alignas(16) SweepRec<double> {
 static_assert(sizeof(SweepRec<float>) == 48, "record layout");
 static_assert(sizeof(SweepRec<double>) == 64, "record layout");
 
+// Slot of cell (i, j) in the diagonal-major record array of one quadrant: with (p, q) the cell's
+// column and row in the quadrant's sweep order, cells of one anti-diagonal S = p + q are contiguous.
+__host__ __device__ inline size_t diag_slot(int nx, int ny, int i, int j, bool xneg, bool yneg) {
+  const int p = xneg ? nx - 1 - i : i, q = yneg ? ny - 1 - j : j;
+  return (size_t)(p + q) * nx + p;
+}
+__host__ __device__ inline size_t diag_quadrant_size(int nx, int ny) { return (size_t)(nx + ny - 1) * nx; }
+
 // Upwind coefficients (a1, a2) of a stencil class: interior (2, -1/2), second cell (1, 0), wall (0, 0).
 __host__ __device__ inline float class_a1(int cls) { return cls == kFull ? 2.0f : (cls == kNear ? 1.0f : 0.0f); }
 __host__ __device__ inline float class_a2(int cls) { return cls == kFull ? -0.5f : 0.0f; }
@@ -121,6 +129,8 @@ struct InstanceDesc {
   const void *vel;      // [ngroups][kNumVelFields][32] T
   const void *inv_den;  // [ngroups][kInvRows][32] T: 1 / (delta + cx kx + cy ky), uniform delta only; row 9 = 0
   void *rec;            // [4][ncell] SweepRec<T>
+  void *rec_diag;       // [4][nx + ny - 1][nx] SweepRec<T>: the same records along the anti-diagonals of
+                        // each quadrant's sweep order (column sweep), see diag_slot
   const uint32_t *code4;   // [ncell][4]
   const int *hw_src;       // [ncell][8]: (quadrant, axis) -> owner cell * 4 + side, or -1
   const double *delta_field;  // [ncell] or nullptr

@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
           }
         }
         store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+        if (D->rec_diag)
+          store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
+                           diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
+                       A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
       }
       du = fabs(u1 - D->u1prev[cell]);
       ua = fabs(u1);
@@ -248,8 +252,13 @@ __global__ void reset_kernel(const InstanceDesc *D) {
     const uint32_t code0 = D->code4[(size_t)cell * 4];
     const double d = (code0 & kSolid) ? 0.0 : (D->uniform_delta ? D->delta : D->delta_field[cell]);
     const double B = (code0 & kSolid) ? 0.0 : D->force;
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q) {
       store_rec<T>(rec + (size_t)q * ncell + cell, 0.0, B, 0.0, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+      if (D->rec_diag)
+        store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
+                         diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
+                     0.0, B, 0.0, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DeviceState *st = D->state;

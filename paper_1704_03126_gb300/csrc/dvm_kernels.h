@@ -41,13 +41,14 @@ size_t sweep_smem_bytes(bool fp64, int warps, int cw);
 // 1/denominator table of the block's velocities and the 3-deep ring of column results.
 constexpr int kColsMaxThreads = 512;
 struct ColsSmemLayout {
-  size_t cst, inv, ring, recs, xseam, yseam, total;
+  size_t cst, inv, ring, recs, xseam, yseam, mbar, total;
 };
 // cell records are staged `depth` steps ahead: 5 (FP32, 48-byte records) or 4 (FP64, 64 bytes); the
 // x-seam values of a row sit in a ring of kColsSeamRows rows, the y-seam values of every column are
 // staged once at the start
 __host__ __device__ inline int cols_depth(int tsize) { return tsize == 4 ? 5 : 4; }
 constexpr int kColsSeamRows = 8;
+constexpr int kColsSpinLimit = 1 << 22;  // bounded mbarrier waits of the column sweep
 __host__ __device__ inline ColsSmemLayout cols_smem_layout(int V, int G, int ncol, int tsize) {
   ColsSmemLayout L;
   size_t off = 0;
@@ -65,6 +66,8 @@ __host__ __device__ inline ColsSmemLayout cols_smem_layout(int V, int G, int nco
   off = align16(off + (size_t)kColsSeamRows * V * 2 * G * tsize);
   L.yseam = off;
   off = align16(off + (size_t)V * ncol * 2 * G * tsize);
+  L.mbar = off;  // one mbarrier per record stage, then the block's abort flag
+  off = align16(off + (size_t)cols_depth(tsize) * 8 + 16);
   L.total = off;
   return L;
 }

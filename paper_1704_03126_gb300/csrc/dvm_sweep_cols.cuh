@@ -81,6 +81,32 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
 
 // ADJ = false: the forward sweep.  ADJ = true: the transposed sweep of the adjoint iteration (see
 // dvm_sweep.cuh): reversed traversal, transposed weights t1, t2 from the record, right-hand side
@@ -125,11 +151,14 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   T *invt = reinterpret_cast<T *>(smem + SL.inv);
   V16 *ring = reinterpret_cast<V16 *>(smem + SL.ring);
   SweepRec<T> *recs = reinterpret_cast<SweepRec<T> *>(smem + SL.recs);  // [DEPTH][ncol]
-  T *xsr = reinterpret_cast<T *>(smem + SL.xseam);  // [SR][V][2][G]: seam columns (nx-2, nx-1) of row q
+  T *xsr = reinterpret_cast<T *>(smem + SL.xseam);  // [SR][2][VB]: seam columns (nx-2, nx-1) of row q
   T *ysr = reinterpret_cast<T *>(smem + SL.yseam);  // [V][ncol][2][G]: seam rows (ny-2, ny-1) of column p
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + SL.mbar);  // [DEPTH] completion of each record stage
+  int *abort_flag = reinterpret_cast<int *>(smem + SL.mbar + DEPTH * sizeof(uint64_t));
 
   for (size_t b = threadIdx.x; b < SL.total / 16; b += blockDim.x)
     reinterpret_cast<float4 *>(smem)[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // before TMA writes to the same bytes
   __syncthreads();
   {
     const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes + sub * VB;
@@ -175,35 +204,54 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
     for (int kq = 0; kq < NQ; ++kq) *reinterpret_cast<V16 *>(dst + kq * (16 / (int)sizeof(T))) = Q::pack(src + kq * PPQ);
   };
 
-  // Nothing a step reads comes straight from global memory: the record of the cell a column reaches
-  // at step S is copied (cp.async, by the column's first thread) into stage S % DEPTH during step
-  // S - DEPTH + 1, and with it, for column 0, the previous sweep's x-seam values of that row; the
-  // y-seam values of every column are copied before the first step.  Every thread commits one group
-  // per step; waiting for all but DEPTH - 2 groups before the step's barrier makes stage S + 1
-  // visible to the whole block at step S + 1.
+  // Nothing a step reads comes straight from global memory.  The records of the cells the block
+  // reaches at step S are contiguous in the diagonal-major record array (one anti-diagonal of the
+  // quadrant); one thread copies them, and for a periodic x axis the previous sweep's seam values of
+  // row S (read by columns 0 and 1), into stage S % DEPTH with TMA bulk copies that complete on that
+  // stage's mbarrier, DEPTH - 1 steps ahead.  At the end of step S the same thread waits for stage
+  // S + 1, and the step's block barrier publishes it to every thread.  The y-seam values of every
+  // column are copied (cp.async) before the first step.
   constexpr int SEGS = G * (int)sizeof(T) / 16;  // 16-byte pieces of one thread's G values
-  auto stage = [&](int S, int slot) {
-    const int q = S - p;
-    if (S < nsteps && p < nx && q >= 0 && q < ny) {
-      const int j = yneg ? ny - 1 - q : q, i = xneg ? nx - 1 - p : p;
-      if (v == 0) {
-        const char *src = reinterpret_cast<const char *>(rec + (size_t)j * nx + i);
-        char *dst = reinterpret_cast<char *>(recs + (size_t)slot * ncol + p);
-#pragma unroll
-        for (int b = 0; b < (int)sizeof(SweepRec<T>); b += 16) cp_async16(dst + b, src + b);
-      }
-      if (px && p == 0) {
-        T *dst = xsr + (size_t)((q % SR) * V + v) * 2 * G;
+  const SweepRec<T> *__restrict__ rdiag =
+      static_cast<const SweepRec<T> *>(D->rec_diag) + (size_t)quad * diag_quadrant_size(nx, ny);
+  const T *seamx_blk = static_cast<const T *>(D->seam_x) + (size_t)g * ny * 2 * kLanes + sub * VB;
+  const bool leader = threadIdx.x == 0;
+  auto issue = [&](int S, int slot) {  // leader only
+    unsigned bytes = 0;
+    int p_lo = 0, count = 0;
+    if (S < nsteps) {
+      p_lo = max(0, S - (ny - 1));
+      count = min(nx - 1, S) - p_lo + 1;
+      bytes = (unsigned)(count * sizeof(SweepRec<T>));
+      if (px && S < ny) bytes += 2u * VB * sizeof(T);
+    }
+    // the stage's previous contents were read with ordinary loads before the last block barrier
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_arrive_expect_tx(&mbar[slot], bytes);
+    if (count > 0) {
+      bulk_g2s(recs + (size_t)slot * ncol + p_lo, rdiag + (size_t)S * nx + p_lo,
+               (unsigned)(count * sizeof(SweepRec<T>)), &mbar[slot]);
+      if (px && S < ny) {
+        const int j = yneg ? ny - 1 - S : S;
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl)
-#pragma unroll
-          for (int b = 0; b < SEGS; ++b)
-            cp_async16(dst + sl * G + b * (16 / (int)sizeof(T)),
-                       seamx + (size_t)(j * 2 + sl) * kLanes + b * (16 / (int)sizeof(T)));
+          bulk_g2s(xsr + (size_t)((S % SR) * 2 + sl) * VB, seamx_blk + (size_t)(j * 2 + sl) * kLanes,
+                   (unsigned)(VB * sizeof(T)), &mbar[slot]);
       }
     }
-    cp_async_commit();
   };
+  // bounded wait of the leader for stage S; false if it did not complete
+  auto wait_stage = [&](int S, int slot) -> bool {
+    const unsigned parity = (unsigned)(S / DEPTH) & 1u;
+    for (int spin = 0; spin < kColsSpinLimit; ++spin)
+      if (mbar_try_wait(&mbar[slot], parity)) return true;
+    return false;
+  };
+  if (leader) {
+    for (int s = 0; s < DEPTH; ++s) mbar_init(&mbar[s], 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   if (py && p < nx) {
     const int i = xneg ? nx - 1 - p : p;
     T *dst = ysr + (size_t)(v * ncol + p) * 2 * G;
@@ -214,10 +262,19 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         cp_async16(dst + sl * G + b * (16 / (int)sizeof(T)),
                    seamy + (size_t)(i * 2 + sl) * kLanes + b * (16 / (int)sizeof(T)));
   }
-#pragma unroll
-  for (int s = 0; s < DEPTH - 1; ++s) stage(s, s);
-  cp_async_wait<DEPTH - 2>();
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
+  if (leader) {
+    for (int s = 0; s < DEPTH - 1; ++s) issue(s, s);
+    if (!wait_stage(0, 0)) {
+      *abort_flag = 1;
+      atomicExch(&st->err_flag, 1);
+      for (int s = 1; s < DEPTH - 1; ++s) wait_stage(s, s);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) return;
 
   // one step: hy1 holds h(p, q-1), hy2 holds h(p, q-2); the new h(p, q) replaces hy2
   // ring slots of steps S, S-1, S-2 and the record stage of step S (rotated, not recomputed)
@@ -225,7 +282,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   auto step = [&](T2 (&hy1)[NP], T2 (&hy2)[NP], const int S) {
     const int q = S - p;
     const bool active = p < nx && q >= 0 && q < ny;
-    stage(S + DEPTH - 1, sd == 0 ? DEPTH - 1 : sd - 1);  // the stage of step S - 1, read before the last barrier
+    if (leader) issue(S + DEPTH - 1, sd == 0 ? DEPTH - 1 : sd - 1);  // the stage of step S - 1
     if (__any_sync(0xffffffffu, active)) {
       const int j = yneg ? ny - 1 - q : q, i = xneg ? nx - 1 - p : p;
       const int cell = j * nx + i;
@@ -269,7 +326,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         }
         T2 u1[NP], u2[NP];
         const int s0 = r0, s1 = r1, s2 = r2;
-        const T *xs = xsr + (size_t)((q % SR) * V + v) * 2 * G;  // staged seam of this row (column 0's)
+        const T *xs = xsr + (size_t)(q % SR) * 2 * VB + v * G;  // staged seam of this row (columns 0, 1)
         if (p >= 2) {
 #pragma unroll
           for (int kq = 0; kq < NQ; ++kq) {
@@ -291,13 +348,13 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
               for (int u = 0; u < PPQ; ++u) u1[kq * PPQ + u] = Q::pair(a, u);
             }
           } else if (px) {
-            load_vec(xs + G, u1, sshift);
+            load_vec(xs + VB, u1, sshift);
           } else {
 #pragma unroll
             for (int k = 0; k < NP; ++k) u1[k] = zero2;
           }
           if (px) {
-            load_vec(xs + p * G, u2, sshift);
+            load_vec(xs + p * VB, u2, sshift);
           } else {
 #pragma unroll
             for (int k = 0; k < NP; ++k) u2[k] = zero2;
@@ -394,7 +451,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         if (v == 0 && fyf) red_add(&facc[(size_t)cell * 4 + sidey], static_cast<double>(fy * scale));
       }
     }
-    cp_async_wait<DEPTH - 2>();
+    if (leader && S + 1 < nsteps && !wait_stage(S + 1, sd + 1 == DEPTH ? 0 : sd + 1)) *abort_flag = 1;
     __syncthreads();
     const int t = r2;
     r2 = r1;
@@ -406,9 +463,17 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   T2 ha[NP], hb[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) ha[k] = hb[k] = zero2;
-  for (int S = 0; S < nsteps; S += 2) {
+  int S = 0;
+  for (; S < nsteps; S += 2) {
     step(ha, hb, S);  // h -> hb
+    if (*abort_flag) break;
     if (S + 1 < nsteps) step(hb, ha, S + 1);
+    if (*abort_flag) break;
+  }
+  if (*abort_flag && leader) {
+    // a stage never completed: report it and wait (bounded) for the copies still in flight
+    atomicExch(&st->err_flag, 1);
+    for (int s2 = S + 1; s2 < min(nsteps, S + DEPTH + 1); ++s2) wait_stage(s2, s2 % DEPTH);
   }
 }
 
