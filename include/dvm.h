@@ -70,7 +70,10 @@ typedef struct {
   double kn;                  /* Knudsen number (> 0, +INFINITY allowed for delta = 0), or <= 0 ... */
   double delta;               /* ... to give delta >= 0 directly instead; exactly one of the two is set */
   dvm_quad quad;
-  double accommodation;       /* 1 = fully diffuse walls (the paper's case); other values: DVM_EINVAL */
+  double accommodation;       /* alpha in [0, 1] of Eq. (diffuse2): the wall value of a reflected velocity
+                                 is alpha rho_w + (1 - alpha) h(mirror v) at the face's gas cell (from the
+                                 previous iterate).  1 = fully diffuse (the paper's case).  alpha < 1 runs
+                                 on the column sweep only and has no adjoint (DVM_EINVAL there). */
   int precision;              /* dvm_precision */
   double force;               /* body-force source coefficient F along x1 (1 for the paper's Poiseuille flow) */
   int store_distribution;     /* 1 = also keep h in device memory (needed by dvm_distribution) */

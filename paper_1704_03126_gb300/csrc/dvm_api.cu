@@ -46,6 +46,10 @@ struct dvm_ctx {
   int cw = 0;                      // row sweep: chunk width preferred by this context
   int sched_kind = DVM_SWEEP_AUTO, sched_v = 0;  // sweep kernel requested by dvm_set_schedule
   int *d_adj_map = nullptr;        // sweep map of the adjoint launch
+  double alpha = 1.0;              // accommodation
+  int nwall = 0;
+  int *d_wall_slot = nullptr;      // alpha < 1: [ncell][4] face slots
+  void *d_wbuf = nullptr;          // alpha < 1: incident values at the wall faces, two parities
   dvm_batch *self = nullptr;       // batch of this context alone (built on first use)
   DeviceState *h_state = nullptr;  // pinned
   std::string err;
@@ -180,11 +184,15 @@ struct Schedule {
 
 // The column sweep needs nx * v <= kColsMaxThreads (a thread per column and velocity subset); the
 // row sweep needs ceil(nx / 16) <= 16 rows in flight, i.e. nx <= 256.
-bool resolve_schedule(int nx_max, int kind, int v, Schedule *out, std::string *why) {
+bool resolve_schedule(int nx_max, int kind, int v, Schedule *out, std::string *why, bool specular = false) {
   if (kind == DVM_SWEEP_AUTO) kind = DVM_SWEEP_COLUMNS;
   if (kind == DVM_SWEEP_ROWS) {
     if (nx_max > 16 * kMaxSweepWarps) {
       *why = "the row sweep needs nx <= 256";
+      return false;
+    }
+    if (specular) {
+      *why = "the row sweep supports fully diffuse walls only (accommodation = 1)";
       return false;
     }
     out->kind = kind;
@@ -280,6 +288,8 @@ dvm_status reset_state(dvm_ctx *c) {
   DVM_CUDA(c, cudaMemsetAsync(c->d_seamx, 0, ts * c->ngroups * c->ny * 2 * kLanes, c->stream));
   DVM_CUDA(c, cudaMemsetAsync(c->d_seamy, 0, ts * c->ngroups * c->nx * 2 * kLanes, c->stream));
   if (c->d_h) DVM_CUDA(c, cudaMemsetAsync(c->d_h, 0, ts * c->ngroups * (size_t)c->ncell * kLanes, c->stream));
+  if (c->d_wbuf)
+    DVM_CUDA(c, cudaMemsetAsync(c->d_wbuf, 0, ts * 2 * (size_t)std::max(c->nwall, 1) * 2 * c->gq * kLanes, c->stream));
   DVM_CUDA(c, launch_reset(c->d_desc, c->ncell, c->fp64, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
   return DVM_OK;
@@ -294,9 +304,10 @@ dvm_status upload_desc(dvm_ctx *c) {
 }
 
 LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const int *fin_map, int ninst, int warps,
-                       int cw, int cols_v = 0) {
+                       int cw, int cols_v = 0, bool specular = false) {
   LaunchDesc L;
   L.cols_v = cols_v;
+  L.specular = specular ? 1 : 0;
   L.inst = insts;
   L.sweep_map = sweep_map;
   L.fin_map = fin_map;
@@ -356,8 +367,10 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   dvm_ctx *c0 = ctxs[0];
   if (n > 32767) return fail(c0, DVM_EINVAL, "too many instances in one batch");
   int nx_max = 0;
+  bool spec = false;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(c0, DVM_EINVAL, "null context in batch");
+    spec = spec || ctxs[i]->alpha < 1.0;
     if (ctxs[i]->fp64 != c0->fp64 || ctxs[i]->store_h != c0->store_h)
       return fail(c0, DVM_EINVAL, "batched contexts must share precision and store_distribution");
     if (ctxs[i]->device != c0->device) return fail(c0, DVM_EINVAL, "batched contexts must share a device");
@@ -368,9 +381,11 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   Schedule sched;
   if (force) {
     sched = *force;
+    if (spec && sched.kind == DVM_SWEEP_ROWS)
+      return fail(c0, DVM_EINVAL, "the row sweep supports fully diffuse walls only (accommodation = 1)");
   } else {
     std::string why;
-    if (!resolve_schedule(nx_max, c0->sched_kind, c0->sched_v, &sched, &why)) return fail(c0, DVM_EINVAL, why);
+    if (!resolve_schedule(nx_max, c0->sched_kind, c0->sched_v, &sched, &why, spec)) return fail(c0, DVM_EINVAL, why);
   }
   const bool cols = sched.kind == DVM_SWEEP_COLUMNS;
   dvm_batch *b = new (std::nothrow) dvm_batch();
@@ -436,7 +451,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   BATCH_CUDA(cudaStreamSynchronize(b->stream));
   for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
 #undef BATCH_CUDA
-  LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw, b->cols_v);
+  LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw, b->cols_v, spec);
   b->m = iters_per_graph(upd);
   dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->uniform, b->m, true, true,
                                 &b->g_many);
@@ -605,8 +620,8 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   if (P.nx < 2 || P.ny < 2 || P.nx > 65536 || P.ny > 65536)
     return fail(nullptr, DVM_EINVAL, "nx and ny must be in [2, 65536]");
   if (!(P.ly > 0.0) || !std::isfinite(P.ly)) return fail(nullptr, DVM_EINVAL, "ly must be positive");
-  if (P.accommodation != 1.0)
-    return fail(nullptr, DVM_EINVAL, "only fully diffuse walls (accommodation = 1) are supported");
+  if (!(P.accommodation >= 0.0 && P.accommodation <= 1.0))
+    return fail(nullptr, DVM_EINVAL, "accommodation must be in [0, 1]");
   if (P.precision != DVM_FP64 && P.precision != DVM_FP32_ACC64) return fail(nullptr, DVM_EINVAL, "bad precision");
   if (!std::isfinite(P.force)) return fail(nullptr, DVM_EINVAL, "force must be finite");
   double delta;
@@ -628,6 +643,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   c->ncell = P.nx * P.ny;
   c->fp64 = P.precision == DVM_FP64;
   c->store_h = P.store_distribution != 0;
+  c->alpha = P.accommodation;
   c->delta = delta;
   c->kn = P.kn > 0.0 ? P.kn : (delta > 0 ? std::sqrt(M_PI) / (2.0 * delta) : INFINITY);
   std::string qerr;
@@ -745,6 +761,19 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   CREATE_CUDA(cudaMemcpy(c->d_code4, c->geo.code4.data(), sizeof(uint32_t) * 4 * ncell, cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemcpy(c->d_hw_src, c->geo.hw_src.data(), sizeof(int) * 8 * ncell, cudaMemcpyHostToDevice));
   CREATE_CUDA(cudaMemset(c->d_delta_field, 0, sizeof(double) * ncell));
+  if (c->alpha < 1.0) {
+    // a slot for every wall face a sweep reads (the faces behind wall-class cells)
+    std::vector<int> slot(ncell * 4, -1);
+    for (size_t k = 0; k < c->geo.hw_src.size(); ++k) {
+      const int f = c->geo.hw_src[k];
+      if (f >= 0 && slot[f] < 0) slot[f] = c->nwall++;
+    }
+    CREATE_CUDA(cudaMalloc(&c->d_wall_slot, sizeof(int) * 4 * ncell));
+    CREATE_CUDA(cudaMemcpy(c->d_wall_slot, slot.data(), sizeof(int) * 4 * ncell, cudaMemcpyHostToDevice));
+    const size_t wbytes = ts * 2 * (size_t)std::max(c->nwall, 1) * 2 * c->gq * kLanes;
+    CREATE_CUDA(cudaMalloc(&c->d_wbuf, wbytes));
+    CREATE_CUDA(cudaMemset(c->d_wbuf, 0, wbytes));
+  }
 
   // launch maps of a single-instance launch
   std::vector<int> smap(c->ngroups), fmap;
@@ -771,6 +800,10 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   D.dA_over_Lx = D.dx * D.dx / (c->nx * D.dx);
   D.delta = delta;
   D.force = P.force;
+  D.alpha = c->alpha;
+  D.nwall = c->nwall;
+  D.wall_slot = c->d_wall_slot;
+  D.wbuf = c->d_wbuf;
   D.fp32 = c->fp64 ? 0 : 1;
   D.vel = c->d_vel;
   D.inv_den = c->d_inv;
@@ -996,7 +1029,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   if (!c->a_graph) {
     Schedule sc;
     std::string why;
-    if (!resolve_schedule(c->nx, c->sched_kind, c->sched_v, &sc, &why)) return fail(c, DVM_EINVAL, why);
+    if (!resolve_schedule(c->nx, c->sched_kind, c->sched_v, &sc, &why, c->alpha < 1.0)) return fail(c, DVM_EINVAL, why);
     const bool cols = sc.kind == DVM_SWEEP_COLUMNS;
     const int parts = cols ? cols_parts(c->fp64, sc.v) : 1;
     std::vector<int> amap;
@@ -1040,6 +1073,7 @@ dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta
   dvm_ctx *c = ctx;
   if (!(tol > 0.0) || max_iter < 1) return fail(c, DVM_EINVAL, "tol must be > 0 and max_iter >= 1");
   if (!c->d_h) return fail(c, DVM_ESTATE, "dvm_adjoint needs the forward distribution (store_distribution = 1)");
+  if (c->alpha < 1.0) return fail(c, DVM_EINVAL, "dvm_adjoint supports fully diffuse walls only (accommodation = 1)");
   DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
   if (c->h_state->iter < 1) return fail(c, DVM_ESTATE, "dvm_adjoint needs a forward solve first");
@@ -1139,7 +1173,7 @@ dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column) {
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (threads_per_column < 0 || !resolve_schedule(ctx->nx, kind, threads_per_column, &sc, &why))
+  if (threads_per_column < 0 || !resolve_schedule(ctx->nx, kind, threads_per_column, &sc, &why, ctx->alpha < 1.0))
     return fail(ctx, DVM_EINVAL, why.empty() ? "bad threads_per_column" : why);
   ctx->sched_kind = sc.kind;
   ctx->sched_v = sc.v;
@@ -1159,7 +1193,7 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why))
+  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, ctx->alpha < 1.0))
     return fail(const_cast<dvm_ctx *>(ctx), DVM_EINVAL, why);
   if (kind) *kind = sc.kind;
   if (threads_per_column) *threads_per_column = sc.v;
@@ -1169,10 +1203,14 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
 dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_column) {
   if (!batch) return DVM_EINVAL;
   int nx_max = 0;
-  for (dvm_ctx *c : batch->ctxs) nx_max = std::max(nx_max, c->nx);
+  bool spec = false;
+  for (dvm_ctx *c : batch->ctxs) {
+    nx_max = std::max(nx_max, c->nx);
+    spec = spec || c->alpha < 1.0;
+  }
   Schedule sc;
   std::string why;
-  if (threads_per_column < 0 || !resolve_schedule(nx_max, kind, threads_per_column, &sc, &why))
+  if (threads_per_column < 0 || !resolve_schedule(nx_max, kind, threads_per_column, &sc, &why, spec))
     return fail(batch->ctxs[0], DVM_EINVAL, why.empty() ? "bad threads_per_column" : why);
   return batch_replan(batch, sc);
 }
@@ -1189,14 +1227,18 @@ dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *thre
   dvm_ctx *c0 = batch->ctxs[0];
   if (sweeps < 1 || sweeps > 1000) return fail(c0, DVM_EINVAL, "sweeps must be in 1..1000");
   int nx_max = 0;
-  for (dvm_ctx *c : batch->ctxs) nx_max = std::max(nx_max, c->nx);
+  bool spec = false;
+  for (dvm_ctx *c : batch->ctxs) {
+    nx_max = std::max(nx_max, c->nx);
+    spec = spec || c->alpha < 1.0;
+  }
   std::vector<Schedule> cands;
   for (int k : {DVM_SWEEP_ROWS, DVM_SWEEP_COLUMNS})
     for (int v : {0, 1, 2, 4}) {
       if ((k == DVM_SWEEP_ROWS) != (v == 0)) continue;
       Schedule sc;
       std::string why;
-      if (resolve_schedule(nx_max, k, v, &sc, &why)) cands.push_back(sc);
+      if (resolve_schedule(nx_max, k, v, &sc, &why, spec)) cands.push_back(sc);
     }
   Schedule best;
   float best_ms = INFINITY;

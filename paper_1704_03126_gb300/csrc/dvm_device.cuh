@@ -122,6 +122,11 @@ struct InstanceDesc {
   double dA_over_Lx;    // dx^2 / (nx dx)
   double delta;         // uniform collision rate
   double force;         // F
+  double alpha;         // accommodation: wall value alpha rho_w + (1 - alpha) h(mirror v), Eq. (diffuse2)
+  int nwall;            // wall faces (gas cell, side) with a solid or outside neighbour across the side
+  const int *wall_slot; // [ncell][4] -> face slot or -1 (alpha < 1 only)
+  void *wbuf;           // [2 parities][nwall][2][groups_per_quadrant][32] T: incident h at each wall face
+                        // from the previous sweep, by the sign of the velocity component along the face
   double sumW[4];       // sum W, sum W v1, sum W v2, sum W |v|^2
   double ginv[16];      // inverse Gram matrix of psi = (1, v1, v2, |v|^2) under the weights W
   double ain[4];        // per side: sum_{v.n<0} |v.n| W  (incident weight of a constant)
@@ -159,6 +164,7 @@ struct LaunchDesc {
   int cw;                    // chunk width (cells per warp and step) of the sweep: 1, 2, 4, 8 or 16
   int cols_v;                // 0: row-wavefront sweep; 1, 2, 4: column sweep with that many threads per
                              // column (the block's velocity set is split among them)
+  int specular;              // 1: some instance has accommodation < 1 (column sweep only)
 };
 
 #ifdef __CUDACC__

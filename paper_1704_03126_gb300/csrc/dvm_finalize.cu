@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
           const int src = D->hw_src[(size_t)cell * 8 + q * 2 + ax];
           if (src >= 0) {
             const int side = src & 3;
-            hw[ax] = (fcur[src] - s * D->ain[side]) / D->nrm[side];
+            // diffuse part alpha rho_w; the specular part (1 - alpha) h(mirror v) is added in the sweep
+            hw[ax] = D->alpha * (fcur[src] - s * D->ain[side]) / D->nrm[side];
           } else {
             hw[ax] = 0.0;
           }

@@ -112,7 +112,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 // dvm_sweep.cuh): reversed traversal, transposed weights t1, t2 from the record, right-hand side
 // W (A + B v1 + C v2 + D (|v|^2 - 1)) + |v1| W TX + |v2| W TY, unweighted moments, and
 // 2 |v_a|/dx z added to the wall adjoint flux of cells whose upstream neighbour is solid.
-template <typename T, bool ADJ, bool UNIF, int V>
+template <typename T, bool ADJ, bool UNIF, int V, bool SPEC>
 __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) {
   using Q = Vec<T>;
   using T2 = typename Q::T2;
@@ -185,6 +185,21 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   double *facc = D->facc + (size_t)((st->iter + 1) & 1) * ncell * 4;
   const int sidex = xneg ? kW : kE;
   const int sidey = yneg ? kS : kN;
+  // accommodation < 1 (forward only): the wall value of a wall-class cell gains (1 - alpha) times the
+  // previous sweep's value of the mirrored velocity at the same face, written by the mirrored
+  // quadrant's block at its incident cells; double-buffered by sweep parity
+  const bool spec = SPEC && !ADJ && D->alpha < 1.0;
+  const T one_m_alpha2 = static_cast<T>(2.0 * (1.0 - D->alpha));
+  const int gi = g % D->groups_per_quadrant, gq = D->groups_per_quadrant;
+  T *wbuf_wr = nullptr;
+  const T *wbuf_rd = nullptr;
+  if (spec) {
+    const size_t half = (size_t)D->nwall * 2 * gq * kLanes;
+    wbuf_wr = static_cast<T *>(D->wbuf) + (size_t)((st->iter + 1) & 1) * half;
+    wbuf_rd = static_cast<const T *>(D->wbuf) + (size_t)(st->iter & 1) * half;
+  }
+  // face record of (slot, sign of the other velocity component, group within quadrant, lanes)
+  auto wface = [&](int slot, int sgn) -> size_t { return ((size_t)(slot * 2 + sgn) * gq + gi) * kLanes + l0; };
   const int nsteps = nx + ny - 1;
   const T2 zero2 = Q::splat(T(0));
 
@@ -360,6 +375,24 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
             for (int k = 0; k < NP; ++k) u2[k] = zero2;
           }
         }
+        if (spec && !(code & kSolid)) {
+          if (((code >> kClsXShift) & 3u) == (uint32_t)kWall) {
+            const int slot = D->wall_slot[(size_t)cell * 4 + (xneg ? kE : kW)];
+            if (slot >= 0) {  // always: every wall-class face has a slot
+              load_vec(wbuf_rd + wface(slot, (quad >> 1) & 1), u1, sshift);
+              ax1 = one_m_alpha2;  // x combination 2 alpha rho_w + 2 (1 - alpha) h(mirror v)
+            }
+          }
+          if (((code >> kClsYShift) & 3u) == (uint32_t)kWall) {
+            const int slot = D->wall_slot[(size_t)cell * 4 + (yneg ? kN : kS)];
+            if (slot >= 0) {
+              // h(p, q-1) lies in a solid cell here, so its register is free; the next cell reads it
+              // only with a zero coefficient
+              load_vec(wbuf_rd + wface(slot, quad & 1), hy1, sshift);
+              ay1 = one_m_alpha2;
+            }
+          }
+        }
         const T2 sA = Q::splat(r.A), sB = Q::splat(r.B), sC = Q::splat(r.C), sD = Q::splat(r.D);
         const T2 sax1 = Q::splat(ax1), sax2 = Q::splat(ax2), say1 = Q::splat(ay1), say2 = Q::splat(ay2);
         const T2 sxw = Q::splat(xw), syw = Q::splat(yw);
@@ -449,6 +482,14 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         const T scale = ADJ ? T(2) : dx;
         if (v == 0 && fxf) red_add(&facc[(size_t)cell * 4 + sidex], static_cast<double>(fx * scale));
         if (v == 0 && fyf) red_add(&facc[(size_t)cell * 4 + sidey], static_cast<double>(fy * scale));
+        if (spec && fxf) {
+          const int slot = D->wall_slot[(size_t)cell * 4 + sidex];
+          if (slot >= 0) store_vec(wbuf_wr + wface(slot, (quad >> 1) & 1), hy2);
+        }
+        if (spec && fyf) {
+          const int slot = D->wall_slot[(size_t)cell * 4 + sidey];
+          if (slot >= 0) store_vec(wbuf_wr + wface(slot, quad & 1), hy2);
+        }
       }
     }
     if (leader && S + 1 < nsteps && !wait_stage(S + 1, sd + 1 == DEPTH ? 0 : sd + 1)) *abort_flag = 1;
@@ -477,9 +518,9 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   }
 }
 
-template <typename T, bool ADJ, bool UNIF, int V>
+template <typename T, bool ADJ, bool UNIF, int V, bool SPEC>
 cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
-  auto kern = cols_kernel<T, ADJ, UNIF, V>;
+  auto kern = cols_kernel<T, ADJ, UNIF, V, SPEC>;
   const int ncol = L.warps * (kLanes / V);
   const size_t smem = layout<T>(V, ncol).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -488,14 +529,23 @@ cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-template <typename T, bool ADJ, bool UNIF>
-cudaError_t launch_v(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+template <typename T, bool ADJ, bool UNIF, bool SPEC>
+cudaError_t launch_vs(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   switch (L.cols_v) {
-    case 1: return launch<T, ADJ, UNIF, 1>(L, nblocks, stream);
-    case 2: return launch<T, ADJ, UNIF, 2>(L, nblocks, stream);
-    case 4: return launch<T, ADJ, UNIF, 4>(L, nblocks, stream);
+    case 1: return launch<T, ADJ, UNIF, 1, SPEC>(L, nblocks, stream);
+    case 2: return launch<T, ADJ, UNIF, 2, SPEC>(L, nblocks, stream);
+    case 4: return launch<T, ADJ, UNIF, 4, SPEC>(L, nblocks, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// SPEC: some instance of the launch has partially specular walls (forward sweeps only)
+template <typename T, bool ADJ, bool UNIF>
+cudaError_t launch_v(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
+  if constexpr (!ADJ) {
+    if (L.specular) return launch_vs<T, ADJ, UNIF, true>(L, nblocks, stream);
+  }
+  return launch_vs<T, ADJ, UNIF, false>(L, nblocks, stream);
 }
 
 }  // namespace cols

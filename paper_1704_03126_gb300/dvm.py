@@ -117,12 +117,13 @@ class Solver:
     mask: uint8 [ny][nx] (1 = solid); quad = (kind, n, vmax) with kind in {"gh", "nc", "cubic"};
     exactly one of kn (> 0, inf allowed) and delta (>= 0).  stream: a cudaStream_t as int (e.g.
     torch.cuda.current_stream().cuda_stream) or None.  schedule: None (automatic), or (kind,
-    threads_per_column) for set_schedule.
+    threads_per_column) for set_schedule.  accommodation: alpha in [0, 1] of Eq. (diffuse2); below 1 the
+    walls reflect the rest specularly (column sweep only; no adjoint).
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
                  precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
-                 schedule=None):
+                 schedule=None, accommodation=1.0):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -141,6 +142,7 @@ class Solver:
         p.quad.vmax = float(quad[2]) if len(quad) > 2 else 5.0
         p.precision = {"fp64": FP64, "fp32": FP32_ACC64}[precision]
         p.force = float(force)
+        p.accommodation = float(accommodation)
         p.store_distribution = int(bool(store_distribution))
         p.sweep_warps = int(sweep_warps)
         self.params = p

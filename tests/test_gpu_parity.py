@@ -351,3 +351,46 @@ def test_enqueued_sweeps_match_iterate():
         assert abs(x.flowrate()[0] - y.flowrate()[0]) < 1e-13 * abs(x.flowrate()[0])
     s_ms, f_ms = bb.timing()
     assert s_ms > 0 and f_ms > 0
+
+
+# ------------------------------------------------------------------ accommodation < 1 (Eq. diffuse2)
+
+SPEC_CASES = [
+    # name, mask, periodic_x, periodic_y, kn, quad, alpha
+    ("plates_gh8_a0.7", inputs.plates_mask(4, 24), True, False, 0.5, ("gh", 8, 0.0), 0.7),
+    ("rough24_nc8_a0.5", inputs.rough_channel_mask(24), True, False, 1.0, ("nc", 8, 4.0), 0.5),
+    ("block_periodic_cubic10_a0.8", _block_mask(20, 16), True, True, 1.0, ("cubic", 10, 4.0), 0.8),
+    ("porous40_cubic12_a0.3", inputs.porous_disks_mask(40, 0.6, 4, 6, seed=5)[0], True, True, 2.0, ("cubic", 12, 4.0), 0.3),
+]
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES[1:], ids=SCHED_IDS[1:])
+@pytest.mark.parametrize("case", SPEC_CASES, ids=[c[0] for c in SPEC_CASES])
+def test_partially_specular_walls_match_oracle_fp64(case, schedule):
+    name, mask, px, py, kn, quad, alpha = case
+    sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision="fp64", schedule=schedule, accommodation=alpha)
+    sol.solve(tol=1e-12, max_iter=200000)
+    orc = oracle.solve(oracle.Problem.make(mask, px, py, dvm.kn_to_delta(kn), quad, alpha=alpha), tol=1e-12,
+                       max_iter=200000)
+    assert orc["converged"]
+    _compare(sol, orc, mask, "fp64")
+
+
+def test_partially_specular_walls_fp32_and_restrictions():
+    name, mask, px, py, kn, quad, alpha = SPEC_CASES[1]
+    sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision="fp32", accommodation=alpha, store_distribution=True)
+    assert sol.schedule()[0] == "columns"
+    sol.solve(tol=1e-6, max_iter=200000)
+    orc = oracle.solve(oracle.Problem.make(mask, px, py, dvm.kn_to_delta(kn), quad, alpha=alpha), tol=1e-12,
+                       max_iter=200000)
+    _compare(sol, orc, mask, "fp32")
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.set_schedule("rows")
+    assert ei.value.status == dvm.DVM_EINVAL
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.adjoint()
+    assert ei.value.status == dvm.DVM_EINVAL
+    # specular walls carry more flow than diffuse ones
+    diffuse = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision="fp32")
+    diffuse.solve(tol=1e-6, max_iter=200000)
+    assert sol.flowrate()[0] > diffuse.flowrate()[0]

@@ -68,6 +68,8 @@ def test_library_rejects_invalid_grids():
     dict(mask=np.zeros((8, 8), np.uint8), kn=-1.0),                    # neither kn nor delta
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, quad=("gh", 7)),     # odd velocity grid
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, ly=0.0),             # bad height
+    dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, accommodation=1.5),  # accommodation outside [0, 1]
+    dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, accommodation=-0.1),
 ])
 def test_create_rejects_invalid_parameters(kwargs):
     with pytest.raises(dvm.DvmError) as ei:
