@@ -65,7 +65,7 @@ def parse():
                     help="keep warming up for at least this long (clock sampling); 0 for profiling")
     ap.add_argument("--workload", default="rough", choices=sorted(METRICS))
     ap.add_argument("--schedule", default="autotune",
-                    help="sweep kernel: autotune, rows, columns1, columns2, columns4")
+                    help="sweep kernel: autotune, rows, rows<cw> (chunk width), columns1, columns2, columns4")
     ap.add_argument("--fd-cells", type=int, default=16, help="adjoint workload: cells checked by central differences")
     return ap.parse_args()
 
@@ -113,13 +113,13 @@ def apply_schedule(batch, spec):
     """Pick the batch's sweep kernel: the library autotuner (5 timed sweeps per candidate) or a fixed one."""
     if spec == "autotune":
         kind, v, ms = batch.autotune(5)
-        return {"kernel": kind, "threads_per_column": v, "tuned_sweep_ms": ms, "by": "autotuner"}
-    if spec == "rows":
-        batch.set_schedule("rows", 0)
+        return {"kernel": kind, "shape": v, "tuned_sweep_ms": ms, "by": "autotuner"}
+    if spec.startswith("rows"):
+        batch.set_schedule("rows", int(spec[4:] or 0))
     else:
         batch.set_schedule("columns", int(spec[len("columns"):]))
     kind, v = batch.schedule()
-    return {"kernel": kind, "threads_per_column": v, "by": "fixed"}
+    return {"kernel": kind, "shape": v, "by": "fixed"}
 
 
 def max_over_ranks(ms, world, device="cpu"):
@@ -276,8 +276,8 @@ def run_ours(args, rank, world, local_rank):
         r = results[prec]
         achieved = FLOPS_PER_UPDATE * upd / (r["sweep_ms"] / 1e3) / 1e12
         sc = schedules[prec]
-        kname = ("sweep_kernel" if sc["kernel"] == "rows"
-                 else f"cols_kernel, {sc['threads_per_column']} thread(s) per column")
+        kname = (f"sweep_kernel, chunk width {sc['shape']}" if sc["kernel"] == "rows"
+                 else f"cols_kernel, {sc['shape']} thread(s) per column")
         return {"bound": "alu", "achieved": achieved, "peak": peak[prec], "unit": "TFLOP/s",
                 "frac": achieved / peak[prec], "traffic": None,
                 "kernel": f"{kname} ({prec})", "schedule": sc, "flops_per_update": FLOPS_PER_UPDATE,
@@ -432,7 +432,8 @@ def run_adjoint(args, rank, world, local_rank):
         probe.close()
         sched = (kind, v)
     else:
-        sched = ("rows", 0) if args.schedule == "rows" else ("columns", int(args.schedule[7:]))
+        sched = (("rows", int(args.schedule[4:] or 0)) if args.schedule.startswith("rows")
+                 else ("columns", int(args.schedule[7:])))
     sol = solver(True, sched)
     sampler = ClockSampler(local_rank)
     sampler.start()

@@ -84,7 +84,8 @@ typedef struct {
 
 /* The transport sweep kernel (both compute the same update; see dvm_set_schedule):
  *   DVM_SWEEP_ROWS     a thread block per group of 32 velocities, lanes = velocities, warps = rows in
- *                      flight of a row wavefront; nx <= 256.
+ *                      flight of a row wavefront, each advancing `shape` cells (the chunk width: 1, 2,
+ *                      4, 8 or 16; 0 = the narrowest with at most 16 rows in flight); nx <= 256.
  *   DVM_SWEEP_COLUMNS  threads = grid columns walking an anti-diagonal wavefront, each with 8 (FP32)
  *                      or 4 (FP64) velocities; `threads_per_column` (1, 2 or 4) threads share a
  *                      column, so a block holds 8, 16 or 32 (FP32) velocities; nx * threads_per_column
@@ -158,13 +159,14 @@ dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info);
  * adjoint state (about as much as the forward state plus one more distribution) on first use. */
 dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta, double *q_identity, int *iters);
 
-/* Choose the sweep kernel of the context's own solves and adjoint (dvm_sweep_kind; threads_per_column
- * 0 = automatic, used by DVM_SWEEP_COLUMNS only).  DVM_EINVAL if the grid does not fit the choice.
+/* Choose the sweep kernel of the context's own solves and adjoint (dvm_sweep_kind) and its shape
+ * (threads_per_column for DVM_SWEEP_COLUMNS, the chunk width for DVM_SWEEP_ROWS; 0 = automatic).
+ * DVM_EINVAL if the grid does not fit the choice.
  * Results agree to rounding; speed differs with the grid width and the number of velocity groups.
  * Default: DVM_SWEEP_AUTO.  Batches created later start from the first member's choice. */
-dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column);
-/* The resolved choice (kind is never DVM_SWEEP_AUTO; threads_per_column 0 for rows). */
-dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_column);
+dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int shape);
+/* The resolved choice (kind is never DVM_SWEEP_AUTO; for rows the second value is the chunk width). */
+dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *shape);
 
 /* Distribution h of selected velocities (needs store_distribution = 1).  ks: host int [nk] with
  * k = a * n + b for v = (x_a, x_b) on the 1D nodes in ascending order.  out: host double
@@ -204,13 +206,14 @@ dvm_status dvm_batch_check(dvm_batch *batch);
  * on the batch stream); read it after the stream has reached them. */
 dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms);
 /* Re-plan the batch's sweep launch for another kernel (see dvm_set_schedule); state is kept. */
-dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_column);
-dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *threads_per_column);
-/* Autotuner: time every sweep kernel that fits the batch's grids (rows; columns with 1, 2, 4 threads
- * per column) over `sweeps` single sweeps each (CUDA events, median), keep the fastest and return it
+dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int shape);
+dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *shape);
+/* Autotuner: time every sweep kernel that fits the batch's grids (rows at three chunk widths; columns
+ * with 1, 2, 4 threads per column) over `sweeps` single sweeps each (CUDA events, median), keep the
+ * fastest and return it
  * (any output may be NULL; sweep_ms is its median sweep time).  The trial sweeps are ordinary source
  * iterations: they advance every member's state. */
-dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *threads_per_column, float *sweep_ms);
+dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *shape, float *sweep_ms);
 /* Kernel launches issued per sweep of the batch (sweep + finalize kernels). */
 int dvm_batch_kernels_per_sweep(const dvm_batch *batch);
 void dvm_batch_destroy(dvm_batch *batch);

@@ -176,7 +176,8 @@ bool table_sums(const dvm_ctx *c, const std::vector<T> &vel, InstanceDesc &D) {
   return true;
 }
 
-// Sweep schedule: the row-wavefront kernel (v = 0) or the column kernel with v threads per column.
+// Sweep schedule: the row-wavefront kernel with chunk width v (cells per warp and step; 0 = the
+// members' own choice) or the column kernel with v threads per column.
 struct Schedule {
   int kind = DVM_SWEEP_COLUMNS;
   int v = 1;
@@ -195,8 +196,16 @@ bool resolve_schedule(int nx_max, int kind, int v, Schedule *out, std::string *w
       *why = "the row sweep supports fully diffuse walls only (accommodation = 1)";
       return false;
     }
+    if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16) {
+      *why = "the row sweep's chunk width must be 1, 2, 4, 8 or 16";
+      return false;
+    }
+    if (v != 0 && (nx_max + v - 1) / v > kMaxSweepWarps) {
+      *why = "chunk width too small: more than 16 rows in flight";
+      return false;
+    }
     out->kind = kind;
-    out->v = 0;
+    out->v = v;
     return true;
   }
   if (kind != DVM_SWEEP_COLUMNS) {
@@ -404,6 +413,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
     b->cw = std::max(b->cw, ctxs[i]->cw);
     b->uniform = b->uniform && ctxs[i]->uniform;
   }
+  if (!cols && sched.v > 0) b->cw = sched.v;
   b->warps = 1;
   std::vector<InstanceDesc> descs(n);
   std::vector<int> smap, fmap;
@@ -1039,8 +1049,9 @@ dvm_status adjoint_setup(dvm_ctx *c) {
     DVM_CUDA(c, cudaMalloc(&c->d_adj_map, sizeof(int) * amap.size()));
     DVM_CUDA(c, cudaMemcpyAsync(c->d_adj_map, amap.data(), sizeof(int) * amap.size(), cudaMemcpyHostToDevice, c->stream));
     DVM_CUDA(c, cudaStreamSynchronize(c->stream));
-    const int warps = cols ? (c->nx + kLanes / sc.v - 1) / (kLanes / sc.v) : (c->nx + c->cw - 1) / c->cw;
-    LaunchDesc L = make_launch(c->a_desc, c->d_adj_map, c->d_fin_map, 1, warps, c->cw, cols ? sc.v : 0);
+    const int cw = (!cols && sc.v > 0) ? sc.v : c->cw;
+    const int warps = cols ? (c->nx + kLanes / sc.v - 1) / (kLanes / sc.v) : (c->nx + cw - 1) / cw;
+    LaunchDesc L = make_launch(c->a_desc, c->d_adj_map, c->d_fin_map, 1, warps, cw, cols ? sc.v : 0);
     const int sweep_blocks = (int)amap.size();
     const int fin_blocks = c->hdesc.fin_nblocks;
     const int lines = (c->hdesc.periodic_x ? c->ngroups * c->ny : 0) + (c->hdesc.periodic_y ? c->ngroups * c->nx : 0);
@@ -1196,7 +1207,7 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
   if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, ctx->alpha < 1.0))
     return fail(const_cast<dvm_ctx *>(ctx), DVM_EINVAL, why);
   if (kind) *kind = sc.kind;
-  if (threads_per_column) *threads_per_column = sc.v;
+  if (threads_per_column) *threads_per_column = (sc.kind == DVM_SWEEP_ROWS && sc.v == 0) ? ctx->cw : sc.v;
   return DVM_OK;
 }
 
@@ -1218,7 +1229,7 @@ dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_co
 dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *threads_per_column) {
   if (!batch) return DVM_EINVAL;
   if (kind) *kind = batch->kind;
-  if (threads_per_column) *threads_per_column = batch->cols_v;
+  if (threads_per_column) *threads_per_column = batch->kind == DVM_SWEEP_ROWS ? batch->cw : batch->cols_v;
   return DVM_OK;
 }
 
@@ -1233,13 +1244,20 @@ dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *thre
     spec = spec || c->alpha < 1.0;
   }
   std::vector<Schedule> cands;
-  for (int k : {DVM_SWEEP_ROWS, DVM_SWEEP_COLUMNS})
-    for (int v : {0, 1, 2, 4}) {
-      if ((k == DVM_SWEEP_ROWS) != (v == 0)) continue;
+  {
+    // the row kernel at its narrowest chunk (most rows in flight) and two wider ones
+    const int cw0 = choose_cw(nx_max, kMaxSweepWarps);
+    for (int cw : {cw0, 2 * cw0, 4 * cw0}) {
       Schedule sc;
       std::string why;
-      if (resolve_schedule(nx_max, k, v, &sc, &why, spec)) cands.push_back(sc);
+      if (cw <= 16 && resolve_schedule(nx_max, DVM_SWEEP_ROWS, cw, &sc, &why, spec)) cands.push_back(sc);
     }
+    for (int v : {1, 2, 4}) {
+      Schedule sc;
+      std::string why;
+      if (resolve_schedule(nx_max, DVM_SWEEP_COLUMNS, v, &sc, &why, spec)) cands.push_back(sc);
+    }
+  }
   Schedule best;
   float best_ms = INFINITY;
   for (const Schedule &sc : cands) {
@@ -1263,7 +1281,7 @@ dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *thre
   dvm_status st = batch_replan(batch, best);
   if (st != DVM_OK) return st;
   if (kind) *kind = best.kind;
-  if (threads_per_column) *threads_per_column = best.v;
+  if (threads_per_column) *threads_per_column = best.v;  // rows: the chunk width
   if (sweep_ms) *sweep_ms = best_ms;
   return DVM_OK;
 }

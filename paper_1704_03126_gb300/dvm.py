@@ -117,7 +117,7 @@ class Solver:
     mask: uint8 [ny][nx] (1 = solid); quad = (kind, n, vmax) with kind in {"gh", "nc", "cubic"};
     exactly one of kn (> 0, inf allowed) and delta (>= 0).  stream: a cudaStream_t as int (e.g.
     torch.cuda.current_stream().cuda_stream) or None.  schedule: None (automatic), or (kind,
-    threads_per_column) for set_schedule.  accommodation: alpha in [0, 1] of Eq. (diffuse2); below 1 the
+    shape) for set_schedule.  accommodation: alpha in [0, 1] of Eq. (diffuse2); below 1 the
     walls reflect the rest specularly (column sweep only; no adjoint).
     """
 
@@ -173,9 +173,10 @@ class Solver:
     def reset(self):
         return self._check(lib().dvm_reset(self._ctx))
 
-    def set_schedule(self, kind="auto", threads_per_column=0):
-        """Sweep kernel of this solver: "rows", "columns" (threads_per_column 1, 2, 4 or 0 = auto) or "auto"."""
-        return self._check(lib().dvm_set_schedule(self._ctx, SWEEP_KINDS[kind], int(threads_per_column)))
+    def set_schedule(self, kind="auto", shape=0):
+        """Sweep kernel of this solver: "rows" (shape = chunk width 1..16, 0 = auto), "columns" (shape =
+        threads per column 1, 2, 4, 0 = auto) or "auto"."""
+        return self._check(lib().dvm_set_schedule(self._ctx, SWEEP_KINDS[kind], int(shape)))
 
     def schedule(self):
         k, v = ctypes.c_int(), ctypes.c_int()
@@ -297,8 +298,8 @@ class Batch:
     def kernels_per_sweep(self):
         return lib().dvm_batch_kernels_per_sweep(self._b)
 
-    def set_schedule(self, kind="auto", threads_per_column=0):
-        st = lib().dvm_batch_set_schedule(self._b, SWEEP_KINDS[kind], int(threads_per_column))
+    def set_schedule(self, kind="auto", shape=0):
+        st = lib().dvm_batch_set_schedule(self._b, SWEEP_KINDS[kind], int(shape))
         if st != DVM_OK:
             self._err(st)
 
@@ -311,7 +312,7 @@ class Batch:
 
     def autotune(self, sweeps=5):
         """Time every fitting sweep kernel (the trial sweeps advance the state); keeps the fastest.
-        Returns (kind, threads_per_column, median sweep ms)."""
+        Returns (kind, shape, median sweep ms); shape is the chunk width for "rows"."""
         k, v, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         st = lib().dvm_batch_autotune(self._b, int(sweeps), ctypes.byref(k), ctypes.byref(v), ctypes.byref(ms))
         if st != DVM_OK:

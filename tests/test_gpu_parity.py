@@ -122,7 +122,8 @@ FP32_SLOW = {"ragged37x29_block_gh8", "ragged37x29_warps5", "narrow3x40_nonperio
 def test_small_geometries_match_oracle_fp64(case, schedule):
     name, mask, px, py, kn, quad, warps = case
     sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp64", 1e-12, schedule=schedule, sweep_warps=warps)
-    assert sol.schedule() == schedule
+    kind, shape = sol.schedule()
+    assert kind == schedule[0] and (kind == "rows" or shape == schedule[1])
     _compare(sol, orc, mask, "fp64")
 
 
@@ -231,10 +232,12 @@ def test_autotune_picks_a_fitting_kernel_and_keeps_the_state():
     refs = [dvm.Solver(m, True, False, kn=kn, quad=q, precision="fp32") for m, q, kn in specs]
     b = dvm.Batch(sols)
     kind, v, ms = b.autotune(sweeps=3)
-    assert (kind, v) in SCHEDULES and ms > 0
+    assert kind in ("rows", "columns") and ms > 0
     assert b.schedule() == (kind, v)
     done = sols[0].info()["iterations"]
-    assert done == 4 * (1 + 3)  # rows + three column variants, each 1 warm-up + 3 timed sweeps
+    # rows at two chunk widths (8, 16 cells for 96 columns) and three column variants, each one
+    # warm-up and three timed sweeps
+    assert done == 5 * (1 + 3)
     b.iterate(10)
     for r in refs:
         r.iterate(done + 10)
@@ -250,6 +253,8 @@ def test_wide_grid_runs_on_the_column_sweep_only():
     assert sol.schedule() == ("columns", 1)
     with pytest.raises(dvm.DvmError):
         sol.set_schedule("rows")
+    with pytest.raises(dvm.DvmError):
+        sol.set_schedule("rows", 3)
     with pytest.raises(dvm.DvmError):
         sol.set_schedule("columns", 2)
     sol.iterate(5)
