@@ -49,6 +49,10 @@ UNIT = "updates/s"
 # FP32 / FP64 operations per interior cell-velocity update of the sweep kernel:
 # right-hand side 3 FMA, two upwind combinations 2 x (FMA + MUL), update 2 FMA + MUL, moments 4 FMA
 FLOPS_PER_UPDATE = 25
+# DRAM bytes (read + write) of one sweep-kernel launch, from an ncu capture of this benchmark's command
+# (profiles/sweep_fp32_rough128x3_kn0.1-1-10.md), keyed by (workload, precision, kernel, shape); other
+# launch configurations report null
+NCU_TRAFFIC = {("rough", "fp32", "rows", 8): 14.35e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -278,8 +282,10 @@ def run_ours(args, rank, world, local_rank):
         sc = schedules[prec]
         kname = (f"sweep_kernel, chunk width {sc['shape']}" if sc["kernel"] == "rows"
                  else f"cols_kernel, {sc['shape']} thread(s) per column")
+        traffic = NCU_TRAFFIC.get((args.workload, prec, sc["kernel"], sc["shape"]))
         return {"bound": "alu", "achieved": achieved, "peak": peak[prec], "unit": "TFLOP/s",
-                "frac": achieved / peak[prec], "traffic": None,
+                "frac": achieved / peak[prec], "traffic": traffic,
+                "traffic_per_update_bytes": None if traffic is None else traffic / upd,
                 "kernel": f"{kname} ({prec})", "schedule": sc, "flops_per_update": FLOPS_PER_UPDATE,
                 "peak_note": ("FP32 FMA units x max SM clock" if prec == "fp32"
                               else "FP64 units (2 FMA/SM/clk) x max SM clock") + ", derived (of unit counts)",

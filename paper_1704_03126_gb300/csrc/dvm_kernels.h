@@ -40,6 +40,7 @@ size_t sweep_smem_bytes(bool fp64, int warps, int cw);
 // Column sweep (dvm_sweep_cols.cuh): shared-memory layout -- per-pair velocity constants, the
 // 1/denominator table of the block's velocities and the 3-deep ring of column results.
 constexpr int kColsMaxThreads = 512;
+constexpr int kColsCstFields = 12;  // per-velocity constants of the column sweep (see dvm_sweep_cols.cuh)
 struct ColsSmemLayout {
   size_t cst, inv, ring, recs, xseam, yseam, mbar, total;
 };
@@ -55,7 +56,7 @@ __host__ __device__ inline ColsSmemLayout cols_smem_layout(int V, int G, int nco
   auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   const int VB = V * G;
   L.cst = off;
-  off = align16(off + (size_t)VB * 8 * tsize);
+  off = align16(off + (size_t)VB * kColsCstFields * tsize);
   L.inv = off;
   off = align16(off + (size_t)kInvRows * VB * tsize);
   L.ring = off;

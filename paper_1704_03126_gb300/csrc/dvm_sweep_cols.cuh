@@ -62,8 +62,11 @@ struct ColsG {
   static constexpr int value = sizeof(T) == 4 ? 8 : 4;
 };
 
-// per-pair constant fields in shared memory ([VB / 2][kCstFields] pairs)
-enum : int { kCV1 = 0, kCV2, kCE, kCCx, kCCy, kCWm, kCWr, kCPad, kCstFields };
+// per-pair constant fields in shared memory ([VB / 2][kCstFields] pairs): v1, v2, |v|^2 - 1, |v1|/dx,
+// |v2|/dx, the moment weight w (W forward, 1 on real lanes for the adjoint), the adjoint's W, and
+// the products w v1, w v2, w (|v|^2 - 1) that let FP64 accumulate each moment with one FMA
+enum : int { kCV1 = 0, kCV2, kCE, kCCx, kCCy, kCWm, kCWr, kCWv1, kCWv2, kCWe, kCPad0, kCPad1, kCstFields };
+static_assert(kCstFields == kColsCstFields, "shared-memory layout");
 
 template <typename T>
 __host__ __device__ inline ColsSmemLayout layout(int V, int ncol) {
@@ -164,9 +167,18 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
     const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes + sub * VB;
     for (int t = threadIdx.x; t < VB * kCstFields; t += blockDim.x) {
       const int vl = t % VB, f = t / VB;
-      const int fld = f == kCV1 ? kV1 : f == kCV2 ? kV2 : f == kCE ? kE2m1 : f == kCCx ? kCx : f == kCCy ? kCy
-                    : f == kCWm ? (ADJ ? kZ0 : kW0) : kW0;
-      cstT[((vl >> 1) * kCstFields + f) * 2 + (vl & 1)] = f == kCPad ? T(0) : vt[fld * kLanes + vl];
+      const int wm = ADJ ? kZ0 : kW0;
+      T val;
+      if (f == kCWv1) val = vt[wm * kLanes + vl] * vt[kV1 * kLanes + vl];
+      else if (f == kCWv2) val = vt[wm * kLanes + vl] * vt[kV2 * kLanes + vl];
+      else if (f == kCWe) val = vt[wm * kLanes + vl] * vt[kE2m1 * kLanes + vl];
+      else if (f >= kCPad0) val = T(0);
+      else {
+        const int fld = f == kCV1 ? kV1 : f == kCV2 ? kV2 : f == kCE ? kE2m1 : f == kCCx ? kCx : f == kCCy ? kCy
+                      : f == kCWm ? wm : kW0;
+        val = vt[fld * kLanes + vl];
+      }
+      cstT[((vl >> 1) * kCstFields + f) * 2 + (vl & 1)] = val;
     }
     if (UNIF) {
       const T *iv = static_cast<const T *>(D->inv_den) + (size_t)g * kInvRows * kLanes + sub * VB;
@@ -419,11 +431,19 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           else iv = Q::rcp2(Q::fma2(ccx, skx, Q::fma2(ccy, sky, sdl)));
           const T2 h = Q::mul2(Q::fma2(ccx, bx, Q::fma2(ccy, by, Rk)), iv);
           hy2[k] = h;
-          const T2 wh = Q::mul2(cwm, h);
-          M0 = Q::add2(M0, wh);
-          M1 = Q::fma2(cv1, wh, M1);
-          M2 = Q::fma2(cv2, wh, M2);
-          M3 = Q::fma2(ce, wh, M3);
+          if constexpr (sizeof(T) == 8) {
+            // FP64 is bound by the FMA pipe: one FMA per moment with the premultiplied weights
+            M0 = Q::fma2(cwm, h, M0);
+            M1 = Q::fma2(c[kCWv1], h, M1);
+            M2 = Q::fma2(c[kCWv2], h, M2);
+            M3 = Q::fma2(c[kCWe], h, M3);
+          } else {
+            const T2 wh = Q::mul2(cwm, h);
+            M0 = Q::add2(M0, wh);
+            M1 = Q::fma2(cv1, wh, M1);
+            M2 = Q::fma2(cv2, wh, M2);
+            M3 = Q::fma2(ce, wh, M3);
+          }
         }
 #pragma unroll
         for (int kq = 0; kq < NQ; ++kq) *ring_at(s0, p, kq) = Q::pack(hy2 + kq * PPQ);
