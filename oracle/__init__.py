@@ -45,7 +45,7 @@ class _Problem(ctypes.Structure):
         ("dx", ctypes.c_double),
         ("mask", ctypes.c_void_p), ("delta", ctypes.c_void_p),
         ("nv", ctypes.c_int), ("xv", ctypes.c_void_p), ("wv", ctypes.c_void_p),
-        ("alpha", ctypes.c_double), ("force", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("force", ctypes.c_double), ("top_u", ctypes.c_double),
     ]
 
 
@@ -112,17 +112,20 @@ class Problem:
     alpha: float = 1.0
     force: float = 1.0
     ly: float = 1.0
+    top_u: float = 0.0          # speed of the plate beyond the last row (Couette flow), 0 = at rest
 
     @staticmethod
-    def make(mask, periodic_x, periodic_y, delta, quad=("gh", 8, 5.0), alpha=1.0, force=1.0, ly=1.0):
+    def make(mask, periodic_x, periodic_y, delta, quad=("gh", 8, 5.0), alpha=1.0, force=1.0, ly=1.0, top_u=0.0):
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         ny, nx = mask.shape
         d = np.broadcast_to(np.asarray(delta, dtype=np.float64), (ny, nx))
         kind, n = quad[0], quad[1]
         vmax = quad[2] if len(quad) > 2 else 5.0
         xv, wv = quadrature(kind, n, vmax)
+        if top_u != 0.0 and periodic_y:
+            raise ValueError("a moving top plate needs a non-periodic x2 axis")
         return Problem(mask, bool(periodic_x), bool(periodic_y), np.ascontiguousarray(d), xv, wv,
-                       float(alpha), float(force), float(ly))
+                       float(alpha), float(force), float(ly), float(top_u))
 
     @property
     def nx(self):
@@ -151,7 +154,7 @@ class Problem:
         self._keep = (self.mask, self.delta, self.xv, self.wv)
         return _Problem(self.nx, self.ny, int(self.periodic_x), int(self.periodic_y), self.dx,
                         self.mask.ctypes.data, self.delta.ctypes.data, self.nv,
-                        self.xv.ctypes.data, self.wv.ctypes.data, self.alpha, self.force)
+                        self.xv.ctypes.data, self.wv.ctypes.data, self.alpha, self.force, self.top_u)
 
 
 def delta_from_kn(kn: float) -> float:

@@ -13,7 +13,9 @@ plus the scalar c that borders the system:
 with M_k(h) = sum_j W_j psi(v_k)^T G^{-1} psi(v_j) h_j, psi = (1, v1, v2, |v|^2), G the quadrature
 Gram matrix of psi: the projection of h onto the collision invariants, which for an exact quadrature
 is rho + 2 u.v + tau (|v|^2 - 1) with the moments rho, u, tau of Sec. II.A.  Wall values h_w = alpha rho_w + (1 - alpha) h(mirror v), with
-rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W at the gas cell owning the face.
+rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W at the gas cell owning the face; the plate beyond
+the last row may move along x1 with speed U (Couette flow, Eq. diffuse1), adding alpha 2 U v1 to its
+wall value (a source term of the system).
 """
 from __future__ import annotations
 
@@ -83,6 +85,7 @@ def assemble(prob):
         for k in range(K):
             row = idx(k, g)
             diag = d
+            src = prob.force * v1[k]
             for axis in (0, 1):
                 va = v1[k] if axis == 0 else v2[k]
                 s = 1 if va > 0 else -1
@@ -94,6 +97,9 @@ def assemble(prob):
                 if _solid(mask, px, py, i1, j1):
                     diag += ca * 2.0
                     add_wall(row, ca * 2.0, g, side, k)
+                    if side == "N" and not py and j == ny - 1 and prob.top_u != 0.0:
+                        # the moving plate's wall value carries the drift 2 U v1 (Eq. diffuse1)
+                        src += ca * 2.0 * prob.alpha * 2.0 * prob.top_u * v1[k]
                 elif _solid(mask, px, py, i2, j2):
                     # second cell from a wall: first-order upwind through the gas neighbour
                     diag += ca
@@ -110,7 +116,7 @@ def assemble(prob):
             for jv in range(K):
                 B[row, idx(jv, g)] -= d * Ckern[k, jv]
             B[row, n] += d
-            b[row] = prob.force * v1[k]
+            b[row] = src
     for g in range(G):
         for k in range(K):
             B[n, idx(k, g)] = W[k]

@@ -32,6 +32,9 @@
  *             on linear fields.  The quadratic through h0, h(u1) and the wall value would put a
  *             negative weight on the lagged wall value, and the iteration then diverges in narrow
  *             pores (an oscillating mode), so the second cell from a wall is first order.
+ *   moving    the plate beyond the last row (x2 = H, non-periodic x2) may move along x1 with speed
+ *             U (Couette flow, Sec. II.A, Eq. diffuse1): its reflected molecules carry the drift
+ *             2 U v1 in addition to rho_w; every other wall is at rest (Eq. diffuse2).
  *   wall      h_w = alpha rho_w + (1 - alpha) h(mirror v) at the face's gas cell, where
  *             rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W (discrete zero mass flux).
  *   collision the discrete L is the projection of h onto span{1, v1, v2, |v|^2} in the quadrature
@@ -157,6 +160,7 @@ typedef struct {
   const double *xv, *wv;     /* 1D nodes and weights; velocity k = a*nv + b has v = (x_a, x_b) */
   double alpha;              /* accommodation: 1 = fully diffuse walls */
   double force;              /* body-force source coefficient F (source F v1) */
+  double top_u;              /* speed U along x1 of the plate beyond the last row (Couette), or 0 */
 } orc_problem;
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
@@ -316,6 +320,9 @@ static double wall_value(const orc_problem *p, const double *rho_w, const double
                          int side, int k) {
   size_t ncell = (size_t)p->nx * p->ny;
   double hw = p->alpha * rho_w[c * 4 + side];
+  /* the moving plate: the wall Maxwellian drifts with U, rho_w + 2 U v1 (Eq. diffuse1) */
+  if (p->top_u != 0.0 && side == SIDE_N && !p->periodic_y && (int)(c / p->nx) == p->ny - 1)
+    hw += p->alpha * 2.0 * p->top_u * p->xv[k / p->nv];
   if (p->alpha < 1.0) hw += (1.0 - p->alpha) * h_old[(size_t)mirror_velocity(p, k, side) * ncell + c];
   return hw;
 }

@@ -105,6 +105,52 @@ def porous_disks_mask(n: int = 256, porosity: float = 0.6, rmin: int = 8, rmax: 
     return mask, float(1.0 - mask.mean())
 
 
+def wm_roughness(x: np.ndarray, D: float = 1.5, gamma: float = 1.5, n1: int = -4, n_max: int = 8) -> np.ndarray:
+    """Weierstrass-Mandelbrot profile of Eq. (WM) with unit scale A: sum over n = n1 .. n_max of
+    cos(2 pi gamma^n x) / gamma^((2 - D) n), x in units of H.  The paper sums to infinity; a grid
+    resolves frequencies up to its Nyquist limit, so the caller truncates there."""
+    r = np.zeros_like(np.asarray(x, dtype=np.float64))
+    for n in range(n1, n_max + 1):
+        r += np.cos(2.0 * math.pi * gamma ** n * x) / gamma ** ((2.0 - D) * n)
+    return r
+
+
+def couette_rough_mask(gap_cells: int = 100, aspect: float = 5.0, eps: float = 0.02, D: float = 1.5,
+                       gamma: float = 1.5, n1: int = -4):
+    """Staircase bottom wall with the WM roughness of Sec. II below a smooth top plate (Couette flow).
+
+    The channel is aspect * H long and has a mean gap H = gap_cells cells; the profile of Eq. (WM) is
+    sampled at the cell centres, truncated at the grid's Nyquist frequency (gamma^n <= 1 / (2 dx)),
+    and scaled so that its root mean square is eps * H (Eq. for epsilon).  A cell is solid when its
+    centre lies below base + r(x), with a base of whole rows under the deepest valley.
+    Returns (mask [ny][nx], ly): ly = ny dx is the domain height to pass as the grid height.
+    """
+    dx = 1.0 / gap_cells
+    nx = int(round(aspect * gap_cells))
+    x = (np.arange(nx) + 0.5) * dx
+    n_max = int(math.floor(math.log(1.0 / (2.0 * dx)) / math.log(gamma)))
+    r = wm_roughness(x, D, gamma, n1, n_max)
+    r *= eps / math.sqrt(float(np.mean(r * r)))
+    base_rows = int(math.ceil(max(0.0, -float(r.min())) / dx)) + 1
+    ny = gap_cells + base_rows
+    yc = (np.arange(ny) + 0.5) * dx
+    mask = (yc[:, None] < base_rows * dx + r[None, :]).astype(np.uint8)
+    return mask, ny * dx
+
+
+def couette_instance(kn: float, gap_cells: int = 100, aspect: float = 5.0, eps: float = 0.02, nv: int = 32,
+                     rough: bool = True) -> Instance:
+    """Couette flow of Sec. II: smooth top plate moving with U = 1 (in units of v_m), bottom plate at
+    rest, rough (WM staircase) or smooth, x1 periodic, no body force; cubic nv x nv velocities."""
+    if rough:
+        mask, ly = couette_rough_mask(gap_cells, aspect, eps)
+    else:
+        mask, ly = plates_mask(int(round(aspect * gap_cells)), gap_cells), 1.0
+    name = f"couette{'_wm' if rough else '_smooth'}{mask.shape[1]}x{mask.shape[0]}_cubic{nv}_kn{kn:g}"
+    return Instance(name, mask, True, False, kn, ("cubic", nv, 4.0),
+                    {"ly": ly, "top_u": 1.0, "force": 0.0, "eps": eps if rough else 0.0})
+
+
 def kn_to_delta(kn: float) -> float:
     """Rarefaction delta = sqrt(pi) / (2 Kn) (coefficient of the BGK operator); Kn = inf gives 0."""
     return 0.0 if math.isinf(kn) else math.sqrt(math.pi) / (2.0 * kn)

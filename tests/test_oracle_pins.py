@@ -236,3 +236,70 @@ def test_sweep_selected_reproduces_fixed_point():
     ks = [0, 5, 17, 40, 63]
     out = oracle.sweep_selected(p, r["h"], r["c"], ks)
     assert np.abs(out - r["h"][ks]).max() < 1e-11 * np.abs(r["h"]).max()
+
+
+# ---------------------------------------------------------------- Couette flow (Sec. II, Eq. diffuse1)
+
+@pytest.mark.parametrize("quad", [("gh", 8, 0.0), ("nc", 8, 4.0), ("cubic", 8, 4.0)])
+@pytest.mark.parametrize("kn", [0.1, 1.0, 10.0])
+def test_plane_couette_flow_rate_is_half(kn, quad):
+    """Smooth plates, the top one moving with U = 1: the linearized problem with walls at (0, U) is the
+    one with walls at (-U/2, U/2) plus the uniform drift 2 (U/2) v1, which the collision operator,
+    the transport and the diffuse walls all leave invariant (rho_w of the drift vanishes on a
+    symmetric grid); the former is odd under the mirror (x2 -> H - x2, v -> -v).  So u1 is the drift's
+    U sum_k W_k v1_k^2 = U m0 m2 (m0 = sum w_a, m2 = sum w_a x_a^2 of the 1D rule) plus an odd part,
+    and Q = U H m0 m2 at every Kn: the paper's Q_s = 0.5 (Sec. II) for a rule exact on x^2 (Gauss-
+    Hermite), and the rule's own second moment otherwise."""
+    ny = 16
+    p = oracle.Problem.make(np.zeros((ny, 4), np.uint8), True, False, oracle.delta_from_kn(kn), quad,
+                            force=0.0, top_u=1.0)
+    m0, m2 = float(p.wv.sum()), float((p.wv * p.xv ** 2).sum())
+    if quad[0] == "gh":
+        assert abs(m0 * m2 - 0.5) < 1e-14
+    r = oracle.solve(p, tol=1e-13, max_iter=400000)
+    assert r["converged"]
+    assert abs(r["Q"] - m0 * m2) < 1e-10
+    u1 = r["u1"][:, 0]
+    assert np.max(np.abs(u1 + u1[::-1] - 2.0 * m0 * m2)) < 1e-10
+    assert np.all(np.diff(u1) > 0)  # the shear profile rises towards the moving plate
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+def test_couette_iteration_matches_dense_solve(alpha):
+    """A rough bottom under a moving plate: the iteration's fixed point against the direct solve
+    (the moving plate enters the dense system as a source term)."""
+    mask = np.zeros((6, 6), np.uint8)
+    mask[0, 1:3] = 1
+    mask[1, 2] = 1
+    p = oracle.Problem.make(mask, True, False, 1.2, ("gh", 6, 0.0), alpha=alpha, force=0.0, top_u=1.0)
+    ds = dense.solve(p)
+    r = oracle.solve(p, tol=1e-14, max_iter=400000)
+    assert r["converged"]
+    assert abs(r["Q"] - ds["Q"]) < 1e-11 * abs(ds["Q"])
+    assert np.max(np.abs(r["h"] - ds["h"])) < 1e-10 * max(1.0, np.abs(ds["h"]).max())
+
+
+def test_couette_force_and_moving_plate_superpose():
+    """The problem is linear: force-driven plus moving-plate flow rates add."""
+    mask = inputs.couette_rough_mask(8, aspect=2.0, eps=0.05)[0]
+    quad = ("gh", 6, 0.0)
+    q = {}
+    for name, force, u in (("force", 1.0, 0.0), ("plate", 0.0, 1.0), ("both", 1.0, 1.0)):
+        p = oracle.Problem.make(mask, True, False, 1.0, quad, force=force, top_u=u, ly=mask.shape[0] / 8)
+        q[name] = oracle.solve(p, tol=1e-13, max_iter=400000)["Q"]
+    assert abs(q["both"] - q["force"] - q["plate"]) < 1e-10 * abs(q["both"])
+
+
+def test_wm_roughness_has_the_requested_rms():
+    mask, ly = inputs.couette_rough_mask(40, aspect=5.0, eps=0.02)
+    ny, nx = mask.shape
+    assert nx == 200 and abs(ly - ny / 40) < 1e-12
+    # the staircase height of every column tracks base + r(x) to within a cell
+    dx = 1.0 / 40
+    x = (np.arange(nx) + 0.5) * dx
+    r = inputs.wm_roughness(x, n_max=int(math.floor(math.log(20.0) / math.log(1.5))))
+    r *= 0.02 / math.sqrt(np.mean(r * r))
+    heights = mask.sum(axis=0) * dx
+    base = heights.mean() - r.mean()
+    assert np.max(np.abs(heights - (base + r))) <= dx
+    assert mask[-1].sum() == 0  # the top rows are gas: the moving plate lies beyond the last row
