@@ -80,6 +80,11 @@ typedef struct {
   int sweep_warps;            /* row sweep only: upper bound on rows in flight (warps) per sweep block,
                                  1..16; 0 = 16.  The chunk width is the smallest of 1, 2, 4, 8, 16
                                  cells with ceil(nx / width) rows within the bound. */
+  double top_wall_u1;         /* speed U along x1 of the plate beyond the last row (x2 = H; needs a
+                                 non-periodic x2 axis): Couette flow, Sec. II, Eq. (diffuse1) with
+                                 U0/v_m = U: its reflected molecules carry the drift 2 U v1.  0 = at rest
+                                 (every other wall is at rest).  A moving plate runs on the column sweep
+                                 only and has no adjoint (DVM_EINVAL there). */
 } dvm_params;
 
 /* The transport sweep kernel (both compute the same update; see dvm_set_schedule):
@@ -94,7 +99,7 @@ typedef struct {
 typedef enum { DVM_SWEEP_AUTO = 0, DVM_SWEEP_ROWS = 1, DVM_SWEEP_COLUMNS = 2 } dvm_sweep_kind;
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
- * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape. */
+ * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape, plates at rest. */
 dvm_status dvm_params_init(dvm_params *params);
 
 /* Build a solver for one geometry.

@@ -47,6 +47,7 @@ struct dvm_ctx {
   int sched_kind = DVM_SWEEP_AUTO, sched_v = 0;  // sweep kernel requested by dvm_set_schedule
   int *d_adj_map = nullptr;        // sweep map of the adjoint launch
   double alpha = 1.0;              // accommodation
+  double top_u = 0.0;              // speed of the plate beyond the last row (Couette flow)
   int nwall = 0;
   int *d_wall_slot = nullptr;      // alpha < 1: [ncell][4] face slots
   void *d_wbuf = nullptr;          // alpha < 1: incident values at the wall faces, two parities
@@ -193,7 +194,7 @@ bool resolve_schedule(int nx_max, int kind, int v, Schedule *out, std::string *w
       return false;
     }
     if (specular) {
-      *why = "the row sweep supports fully diffuse walls only (accommodation = 1)";
+      *why = "the row sweep supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)";
       return false;
     }
     if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16) {
@@ -379,7 +380,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   bool spec = false;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(c0, DVM_EINVAL, "null context in batch");
-    spec = spec || ctxs[i]->alpha < 1.0;
+    spec = spec || ctxs[i]->alpha < 1.0 || ctxs[i]->top_u != 0.0;
     if (ctxs[i]->fp64 != c0->fp64 || ctxs[i]->store_h != c0->store_h)
       return fail(c0, DVM_EINVAL, "batched contexts must share precision and store_distribution");
     if (ctxs[i]->device != c0->device) return fail(c0, DVM_EINVAL, "batched contexts must share a device");
@@ -391,7 +392,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   if (force) {
     sched = *force;
     if (spec && sched.kind == DVM_SWEEP_ROWS)
-      return fail(c0, DVM_EINVAL, "the row sweep supports fully diffuse walls only (accommodation = 1)");
+      return fail(c0, DVM_EINVAL, "the row sweep supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)");
   } else {
     std::string why;
     if (!resolve_schedule(nx_max, c0->sched_kind, c0->sched_v, &sched, &why, spec)) return fail(c0, DVM_EINVAL, why);
@@ -605,6 +606,7 @@ dvm_status dvm_params_init(dvm_params *p) {
   p->force = 1.0;
   p->store_distribution = 0;
   p->sweep_warps = 0;
+  p->top_wall_u1 = 0.0;
   return DVM_OK;
 }
 
@@ -632,6 +634,9 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   if (!(P.ly > 0.0) || !std::isfinite(P.ly)) return fail(nullptr, DVM_EINVAL, "ly must be positive");
   if (!(P.accommodation >= 0.0 && P.accommodation <= 1.0))
     return fail(nullptr, DVM_EINVAL, "accommodation must be in [0, 1]");
+  if (!std::isfinite(P.top_wall_u1)) return fail(nullptr, DVM_EINVAL, "top_wall_u1 must be finite");
+  if (P.top_wall_u1 != 0.0 && P.periodic_y)
+    return fail(nullptr, DVM_EINVAL, "a moving top plate needs a non-periodic x2 axis");
   if (P.precision != DVM_FP64 && P.precision != DVM_FP32_ACC64) return fail(nullptr, DVM_EINVAL, "bad precision");
   if (!std::isfinite(P.force)) return fail(nullptr, DVM_EINVAL, "force must be finite");
   double delta;
@@ -654,6 +659,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   c->fp64 = P.precision == DVM_FP64;
   c->store_h = P.store_distribution != 0;
   c->alpha = P.accommodation;
+  c->top_u = P.top_wall_u1;
   c->delta = delta;
   c->kn = P.kn > 0.0 ? P.kn : (delta > 0 ? std::sqrt(M_PI) / (2.0 * delta) : INFINITY);
   std::string qerr;
@@ -811,6 +817,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   D.delta = delta;
   D.force = P.force;
   D.alpha = c->alpha;
+  D.top_u = c->top_u;
   D.nwall = c->nwall;
   D.wall_slot = c->d_wall_slot;
   D.wbuf = c->d_wbuf;
@@ -1039,7 +1046,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   if (!c->a_graph) {
     Schedule sc;
     std::string why;
-    if (!resolve_schedule(c->nx, c->sched_kind, c->sched_v, &sc, &why, c->alpha < 1.0)) return fail(c, DVM_EINVAL, why);
+    if (!resolve_schedule(c->nx, c->sched_kind, c->sched_v, &sc, &why, c->alpha < 1.0 || c->top_u != 0.0)) return fail(c, DVM_EINVAL, why);
     const bool cols = sc.kind == DVM_SWEEP_COLUMNS;
     const int parts = cols ? cols_parts(c->fp64, sc.v) : 1;
     std::vector<int> amap;
@@ -1084,7 +1091,8 @@ dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta
   dvm_ctx *c = ctx;
   if (!(tol > 0.0) || max_iter < 1) return fail(c, DVM_EINVAL, "tol must be > 0 and max_iter >= 1");
   if (!c->d_h) return fail(c, DVM_ESTATE, "dvm_adjoint needs the forward distribution (store_distribution = 1)");
-  if (c->alpha < 1.0) return fail(c, DVM_EINVAL, "dvm_adjoint supports fully diffuse walls only (accommodation = 1)");
+  if (c->alpha < 1.0 || c->top_u != 0.0)
+    return fail(c, DVM_EINVAL, "dvm_adjoint supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)");
   DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
   if (c->h_state->iter < 1) return fail(c, DVM_ESTATE, "dvm_adjoint needs a forward solve first");
@@ -1184,7 +1192,7 @@ dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column) {
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (threads_per_column < 0 || !resolve_schedule(ctx->nx, kind, threads_per_column, &sc, &why, ctx->alpha < 1.0))
+  if (threads_per_column < 0 || !resolve_schedule(ctx->nx, kind, threads_per_column, &sc, &why, ctx->alpha < 1.0 || ctx->top_u != 0.0))
     return fail(ctx, DVM_EINVAL, why.empty() ? "bad threads_per_column" : why);
   ctx->sched_kind = sc.kind;
   ctx->sched_v = sc.v;
@@ -1204,7 +1212,7 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, ctx->alpha < 1.0))
+  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, ctx->alpha < 1.0 || ctx->top_u != 0.0))
     return fail(const_cast<dvm_ctx *>(ctx), DVM_EINVAL, why);
   if (kind) *kind = sc.kind;
   if (threads_per_column) *threads_per_column = (sc.kind == DVM_SWEEP_ROWS && sc.v == 0) ? ctx->cw : sc.v;
@@ -1217,7 +1225,7 @@ dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_co
   bool spec = false;
   for (dvm_ctx *c : batch->ctxs) {
     nx_max = std::max(nx_max, c->nx);
-    spec = spec || c->alpha < 1.0;
+    spec = spec || c->alpha < 1.0 || c->top_u != 0.0;
   }
   Schedule sc;
   std::string why;
@@ -1241,7 +1249,7 @@ dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *thre
   bool spec = false;
   for (dvm_ctx *c : batch->ctxs) {
     nx_max = std::max(nx_max, c->nx);
-    spec = spec || c->alpha < 1.0;
+    spec = spec || c->alpha < 1.0 || c->top_u != 0.0;
   }
   std::vector<Schedule> cands;
   {

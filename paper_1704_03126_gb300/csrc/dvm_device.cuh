@@ -32,6 +32,7 @@ enum : uint32_t {
   kAdjT2X = 1u << 14, // t2 = -1/2 along x
   kAdjT1YShift = 15,  // 2 bits: t1 along y
   kAdjT2Y = 1u << 17,
+  kTopWall = 1u << 18,  // the upstream y wall of this quadrant is the plate beyond the last row
 };
 enum : int { kFull = 0, kNear = 1, kWall = 2 };
 // sides of a cell: the solid neighbour lies at -x (W), +x (E), -y (S), +y (N)
@@ -123,6 +124,7 @@ struct InstanceDesc {
   double delta;         // uniform collision rate
   double force;         // F
   double alpha;         // accommodation: wall value alpha rho_w + (1 - alpha) h(mirror v), Eq. (diffuse2)
+  double top_u;         // speed along x1 of the plate beyond the last row (Couette flow), or 0
   int nwall;            // wall faces (gas cell, side) with a solid or outside neighbour across the side
   const int *wall_slot; // [ncell][4] -> face slot or -1 (alpha < 1 only)
   void *wbuf;           // [2 parities][nwall][2][groups_per_quadrant][32] T: incident h at each wall face
@@ -164,7 +166,7 @@ struct LaunchDesc {
   int cw;                    // chunk width (cells per warp and step) of the sweep: 1, 2, 4, 8 or 16
   int cols_v;                // 0: row-wavefront sweep; 1, 2, 4: column sweep with that many threads per
                              // column (the block's velocity set is split among them)
-  int specular;              // 1: some instance has accommodation < 1 (column sweep only)
+  int specular;              // 1: some instance has accommodation < 1 or a moving plate (column sweep only)
 };
 
 #ifdef __CUDACC__

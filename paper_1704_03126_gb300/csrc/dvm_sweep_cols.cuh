@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   // previous sweep's value of the mirrored velocity at the same face, written by the mirrored
   // quadrant's block at its incident cells; double-buffered by sweep parity
   const bool spec = SPEC && !ADJ && D->alpha < 1.0;
+  // a moving plate beyond the last row (Couette flow, Eq. diffuse1): its wall value alpha (rho_w +
+  // 2 U v1) adds 4 alpha U v1 to the y combination of the cells under it (forward only)
+  const T top_term = static_cast<T>(4.0 * D->alpha * D->top_u);
   const T one_m_alpha2 = static_cast<T>(2.0 * (1.0 - D->alpha));
   const int gi = g % D->groups_per_quadrant, gq = D->groups_per_quadrant;
   T *wbuf_wr = nullptr;
@@ -405,6 +408,11 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
             }
           }
         }
+        T mw = T(0);
+        if constexpr (SPEC && !ADJ) {
+          if ((code & kTopWall) && !(code & kSolid) && ((code >> kClsYShift) & 3u) == (uint32_t)kWall) mw = top_term;
+        }
+        const T2 smw = Q::splat(mw);
         const T2 sA = Q::splat(r.A), sB = Q::splat(r.B), sC = Q::splat(r.C), sD = Q::splat(r.D);
         const T2 sax1 = Q::splat(ax1), sax2 = Q::splat(ax2), say1 = Q::splat(ay1), say2 = Q::splat(ay2);
         const T2 sxw = Q::splat(xw), syw = Q::splat(yw);
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           const T2 cv1 = c[kCV1], cv2 = c[kCV2], ce = c[kCE], ccx = c[kCCx], ccy = c[kCCy], cwm = c[kCWm];
           T2 Rk = Q::fma2(sD, ce, Q::fma2(sC, cv2, Q::fma2(sB, cv1, sA)));
           if (ADJ) Rk = Q::mul2(c[kCWr], Q::fma2(ccx, stx, Q::fma2(ccy, sty, Rk)));
-          const T2 by = Q::fma2(say1, hy1[k], Q::fma2(say2, hy2[k], syw));
+          const T2 by = Q::fma2(say1, hy1[k], Q::fma2(say2, hy2[k], (SPEC && !ADJ) ? Q::fma2(smw, cv1, syw) : syw));
           const T2 bx = Q::fma2(sax1, u1[k], Q::fma2(sax2, u2[k], sxw));
           T2 iv;
           if (UNIF) iv = *reinterpret_cast<const T2 *>(invt + irow * VB + v * G + 2 * k);
@@ -559,7 +567,7 @@ cudaError_t launch_vs(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   }
 }
 
-// SPEC: some instance of the launch has partially specular walls (forward sweeps only)
+// SPEC: some instance of the launch has partially specular walls or a moving plate (forward sweeps only)
 template <typename T, bool ADJ, bool UNIF>
 cudaError_t launch_v(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   if constexpr (!ADJ) {

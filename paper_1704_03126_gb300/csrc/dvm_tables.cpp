@@ -167,6 +167,7 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
             cls = kNear;
           }
           code |= (uint32_t)cls << kClsYShift;
+          if (!py && j == ny - 1 && sy < 0) code |= kTopWall;
           G.hw_src[(size_t)cell * 8 + q * 2 + 1] = src;
           if (solid(i, j + sy)) code |= kIncY;
         }

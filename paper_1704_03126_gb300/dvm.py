@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("ly", ctypes.c_double), ("kn", ctypes.c_double), ("delta", ctypes.c_double),
         ("quad", Quad), ("accommodation", ctypes.c_double), ("precision", ctypes.c_int),
         ("force", ctypes.c_double), ("store_distribution", ctypes.c_int), ("sweep_warps", ctypes.c_int),
+        ("top_wall_u1", ctypes.c_double),
     ]
 
 
@@ -118,12 +119,13 @@ class Solver:
     exactly one of kn (> 0, inf allowed) and delta (>= 0).  stream: a cudaStream_t as int (e.g.
     torch.cuda.current_stream().cuda_stream) or None.  schedule: None (automatic), or (kind,
     shape) for set_schedule.  accommodation: alpha in [0, 1] of Eq. (diffuse2); below 1 the
-    walls reflect the rest specularly (column sweep only; no adjoint).
+    walls reflect the rest specularly (column sweep only; no adjoint).  top_wall_u1: speed of the plate
+    beyond the last row (Couette flow; column sweep only; no adjoint).
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
                  precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
-                 schedule=None, accommodation=1.0):
+                 schedule=None, accommodation=1.0, top_wall_u1=0.0):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -143,6 +145,7 @@ class Solver:
         p.precision = {"fp64": FP64, "fp32": FP32_ACC64}[precision]
         p.force = float(force)
         p.accommodation = float(accommodation)
+        p.top_wall_u1 = float(top_wall_u1)
         p.store_distribution = int(bool(store_distribution))
         p.sweep_warps = int(sweep_warps)
         self.params = p

@@ -399,3 +399,44 @@ def test_partially_specular_walls_fp32_and_restrictions():
     diffuse = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision="fp32")
     diffuse.solve(tol=1e-6, max_iter=200000)
     assert sol.flowrate()[0] > diffuse.flowrate()[0]
+
+
+# ------------------------------------------------------------------ Couette flow (Sec. II, Eq. diffuse1)
+
+@pytest.mark.parametrize("alpha", [1.0, 0.7])
+@pytest.mark.parametrize("schedule", SCHEDULES[1:], ids=SCHED_IDS[1:])
+def test_couette_over_wm_wall_matches_oracle(schedule, alpha):
+    """Smooth top plate moving with U = 1 over a Weierstrass-Mandelbrot staircase bottom, no force."""
+    mask, ly = inputs.couette_rough_mask(12, aspect=5.0, eps=0.05)
+    quad = ("cubic", 8, 4.0)
+    sol = dvm.Solver(mask, True, False, kn=0.5, quad=quad, precision="fp64", ly=ly, force=0.0,
+                     top_wall_u1=1.0, accommodation=alpha, schedule=schedule)
+    sol.solve(tol=1e-12, max_iter=200000)
+    p = oracle.Problem.make(mask, True, False, dvm.kn_to_delta(0.5), quad, alpha=alpha, force=0.0, ly=ly,
+                            top_u=1.0)
+    orc = oracle.solve(p, tol=1e-12, max_iter=200000)
+    assert orc["converged"]
+    _compare(sol, orc, mask, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plane_couette_flow_rate_is_half_on_the_gpu(precision):
+    """Gauss-Hermite velocities integrate v1^2 exactly, so smooth plates give Q = U H / 2 at any Kn."""
+    for kn in (0.1, 1.0, 10.0):
+        sol = dvm.Solver(inputs.plates_mask(4, 16), True, False, kn=kn, quad=("gh", 8, 0.0), precision=precision,
+                         force=0.0, top_wall_u1=1.0)
+        sol.solve(tol=1e-12 if precision == "fp64" else 1e-6, max_iter=200000)
+        assert abs(sol.flowrate()[0] - 0.5) < (1e-10 if precision == "fp64" else 1e-5)
+
+
+def test_moving_plate_restrictions():
+    sol = dvm.Solver(inputs.plates_mask(4, 8), True, False, kn=1.0, quad=("gh", 4, 0.0), force=0.0,
+                     top_wall_u1=1.0, store_distribution=True)
+    assert sol.schedule()[0] == "columns"
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.set_schedule("rows")
+    assert ei.value.status == dvm.DVM_EINVAL
+    sol.solve(tol=1e-10)
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.adjoint()
+    assert ei.value.status == dvm.DVM_EINVAL

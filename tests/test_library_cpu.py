@@ -70,6 +70,7 @@ def test_library_rejects_invalid_grids():
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, ly=0.0),             # bad height
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, accommodation=1.5),  # accommodation outside [0, 1]
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, accommodation=-0.1),
+    dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, periodic_y=True, top_wall_u1=1.0),  # moving plate, periodic x2
 ])
 def test_create_rejects_invalid_parameters(kwargs):
     with pytest.raises(dvm.DvmError) as ei:
