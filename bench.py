@@ -15,6 +15,10 @@ Other workloads, one JSON line each:
            compared with 64 plain solves.
   adjoint  porous 256 x 256 (porosity 0.5), cubic 32 x 32, Kn = 1, FP64: one step = one transposed
            (adjoint) sweep; gradient checked against central differences of forward solves.
+  couette  Couette flow of Sec. II: top plate moving with U = 1, no force, 500 columns (aspect 5,
+           dx = H / 100), bottom wall a Weierstrass-Mandelbrot staircase (D = 1.5, eps = 2 %) or smooth,
+           cubic 32 x 32 velocities, Kn = 0.1, 1, 10: six instances advanced together; reports
+           Q* = Q_rough / Q_smooth per Kn from the converged solves.
 
 The sweep kernel of every launch is chosen by the library's autotuner before the timed region.
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
@@ -37,12 +41,15 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 KNS = (0.1, 1.0, 10.0)
+COUETTE_GAP = 100  # cells across the mean gap H of the Couette channels (500 columns at aspect 5)
 POROUS_KNS = (0.05, 0.5, 5.0)
 METRICS = {
     "rough": "DVM cell-velocity updates/s (rough channel 128x128, 32x32 velocities, Kn 0.1/1/10)",
     "porous": "DVM cell-velocity updates/s (porous 256x256 phi 0.6, cubic 48x48 velocities, Kn 0.05/0.5/5)",
     "batched": "DVM cell-velocity updates/s (64 mixed instances, one batched launch per kernel)",
     "adjoint": "adjoint sweep cell-velocity updates/s (porous 256x256 phi 0.5, cubic 32x32, Kn 1, FP64)",
+    "couette": "DVM cell-velocity updates/s (Couette, WM-rough and smooth 500-column channels, cubic 32x32, "
+               "Kn 0.1/1/10)",
 }
 METRIC = METRICS["rough"]
 UNIT = "updates/s"
@@ -83,6 +90,9 @@ WORKLOAD_TEXT = {
                "velocities; one launch per kernel per sweep",
     "adjoint": "periodic disk medium 256x256 (porosity 0.5, seed 1), cubic 32x32 velocities, Kn 1, FP64; "
                "transposed sweeps of the adjoint iteration at the converged forward state",
+    "couette": "Couette flow, top plate U = 1, no force, x1 periodic, 500 columns (aspect 5, dx = H/100): "
+               "Weierstrass-Mandelbrot staircase bottom (D 1.5, gamma 1.5, n1 -4, eps 2%, truncated at the "
+               "grid Nyquist frequency) and smooth plates, cubic 32x32 velocities |v|<=4, Kn 0.1/1/10 batched",
 }
 
 
@@ -108,9 +118,29 @@ def instances(workload="rough"):
             _INSTANCES[workload] = [inputs.porous_instance(kn) for kn in POROUS_KNS]
         elif workload == "batched":
             _INSTANCES[workload] = inputs.batched_instances(64)
+        elif workload == "couette":
+            _INSTANCES[workload] = [inputs.couette_instance(kn, gap_cells=COUETTE_GAP, rough=rough)
+                                    for rough in (True, False) for kn in KNS]
         else:
             _INSTANCES[workload] = [inputs.porous_instance(1.0, nv=32, porosity=0.5, seed=1)]
     return _INSTANCES[workload]
+
+
+def drive(inst):
+    """Grid height, body force and top-plate speed of an instance (force-driven flow unless it says)."""
+    x = inst.extra
+    return {"ly": float(x.get("ly", 1.0)), "force": float(x.get("force", 1.0)), "top_wall_u1": float(x.get("top_u", 0.0))}
+
+
+def solver(dvm, inst, precision, stream):
+    return dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, kn=inst.kn, quad=inst.quad,
+                      precision=precision, stream=stream, **drive(inst))
+
+
+def oracle_problem(oracle, inst):
+    d = drive(inst)
+    return oracle.Problem.make(inst.mask, inst.periodic_x, inst.periodic_y, oracle.delta_from_kn(inst.kn), inst.quad,
+                               force=d["force"], ly=d["ly"], top_u=d["top_wall_u1"])
 
 
 def apply_schedule(batch, spec):
@@ -208,8 +238,7 @@ def run_ours(args, rank, world, local_rank):
     upd = updates_per_step(insts)
 
     def make(precision):
-        return [dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, kn=inst.kn, quad=inst.quad,
-                           precision=precision, stream=stream.cuda_stream) for inst in insts]
+        return [solver(dvm, inst, precision, stream.cuda_stream) for inst in insts]
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -333,8 +362,7 @@ def e2e(args, insts, stream, dvm, torch, sweeps=50, reps=3):
     h2d = d2h = 0
     for _ in range(reps):
         for inst in insts:
-            s = dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, kn=inst.kn, quad=inst.quad,
-                           precision=args.precision, stream=stream.cuda_stream)
+            s = solver(dvm, inst, args.precision, stream.cuda_stream)
             s.iterate(sweeps)
             q, _ = s.flowrate()
             f = s.fields()
@@ -378,10 +406,20 @@ def converge(results, insts, torch, max_iter=200000):
                      "converged_plain": sum(v["status"] == 0 for v in per.values()),
                      "converged_batched": int((np.asarray(status) == 0).sum()), "instances": len(insts),
                      "max_rel_dQ_batched_vs_plain": max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(bq, pq))}
-        if len(insts) <= 4:
+        if len(insts) <= 6:
             out[prec]["plain"] = per
             out[prec]["batched_Q"] = bq
+        if any(i.extra.get("top_u", 0.0) != 0.0 for i in insts):
+            out[prec]["Q_star"] = couette_q_star(insts, bq)
     return out
+
+
+def couette_q_star(insts, q):
+    """Q* = Q_r / Q_s of Sec. II at each Kn: flow rate over the rough wall over that of smooth plates."""
+    rough = {i.kn: v for i, v in zip(insts, q) if i.extra.get("eps", 0.0) > 0.0}
+    smooth = {i.kn: v for i, v in zip(insts, q) if i.extra.get("eps", 0.0) == 0.0}
+    return {f"{kn:g}": {"Q_r": rough[kn], "Q_s": smooth[kn], "Q_star": rough[kn] / smooth[kn]}
+            for kn in sorted(rough) if kn in smooth}
 
 
 def cpu_baseline(insts, workload="rough", budget_s=12.0):
@@ -389,8 +427,8 @@ def cpu_baseline(insts, workload="rough", budget_s=12.0):
     middle Knudsen number, or the first batched instance)."""
     import oracle
 
-    inst = insts[1] if len(insts) == 3 else insts[0]
-    p = oracle.Problem.make(inst.mask, inst.periodic_x, inst.periodic_y, oracle.delta_from_kn(inst.kn), inst.quad)
+    inst = insts[1] if len(insts) in (3, 6) else insts[0]
+    p = oracle_problem(oracle, inst)
     K = inst.quad[1] ** 2
     h = np.zeros((K, p.ny, p.nx))
     t0 = time.perf_counter()
@@ -539,7 +577,7 @@ def run_reference(args):
     import oracle
 
     insts = instances(args.workload if args.workload != "adjoint" else "rough")
-    probs = [oracle.Problem.make(i.mask, i.periodic_x, i.periodic_y, oracle.delta_from_kn(i.kn), i.quad) for i in insts]
+    probs = [oracle_problem(oracle, i) for i in insts]
     states = [np.zeros((i.quad[1] ** 2, p.ny, p.nx)) for i, p in zip(insts, probs)]
     upd = updates_per_step(insts)
     for _ in range(args.warmup):
