@@ -63,6 +63,18 @@ typedef enum {
   DVM_FP32_ACC64 = 1 /* distribution stored and swept in FP32; moments, wall fluxes, residual and Q in FP64 */
 } dvm_precision;
 
+/* How the grid is held in device memory.  Both sweep kernels run their wavefront along the stored
+ * x2 axis and spread the stored x1 axis over threads (column sweep: one thread per stored column,
+ * at most 512; row sweep: rows in flight across the stored x1, at most 256 cells), so a wide, short
+ * grid (e.g. the Couette channel of Sec. II, aspect 5) runs faster, and up to 65536 cells long,
+ * when stored transposed.  Every argument and result of this API stays in the caller's layout
+ * ([ny][nx], x1 along the flow) whatever the storage. */
+typedef enum {
+  DVM_STORAGE_AUTO = 0,       /* transposed when nx > ny */
+  DVM_STORAGE_AS_GIVEN = 1,
+  DVM_STORAGE_TRANSPOSED = 2
+} dvm_storage;
+
 typedef struct {
   int nx, ny;                 /* cells along x1 (flow) and x2; both >= 2 */
   int periodic_x, periodic_y; /* 1 = periodic axis; a non-periodic axis is closed by diffuse walls */
@@ -85,9 +97,12 @@ typedef struct {
                                  U0/v_m = U: its reflected molecules carry the drift 2 U v1.  0 = at rest
                                  (every other wall is at rest).  A moving plate runs on the column sweep
                                  only and has no adjoint (DVM_EINVAL there). */
+  int storage;                /* dvm_storage; the width limits of the sweeps (nx <= 256 rows, 512
+                                 columns) apply to the stored x1 axis */
 } dvm_params;
 
-/* The transport sweep kernel (both compute the same update; see dvm_set_schedule):
+/* The transport sweep kernel (both compute the same update; see dvm_set_schedule; nx below is the
+ * stored x1 extent, see dvm_storage):
  *   DVM_SWEEP_ROWS     a thread block per group of 32 velocities, lanes = velocities, warps = rows in
  *                      flight of a row wavefront, each advancing `shape` cells (the chunk width: 1, 2,
  *                      4, 8 or 16; 0 = the narrowest with at most 16 rows in flight); nx <= 256.
@@ -99,7 +114,8 @@ typedef struct {
 typedef enum { DVM_SWEEP_AUTO = 0, DVM_SWEEP_ROWS = 1, DVM_SWEEP_COLUMNS = 2 } dvm_sweep_kind;
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
- * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape, plates at rest. */
+ * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape, plates at rest,
+ * automatic storage. */
 dvm_status dvm_params_init(dvm_params *params);
 
 /* Build a solver for one geometry.
@@ -143,11 +159,13 @@ dvm_status dvm_flowrate(const dvm_ctx *ctx, double *Q, double *k_a);
 dvm_status dvm_fields(const dvm_ctx *ctx, double *rho, double *u1, double *u2, double *tau);
 
 /* Diagnostics of the current state: sweeps run since the last reset, last eps and estimate, the
- * accumulated mass shift c of the mean-density projection, and the stored status of the last solve. */
+ * accumulated mass shift c of the mean-density projection, the stored status of the last solve, and
+ * whether the grid is stored transposed (dvm_storage). */
 typedef struct {
   int iterations;
   double eps, est, mass_shift, Q;
   int status;
+  int transposed;
 } dvm_info;
 dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info);
 

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kBlock) aseam_kernel(const InstanceDesc *D) {
 }
 
 // Adjoint moments -> collision coefficients alpha = delta G^{-T} Z + (0, dA/Lx, 0, 0) per cell, the
-// sums for mu and sum lambda, the relative change of Z1 = sum v1 z (stopping test).
+// sums for mu and sum lambda, the relative change of Z1 = sum v_flow z (stopping test); v_flow = v1, or
+// v2 for an instance stored transposed (then g and Z1 use the second moment).
 __global__ void __launch_bounds__(kBlock) afin1_kernel(const InstanceDesc *D) {
   __shared__ double sh[32];
   DeviceState *st = D->state;
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(kBlock) afin1_kernel(const InstanceDesc *D) {
       for (int j = 0; j < 4; ++j) y += D->ginv[j * 4 + i] * Z[j];
       al[i] = d * y;
     }
-    al[1] += D->dA_over_Lx;  // g = W v1 dA / Lx
+    (D->flow_axis ? al[2] : al[1]) += D->dA_over_Lx;  // g = W v_flow dA / L
+    const double zf = D->flow_axis ? Z[2] : Z[1];
     reinterpret_cast<Dbl4 *>(D->mom)[cell] = Dbl4{al[0], al[1], al[2], al[3]};
     dz = d * Z[0];
 #pragma unroll
@@ -127,9 +129,9 @@ __global__ void __launch_bounds__(kBlock) afin1_kernel(const InstanceDesc *D) {
     if (c1 & kIncX) lam += fcur[(size_t)cell * 4 + kW] * D->ain[kW] / D->nrm[kW];
     if (c0 & kIncY) lam += fcur[(size_t)cell * 4 + kN] * D->ain[kN] / D->nrm[kN];
     if (c2 & kIncY) lam += fcur[(size_t)cell * 4 + kS] * D->ain[kS] / D->nrm[kS];
-    du = fabs(Z[1] - D->u1prev[cell]);
-    ua = fabs(Z[1]);
-    D->u1prev[cell] = Z[1];
+    du = fabs(zf - D->u1prev[cell]);
+    ua = fabs(zf);
+    D->u1prev[cell] = zf;
     if (!isfinite(Z[0]) || !isfinite(Z[1]) || !isfinite(Z[2]) || !isfinite(Z[3])) bad = 1.0;
   }
   dz = block_sum(dz, sh);
@@ -304,7 +306,7 @@ __global__ void areset_kernel(const InstanceDesc *D) {
 
 // dQ/d delta_c = sum_k z_kc (M_kc - c - h_kc), one warp per cell over the groups; M from the forward
 // moments through the collision projection, h the stored forward distribution minus its last shift.
-// Also Q_identity = F sum z v1 (equals Q at convergence), accumulated in state->Q.
+// Also Q_identity = F sum z v_flow (equals Q at convergence), accumulated in state->Q.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) agrad_kernel(const InstanceDesc *D) {
   const int lane = threadIdx.x & 31;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kBlock) agrad_kernel(const InstanceDesc *D) {
     const double h = (double)static_cast<const T *>(D->h_fwd)[((size_t)g * ncell + cell) * kLanes + lane] - s;
     const double M = a[0] + a[1] * v1 + a[2] * v2 + a[3] * vsq;
     gsum += z * (M - c - h);
-    qsum += z * v1;
+    qsum += z * (D->flow_axis ? v2 : v1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

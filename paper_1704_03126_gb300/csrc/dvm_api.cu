@@ -24,7 +24,12 @@ void set_moments_error(const std::string &msg) { g_create_error = msg; }
 
 struct dvm_ctx {
   dvm_params P{};
-  int nx = 0, ny = 0, ncell = 0, nv = 0, half = 0, gq = 0, ngroups = 0;
+  int nx = 0, ny = 0, ncell = 0, nv = 0, half = 0, gq = 0, ngroups = 0;  // stored (internal) grid
+  // tr: the caller's grid (unx x uny, x1 along rows) is stored transposed, so that the sweeps walk
+  // the longer axis; the caller's cell (i, j) is stored at (j, i) and its x1 is the stored x2
+  bool tr = false;
+  int unx = 0, uny = 0;
+  double dx = 0.0;
   bool fp64 = true, store_h = false, uniform = true;
   double delta = 0.0, kn = 0.0;
   std::vector<double> x1, w1;
@@ -88,6 +93,12 @@ dvm_status fail(dvm_ctx *ctx, dvm_status st, const std::string &msg) {
   return st;
 }
 
+// Stored cell of the caller's cell index ucell = j unx + i: (j, i) when the grid is stored transposed.
+inline size_t stored_cell(const dvm_ctx *c, size_t ucell) {
+  if (!c->tr) return ucell;
+  return (ucell % c->unx) * (size_t)c->nx + ucell / c->unx;
+}
+
 #define DVM_CUDA(ctx, call)                                                                     \
   do {                                                                                          \
     cudaError_t e_ = (call);                                                                    \
@@ -100,7 +111,7 @@ constexpr int kFinBlock = 256;
 template <typename T>
 void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T> &inv) {
   const int half = c->half, gq = c->gq;
-  const double dx = c->P.ly / c->ny;
+  const double dx = c->dx;
   vel.assign((size_t)c->ngroups * kNumVelFields * kLanes, T(0));
   inv.assign((size_t)c->ngroups * kInvRows * kLanes, T(0));  // row 9 stays 0 (solid cells)
   const double kap[3] = {1.5, 1.0, 2.0};  // interior, second cell from a wall, next to a wall
@@ -607,6 +618,7 @@ dvm_status dvm_params_init(dvm_params *p) {
   p->store_distribution = 0;
   p->sweep_warps = 0;
   p->top_wall_u1 = 0.0;
+  p->storage = DVM_STORAGE_AUTO;
   return DVM_OK;
 }
 
@@ -649,13 +661,21 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
     return fail(nullptr, DVM_EINVAL, "set exactly one of kn (> 0) and delta (>= 0)");
   }
   if (P.sweep_warps < 0 || P.sweep_warps > kMaxWarps) return fail(nullptr, DVM_EINVAL, "sweep_warps must be 0..32");
+  if (P.storage != DVM_STORAGE_AUTO && P.storage != DVM_STORAGE_AS_GIVEN && P.storage != DVM_STORAGE_TRANSPOSED)
+    return fail(nullptr, DVM_EINVAL, "storage must be DVM_STORAGE_AUTO, _AS_GIVEN or _TRANSPOSED");
 
   dvm_ctx *c = new (std::nothrow) dvm_ctx();
   if (!c) return fail(nullptr, DVM_ENOMEM, "host allocation failed");
   c->P = P;
-  c->nx = P.nx;
-  c->ny = P.ny;
+  // the sweeps run along the stored x2 (column sweep: one thread per stored column; row sweep: rows in
+  // flight across the stored x1), so a grid wider than tall is stored transposed by default
+  c->tr = P.storage == DVM_STORAGE_TRANSPOSED || (P.storage == DVM_STORAGE_AUTO && P.nx > P.ny);
+  c->unx = P.nx;
+  c->uny = P.ny;
+  c->nx = c->tr ? P.ny : P.nx;
+  c->ny = c->tr ? P.nx : P.ny;
   c->ncell = P.nx * P.ny;
+  c->dx = P.ly / P.ny;
   c->fp64 = P.precision == DVM_FP64;
   c->store_h = P.store_distribution != 0;
   c->alpha = P.accommodation;
@@ -671,7 +691,15 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   c->half = c->nv / 2;
   c->gq = (c->half * c->half + kLanes - 1) / kLanes;
   c->ngroups = 4 * c->gq;
-  build_geometry(mask, c->nx, c->ny, P.periodic_x != 0, P.periodic_y != 0, c->geo);
+  const bool spx = (c->tr ? P.periodic_y : P.periodic_x) != 0, spy = (c->tr ? P.periodic_x : P.periodic_y) != 0;
+  if (c->tr) {
+    std::vector<uint8_t> tmask((size_t)c->ncell);
+    for (int j = 0; j < c->uny; ++j)
+      for (int i = 0; i < c->unx; ++i) tmask[(size_t)i * c->nx + j] = mask[(size_t)j * c->unx + i];
+    build_geometry(tmask.data(), c->nx, c->ny, spx, spy, true, c->geo);
+  } else {
+    build_geometry(mask, c->nx, c->ny, spx, spy, false, c->geo);
+  }
   if (c->geo.n_gas == 0) {
     delete c;
     return fail(nullptr, DVM_EINVAL, "the mask has no gas cell");
@@ -806,14 +834,15 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   D.nx = c->nx;
   D.ny = c->ny;
   D.ncell = c->ncell;
-  D.periodic_x = P.periodic_x != 0;
-  D.periodic_y = P.periodic_y != 0;
+  D.periodic_x = spx;
+  D.periodic_y = spy;
   D.ngroups = c->ngroups;
   D.groups_per_quadrant = c->gq;
   D.n_gas = c->geo.n_gas;
   D.fin_nblocks = fin_nblocks;
-  D.dx = P.ly / c->ny;
-  D.dA_over_Lx = D.dx * D.dx / (c->nx * D.dx);
+  D.dx = c->dx;
+  D.flow_axis = c->tr ? 1 : 0;
+  D.dA_over_Lx = D.dx / c->unx;  // dx^2 / Lx with the caller's Lx = unx dx
   D.delta = delta;
   D.force = P.force;
   D.alpha = c->alpha;
@@ -853,11 +882,12 @@ dvm_status dvm_set_delta_field(dvm_ctx *ctx, const double *delta_c) {
   if (!ctx) return DVM_EINVAL;
   if (delta_c) {
     std::vector<double> d((size_t)ctx->ncell, 0.0);
-    for (int cell = 0; cell < ctx->ncell; ++cell) {
-      if (ctx->geo.code4[(size_t)cell * 4] & kSolid) continue;
-      if (!(delta_c[cell] >= 0.0) || !std::isfinite(delta_c[cell]))
+    for (int ucell = 0; ucell < ctx->ncell; ++ucell) {
+      const size_t cell = stored_cell(ctx, ucell);
+      if (ctx->geo.code4[cell * 4] & kSolid) continue;
+      if (!(delta_c[ucell] >= 0.0) || !std::isfinite(delta_c[ucell]))
         return fail(ctx, DVM_EINVAL, "delta field entries must be finite and >= 0 in gas cells");
-      d[cell] = delta_c[cell];
+      d[cell] = delta_c[ucell];
     }
     DVM_CUDA(ctx, cudaMemcpyAsync(ctx->d_delta_field, d.data(), sizeof(double) * ctx->ncell, cudaMemcpyHostToDevice,
                                   ctx->stream));
@@ -905,6 +935,7 @@ dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info) {
   info->mass_shift = c->h_state->c;
   info->Q = c->h_state->Q;
   info->status = c->h_state->status;
+  info->transposed = c->tr ? 1 : 0;
   return DVM_OK;
 }
 
@@ -925,11 +956,13 @@ dvm_status dvm_fields(const dvm_ctx *ctx, double *rho, double *u1, double *u2, d
   std::vector<double> mom((size_t)4 * c->ncell);
   DVM_CUDA(c, cudaMemcpyAsync(mom.data(), c->d_mom, sizeof(double) * 4 * c->ncell, cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
-  double *outs[4] = {rho, u1, u2, tau};
-  for (int cell = 0; cell < c->ncell; ++cell) {
-    const bool solid = (c->geo.code4[(size_t)cell * 4] & kSolid) != 0;
+  // stored moments (rho, u1, u2, tau) of the stored axes; a transposed grid swaps u1 and u2
+  double *outs[4] = {rho, c->tr ? u2 : u1, c->tr ? u1 : u2, tau};
+  for (int ucell = 0; ucell < c->ncell; ++ucell) {
+    const size_t cell = stored_cell(c, ucell);
+    const bool solid = (c->geo.code4[cell * 4] & kSolid) != 0;
     for (int m = 0; m < 4; ++m)
-      if (outs[m]) outs[m][cell] = solid ? NAN : mom[(size_t)cell * 4 + m];
+      if (outs[m]) outs[m][ucell] = solid ? NAN : mom[cell * 4 + m];
   }
   return DVM_OK;
 }
@@ -947,7 +980,8 @@ dvm_status dvm_distribution(const dvm_ctx *ctx, const int *ks, int nk, double *o
   for (int m = 0; m < nk; ++m) {
     const int k = ks[m];
     if (k < 0 || k >= c->nv * c->nv) return fail(c, DVM_EINVAL, "velocity index out of range");
-    const int a = k / c->nv, b = k % c->nv;
+    // (a, b): indices of the stored v1 and v2 (the caller's v2 and v1 when the grid is transposed)
+    const int a = c->tr ? k % c->nv : k / c->nv, b = c->tr ? k / c->nv : k % c->nv;
     const int s1neg = a < c->half, s2neg = b < c->half;
     const int ap = s1neg ? c->half - 1 - a : a - c->half;
     const int bp = s2neg ? c->half - 1 - b : b - c->half;
@@ -957,16 +991,17 @@ dvm_status dvm_distribution(const dvm_ctx *ctx, const int *ks, int nk, double *o
     const char *src = static_cast<const char *>(c->d_h) + ((size_t)g * c->ncell * kLanes + lane) * ts;
     DVM_CUDA(c, cudaMemcpy2DAsync(buf.data(), ts, src, ts * kLanes, ts, c->ncell, cudaMemcpyDeviceToHost, c->stream));
     DVM_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int cell = 0; cell < c->ncell; ++cell) {
+    for (int ucell = 0; ucell < c->ncell; ++ucell) {
+      const size_t cell = stored_cell(c, ucell);
       double v;
-      if (c->fp64) std::memcpy(&v, &buf[(size_t)cell * 8], 8);
+      if (c->fp64) std::memcpy(&v, &buf[cell * 8], 8);
       else {
         float f;
-        std::memcpy(&f, &buf[(size_t)cell * 4], 4);
+        std::memcpy(&f, &buf[cell * 4], 4);
         v = f;
       }
-      v = (c->geo.code4[(size_t)cell * 4] & kSolid) ? 0.0 : v - shift;
-      out[(size_t)m * c->ncell + cell] = v;
+      v = (c->geo.code4[cell * 4] & kSolid) ? 0.0 : v - shift;
+      out[(size_t)m * c->ncell + ucell] = v;
     }
   }
   return DVM_OK;
@@ -1116,8 +1151,10 @@ dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta
   DVM_CUDA(c, cudaMemcpyAsync(g.data(), c->a_grad, sizeof(double) * c->ncell, cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->a_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
-  for (int cell = 0; cell < c->ncell; ++cell)
-    dQ_ddelta[cell] = (c->geo.code4[(size_t)cell * 4] & kSolid) ? 0.0 : g[cell];
+  for (int ucell = 0; ucell < c->ncell; ++ucell) {
+    const size_t cell = stored_cell(c, ucell);
+    dQ_ddelta[ucell] = (c->geo.code4[cell * 4] & kSolid) ? 0.0 : g[cell];
+  }
   if (q_identity) *q_identity = c->h_state->Q;
   if (iters) *iters = n;
   return status;

@@ -32,7 +32,8 @@ enum : uint32_t {
   kAdjT2X = 1u << 14, // t2 = -1/2 along x
   kAdjT1YShift = 15,  // 2 bits: t1 along y
   kAdjT2Y = 1u << 17,
-  kTopWall = 1u << 18,  // the upstream y wall of this quadrant is the plate beyond the last row
+  kTopWall = 1u << 18,   // the upstream y wall of this quadrant is the moving plate beyond the last row
+  kTopWallX = 1u << 19,  // the upstream x wall is the moving plate beyond the last column (transposed)
 };
 enum : int { kFull = 0, kNear = 1, kWall = 2 };
 // sides of a cell: the solid neighbour lies at -x (W), +x (E), -y (S), +y (N)
@@ -119,12 +120,14 @@ struct InstanceDesc {
   int uniform_delta;
   int fin_nblocks;      // blocks of this instance in the finalize grids
   int fp32;             // 1 = FP32 storage (enables the noise-floor exit of the stopping test)
+  int flow_axis;        // 0: the force, the moving plate's drift, Q and the stopping test are along x1;
+                        // 1: along x2 (the caller's grid stored transposed: its x1 is this grid's x2)
   double dx;            // cell size
-  double dA_over_Lx;    // dx^2 / (nx dx)
+  double dA_over_Lx;    // dx^2 / (length of the grid along the flow axis)
   double delta;         // uniform collision rate
   double force;         // F
   double alpha;         // accommodation: wall value alpha rho_w + (1 - alpha) h(mirror v), Eq. (diffuse2)
-  double top_u;         // speed along x1 of the plate beyond the last row (Couette flow), or 0
+  double top_u;         // speed of the moving plate (Couette flow), or 0
   int nwall;            // wall faces (gas cell, side) with a solid or outside neighbour across the side
   const int *wall_slot; // [ncell][4] -> face slot or -1 (alpha < 1 only)
   void *wbuf;           // [2 parities][nwall][2][groups_per_quadrant][32] T: incident h at each wall face
@@ -144,7 +147,7 @@ struct InstanceDesc {
   double *acc;          // [ncell][4]   moment accumulators of the running sweep
   double *facc;         // [2][ncell][4] incident wall-flux accumulators (by iteration parity)
   double *mom;          // [ncell][4]   rho, u1, u2, tau of the current state
-  double *u1prev;       // [ncell]
+  double *u1prev;       // [ncell] velocity along the flow axis after the previous sweep
   void *seam_x;         // [ngroups][ny][2][32] T: last two columns of the previous sweep
   void *seam_y;         // [ngroups][nx][2][32] T: last two rows of the previous sweep
   void *h;              // [ngroups][ncell][32] T, or nullptr

@@ -140,10 +140,10 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         a[i] = D->ginv[i * 4] * m[0] + D->ginv[i * 4 + 1] * m[1] + D->ginv[i * 4 + 2] * m[2] + D->ginv[i * 4 + 3] * m[3];
-      // R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v1 in the basis 1, v1, v2, |v|^2 - 1
+      // R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v_flow in the basis 1, v1, v2, |v|^2 - 1
       const double A = d * (a[0] + a[3] - c_new);
-      const double B = d * a[1] + D->force;
-      const double Cc = d * a[2];
+      const double B = d * a[1] + (D->flow_axis ? 0.0 : D->force);
+      const double Cc = d * a[2] + (D->flow_axis ? D->force : 0.0);
       const double Dd = d * a[3];
       SweepRec<T> *rec = static_cast<SweepRec<T> *>(D->rec);
 #pragma unroll
@@ -166,10 +166,11 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
                            diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
                        A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
       }
-      du = fabs(u1 - D->u1prev[cell]);
-      ua = fabs(u1);
-      uq = u1;
-      D->u1prev[cell] = u1;
+      const double uf = D->flow_axis ? u2 : u1;  // velocity along the flow
+      du = fabs(uf - D->u1prev[cell]);
+      ua = fabs(uf);
+      uq = uf;
+      D->u1prev[cell] = uf;
       if (!isfinite(rho) || !isfinite(u1) || !isfinite(u2) || !isfinite(tau)) bad = 1.0;
     }
     reinterpret_cast<Dbl4 *>(fnext)[cell] = Dbl4{0.0, 0.0, 0.0, 0.0};
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
   }
 }
 
-// h = 0: records with B = F (force) and everything else zero; state cleared.
+// h = 0: records with B = F (C = F when the flow is along x2) and everything else zero; state cleared.
 template <typename T>
 __global__ void reset_kernel(const InstanceDesc *D) {
   const int ncell = D->ncell;
@@ -252,13 +253,14 @@ __global__ void reset_kernel(const InstanceDesc *D) {
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncell; cell += gridDim.x * blockDim.x) {
     const uint32_t code0 = D->code4[(size_t)cell * 4];
     const double d = (code0 & kSolid) ? 0.0 : (D->uniform_delta ? D->delta : D->delta_field[cell]);
-    const double B = (code0 & kSolid) ? 0.0 : D->force;
+    const double F = (code0 & kSolid) ? 0.0 : D->force;
+    const double B = D->flow_axis ? 0.0 : F, C = D->flow_axis ? F : 0.0;
     for (int q = 0; q < 4; ++q) {
-      store_rec<T>(rec + (size_t)q * ncell + cell, 0.0, B, 0.0, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+      store_rec<T>(rec + (size_t)q * ncell + cell, 0.0, B, C, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
       if (D->rec_diag)
         store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
                          diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
-                     0.0, B, 0.0, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
+                     0.0, B, C, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], d);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -408,11 +408,15 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
             }
           }
         }
-        T mw = T(0);
+        // moving plate (set only on gas cells whose upstream wall along that axis is the plate): the
+        // reflected drift 2 U v_t along the plate, v_t = v1 for a plate beyond the last row, v2 for
+        // one beyond the last column (an instance stored transposed)
+        T mwy = T(0), mwx = T(0);
         if constexpr (SPEC && !ADJ) {
-          if ((code & kTopWall) && !(code & kSolid) && ((code >> kClsYShift) & 3u) == (uint32_t)kWall) mw = top_term;
+          if (code & kTopWall) mwy = top_term;
+          if (code & kTopWallX) mwx = top_term;
         }
-        const T2 smw = Q::splat(mw);
+        const T2 smwy = Q::splat(mwy), smwx = Q::splat(mwx);
         const T2 sA = Q::splat(r.A), sB = Q::splat(r.B), sC = Q::splat(r.C), sD = Q::splat(r.D);
         const T2 sax1 = Q::splat(ax1), sax2 = Q::splat(ax2), say1 = Q::splat(ay1), say2 = Q::splat(ay2);
         const T2 sxw = Q::splat(xw), syw = Q::splat(yw);
@@ -432,8 +436,8 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           const T2 cv1 = c[kCV1], cv2 = c[kCV2], ce = c[kCE], ccx = c[kCCx], ccy = c[kCCy], cwm = c[kCWm];
           T2 Rk = Q::fma2(sD, ce, Q::fma2(sC, cv2, Q::fma2(sB, cv1, sA)));
           if (ADJ) Rk = Q::mul2(c[kCWr], Q::fma2(ccx, stx, Q::fma2(ccy, sty, Rk)));
-          const T2 by = Q::fma2(say1, hy1[k], Q::fma2(say2, hy2[k], (SPEC && !ADJ) ? Q::fma2(smw, cv1, syw) : syw));
-          const T2 bx = Q::fma2(sax1, u1[k], Q::fma2(sax2, u2[k], sxw));
+          const T2 by = Q::fma2(say1, hy1[k], Q::fma2(say2, hy2[k], (SPEC && !ADJ) ? Q::fma2(smwy, cv1, syw) : syw));
+          const T2 bx = Q::fma2(sax1, u1[k], Q::fma2(sax2, u2[k], (SPEC && !ADJ) ? Q::fma2(smwx, cv2, sxw) : sxw));
           T2 iv;
           if (UNIF) iv = *reinterpret_cast<const T2 *>(invt + irow * VB + v * G + 2 * k);
           else iv = Q::rcp2(Q::fma2(ccx, skx, Q::fma2(ccy, sky, sdl)));

@@ -115,7 +115,7 @@ bool quadrature_1d(int kind, int n, double vmax, std::vector<double> &x, std::ve
   return false;
 }
 
-void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geometry &G) {
+void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, bool plate_x, Geometry &G) {
   const int ncell = nx * ny;
   G.code4.assign((size_t)ncell * 4, 0u);
   G.hw_src.assign((size_t)ncell * 8, -1);
@@ -154,6 +154,7 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
             cls = kNear;  // first order through the gas neighbour: no wall value
           }
           code |= (uint32_t)cls << kClsXShift;
+          if (plate_x && !px && i == nx - 1 && sx < 0) code |= kTopWallX;
           G.hw_src[(size_t)cell * 8 + q * 2 + 0] = src;
           if (solid(i + sx, j)) code |= kIncX;
         }
@@ -167,7 +168,7 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geome
             cls = kNear;
           }
           code |= (uint32_t)cls << kClsYShift;
-          if (!py && j == ny - 1 && sy < 0) code |= kTopWall;
+          if (!plate_x && !py && j == ny - 1 && sy < 0) code |= kTopWall;
           G.hw_src[(size_t)cell * 8 + q * 2 + 1] = src;
           if (solid(i, j + sy)) code |= kIncY;
         }

@@ -19,6 +19,7 @@ struct Geometry {
   std::vector<int> hw_src;      // [ncell][8]
   int n_gas = 0;
 };
-void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, Geometry &G);
+// plate_x: the moving plate (if any) lies beyond the last column instead of beyond the last row
+void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, bool plate_x, Geometry &G);
 
 }  // namespace dvm

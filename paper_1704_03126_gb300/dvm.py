@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdvm.so")
 
 DVM_OK, DVM_EINVAL, DVM_ENOMEM, DVM_ECUDA, DVM_ENOCONV, DVM_ETIMEOUT, DVM_ENUMERIC, DVM_ESTATE = range(8)
 QUAD_KINDS = {"gh": 0, "nc": 1, "cubic": 2}
+STORAGE = {"auto": 0, "as_given": 1, "transposed": 2}
 FP64, FP32_ACC64 = 0, 1
 
 
@@ -40,13 +41,14 @@ class Params(ctypes.Structure):
         ("ly", ctypes.c_double), ("kn", ctypes.c_double), ("delta", ctypes.c_double),
         ("quad", Quad), ("accommodation", ctypes.c_double), ("precision", ctypes.c_int),
         ("force", ctypes.c_double), ("store_distribution", ctypes.c_int), ("sweep_warps", ctypes.c_int),
-        ("top_wall_u1", ctypes.c_double),
+        ("top_wall_u1", ctypes.c_double), ("storage", ctypes.c_int),
     ]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("eps", ctypes.c_double), ("est", ctypes.c_double),
-                ("mass_shift", ctypes.c_double), ("Q", ctypes.c_double), ("status", ctypes.c_int)]
+                ("mass_shift", ctypes.c_double), ("Q", ctypes.c_double), ("status", ctypes.c_int),
+                ("transposed", ctypes.c_int)]
 
 
 _lib = None
@@ -120,12 +122,14 @@ class Solver:
     torch.cuda.current_stream().cuda_stream) or None.  schedule: None (automatic), or (kind,
     shape) for set_schedule.  accommodation: alpha in [0, 1] of Eq. (diffuse2); below 1 the
     walls reflect the rest specularly (column sweep only; no adjoint).  top_wall_u1: speed of the plate
-    beyond the last row (Couette flow; column sweep only; no adjoint).
+    beyond the last row (Couette flow; column sweep only; no adjoint).  storage: "auto" (the library
+    stores a grid wider than tall transposed, so that its sweeps walk the long axis), "as_given" or
+    "transposed"; arguments and results keep the [ny][nx] layout either way.
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
                  precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
-                 schedule=None, accommodation=1.0, top_wall_u1=0.0):
+                 schedule=None, accommodation=1.0, top_wall_u1=0.0, storage="auto"):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -146,6 +150,9 @@ class Solver:
         p.force = float(force)
         p.accommodation = float(accommodation)
         p.top_wall_u1 = float(top_wall_u1)
+        if storage not in STORAGE:
+            raise ValueError(f"storage must be one of {sorted(STORAGE)}")
+        p.storage = STORAGE[storage]
         p.store_distribution = int(bool(store_distribution))
         p.sweep_warps = int(sweep_warps)
         self.params = p
@@ -212,7 +219,7 @@ class Solver:
         inf = Info()
         self._check(lib().dvm_get_info(self._ctx, ctypes.byref(inf)))
         return dict(iterations=inf.iterations, eps=inf.eps, est=inf.est, mass_shift=inf.mass_shift, Q=inf.Q,
-                    status=inf.status)
+                    status=inf.status, transposed=bool(inf.transposed))
 
     def adjoint(self, tol=1e-10, max_iter=100000):
         """dQ/d delta_c at the current forward state: (grad [ny][nx], F sum z v1, adjoint sweeps)."""

@@ -127,3 +127,23 @@ def test_autograd_flow_rate_backward():
     qp = flow_rate(torch.tensor(d0 + eps * dirn, device="cuda"), sol, tol=1e-14).item()
     qm = flow_rate(torch.tensor(d0 - eps * dirn, device="cuda"), sol, tol=1e-14).item()
     assert abs((qp - qm) / (2 * eps) - float((g_auto * dirn).sum())) < 1e-6 * np.abs(g_auto).sum()
+
+
+@pytest.mark.parametrize("storage", ["as_given", "transposed"])
+@pytest.mark.parametrize("schedule", SCHEDULES[:2], ids=["rows", "cols1"])
+@pytest.mark.parametrize("name", ["rough24_nc8", "block_periodic_cubic10"])
+def test_adjoint_gradient_in_either_storage_order(name, schedule, storage):
+    """The transposed grid takes the adjoint source g = W v_flow dA / L along its x2; the gradient comes
+    back in the caller's layout."""
+    _, mask, px, py, delta, quad = next(c for c in CASES if c[0] == name)
+    d = _delta_field(mask, delta, 3)
+    sol = dvm.Solver(mask, px, py, delta=delta, quad=quad, precision="fp64", store_distribution=True,
+                     schedule=schedule, storage=storage)
+    assert sol.info()["transposed"] == (storage == "transposed")
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=200000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=200000)
+    g_ref, q_ref_id, _, ok = _oracle_gradient(name)
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale
+    assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)

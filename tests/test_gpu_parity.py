@@ -165,14 +165,17 @@ def test_delta_field_matches_oracle(schedule, precision):
     assert np.isnan(ka)
 
 
+@pytest.mark.parametrize("storage", ["as_given", "transposed"])
 @pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
-def test_one_sweep_matches_oracle_velocity_by_velocity(schedule):
+def test_one_sweep_matches_oracle_velocity_by_velocity(schedule, storage):
     """From the GPU's stored state h^n, the oracle sweeps selected velocities once; the GPU's h^{n+1}
-    must agree (after the same mass shift)."""
+    must agree (after the same mass shift).  Transposed storage swaps the stored cells and the roles of
+    v1 and v2; the distribution comes back in the caller's layout and velocity numbering."""
     mask = inputs.rough_channel_mask(24)
     quad = ("nc", 8, 4.0)
     sol = dvm.Solver(mask, True, False, kn=0.5, quad=quad, precision="fp64", store_distribution=True,
-                     schedule=schedule)
+                     schedule=schedule, storage=storage)
+    assert sol.info()["transposed"] == (storage == "transposed")
     sol.iterate(3)
     K = quad[1] ** 2
     h_n = sol.distribution(np.arange(K))
@@ -248,8 +251,10 @@ def test_autotune_picks_a_fitting_kernel_and_keeps_the_state():
 
 
 def test_wide_grid_runs_on_the_column_sweep_only():
-    mask = inputs.rough_channel_mask(384)[:64].copy()  # 384 columns: beyond the row sweep's 256
-    sol = dvm.Solver(mask, True, False, kn=1.0, quad=("cubic", 8, 4.0), precision="fp32")
+    """Stored as given, 384 columns exceed the row sweep's 256 and allow one thread per column only."""
+    mask = inputs.rough_channel_mask(384)[:64].copy()
+    sol = dvm.Solver(mask, True, False, kn=1.0, quad=("cubic", 8, 4.0), precision="fp32", storage="as_given")
+    assert not sol.info()["transposed"]
     assert sol.schedule() == ("columns", 1)
     with pytest.raises(dvm.DvmError):
         sol.set_schedule("rows")
@@ -259,6 +264,13 @@ def test_wide_grid_runs_on_the_column_sweep_only():
         sol.set_schedule("columns", 2)
     sol.iterate(5)
     assert np.isfinite(sol.flowrate()[0])
+    # the automatic storage holds it transposed (64 stored columns): every kernel fits
+    auto = dvm.Solver(mask, True, False, kn=1.0, quad=("cubic", 8, 4.0), precision="fp32")
+    assert auto.info()["transposed"]
+    assert auto.schedule() == ("columns", 4)
+    auto.set_schedule("rows")
+    auto.iterate(5)
+    assert abs(auto.flowrate()[0] - sol.flowrate()[0]) < 1e-5 * abs(sol.flowrate()[0])
 
 
 # ------------------------------------------------------------------ full-size workloads
@@ -299,7 +311,7 @@ def test_one_sweep_on_a_256_column_periodic_grid(schedule, precision):
     mask = _wide_porous_slice()
     quad = ("cubic", 8, 4.0)
     sol = dvm.Solver(mask, True, True, kn=0.5, quad=quad, precision=precision, store_distribution=True,
-                     schedule=schedule)
+                     schedule=schedule, storage="as_given")
     sol.iterate(3)
     K = quad[1] ** 2
     h_n = sol.distribution(np.arange(K))
@@ -320,7 +332,8 @@ def test_one_sweep_on_a_256_column_periodic_grid(schedule, precision):
 def test_256_column_periodic_grid_fixed_point(schedule):
     mask = _wide_porous_slice()
     quad = ("cubic", 8, 4.0)
-    sol, orc, iters = _solve_both(mask, True, True, 0.5, quad, "fp64", 1e-11, orc_tol=1e-11, schedule=schedule)
+    sol, orc, iters = _solve_both(mask, True, True, 0.5, quad, "fp64", 1e-11, orc_tol=1e-11, schedule=schedule,
+                                  storage="as_given")
     _compare(sol, orc, mask, "fp64")
 
 
@@ -403,14 +416,18 @@ def test_partially_specular_walls_fp32_and_restrictions():
 
 # ------------------------------------------------------------------ Couette flow (Sec. II, Eq. diffuse1)
 
+@pytest.mark.parametrize("storage", ["auto", "as_given"])
 @pytest.mark.parametrize("alpha", [1.0, 0.7])
 @pytest.mark.parametrize("schedule", SCHEDULES[1:], ids=SCHED_IDS[1:])
-def test_couette_over_wm_wall_matches_oracle(schedule, alpha):
-    """Smooth top plate moving with U = 1 over a Weierstrass-Mandelbrot staircase bottom, no force."""
+def test_couette_over_wm_wall_matches_oracle(schedule, alpha, storage):
+    """Smooth top plate moving with U = 1 over a Weierstrass-Mandelbrot staircase bottom, no force.
+    The channel is 5 times wider than tall: the automatic storage holds it transposed, with the plate
+    beyond the last stored column, drifting along the stored x2."""
     mask, ly = inputs.couette_rough_mask(12, aspect=5.0, eps=0.05)
     quad = ("cubic", 8, 4.0)
     sol = dvm.Solver(mask, True, False, kn=0.5, quad=quad, precision="fp64", ly=ly, force=0.0,
-                     top_wall_u1=1.0, accommodation=alpha, schedule=schedule)
+                     top_wall_u1=1.0, accommodation=alpha, schedule=schedule, storage=storage)
+    assert sol.info()["transposed"] == (storage == "auto")
     sol.solve(tol=1e-12, max_iter=200000)
     p = oracle.Problem.make(mask, True, False, dvm.kn_to_delta(0.5), quad, alpha=alpha, force=0.0, ly=ly,
                             top_u=1.0)
@@ -440,3 +457,71 @@ def test_moving_plate_restrictions():
     with pytest.raises(dvm.DvmError) as ei:
         sol.adjoint()
     assert ei.value.status == dvm.DVM_EINVAL
+
+
+# ------------------------------------------------------------------ storage order (dvm_storage)
+
+STORAGE_CASES = [c for c in CASES if c[0] in ("rough32_nc8_kn1", "ragged37x29_block_gh8", "narrow3x40_nonperiodic_y",
+                                               "closed_box_16", "periodic_y_only")]
+
+
+@pytest.mark.parametrize("storage", ["as_given", "transposed"])
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
+@pytest.mark.parametrize("case", STORAGE_CASES, ids=[c[0] for c in STORAGE_CASES])
+def test_storage_orders_match_oracle(case, schedule, storage):
+    """Either storage order reaches the oracle's fixed point: the transposed grid carries the force,
+    the flow rate and the stopping test along its x2 and returns every field in the caller's layout."""
+    name, mask, px, py, kn, quad, warps = case
+    sol, orc, iters = _solve_both(mask, px, py, kn, quad, "fp64", 1e-12, schedule=schedule, storage=storage)
+    assert sol.info()["transposed"] == (storage == "transposed")
+    _compare(sol, orc, mask, "fp64")
+
+
+def test_automatic_storage_transposes_wide_grids_only():
+    for shape, tr in (((8, 20), True), ((20, 8), False), ((12, 12), False)):
+        sol = dvm.Solver(np.zeros(shape, np.uint8), True, False, kn=1.0, quad=("gh", 4, 0.0))
+        assert sol.info()["transposed"] == tr, shape
+    with pytest.raises(ValueError):
+        dvm.Solver(np.zeros((4, 4), np.uint8), True, False, kn=1.0, quad=("gh", 4, 0.0), storage="diagonal")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_delta_field_in_transposed_storage(precision):
+    mask = _block_mask(24, 14)
+    rng = np.random.default_rng(9)
+    d = rng.uniform(0.3, 3.0, size=mask.shape)
+    quad = ("cubic", 10, 4.0)
+    sol = dvm.Solver(mask, True, False, delta=1.0, quad=quad, precision=precision)
+    assert sol.info()["transposed"]
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-12 if precision == "fp64" else 1e-6, max_iter=100000)
+    orc = oracle.solve(_oracle_problem(mask, True, False, d, quad), tol=1e-12, max_iter=100000)
+    _compare(sol, orc, mask, precision)
+
+
+def test_paper_size_couette_channels():
+    """The Couette channels of Sec. II at the paper's resolution along x1: 1500 columns, aspect 5
+    (dx = H / 300), cubic 32 x 32 velocities, Kn = 1, FP32, stored transposed (beyond the column
+    sweep's 512 as given).  No oracle run at this size; instead what holds exactly for the discrete
+    equations: smooth plates give Q = U H m0 m2, and the mirror image of the plane problem (plate
+    and wall exchanged) adds to the uniform drift 2 U v1, so u1(x2) + u1(H - x2) = 2 U m0 m2.  The
+    rough wall slows the flow: 0.9 < Q_r / Q_s < 1."""
+    quad = ("cubic", 32, 4.0)
+    x, w = oracle.quadrature("cubic", 32, 4.0)
+    m0m2 = float(w.sum() * (w * x * x).sum())
+    smooth = dvm.Solver(inputs.plates_mask(1500, 300), True, False, kn=1.0, quad=quad, precision="fp32", force=0.0,
+                        top_wall_u1=1.0)
+    assert smooth.info()["transposed"]
+    st, iters, est = smooth.solve(tol=1e-6, max_iter=20000)
+    q_s = smooth.flowrate()[0]
+    assert abs(q_s - m0m2) < 2e-5, (q_s, m0m2)
+    u1 = smooth.fields()["u1"]
+    assert np.abs(u1 + u1[::-1, :] - 2.0 * m0m2).max() < 1e-4
+    assert np.abs(u1 - u1[:, :1]).max() < 1e-5  # x1-invariant
+    mask, ly = inputs.couette_rough_mask(300, aspect=5.0, eps=0.02)
+    assert mask.shape[1] == 1500
+    rough = dvm.Solver(mask, True, False, kn=1.0, quad=quad, precision="fp32", ly=ly, force=0.0, top_wall_u1=1.0)
+    assert rough.info()["transposed"]
+    rough.solve(tol=1e-6, max_iter=20000)
+    q_star = rough.flowrate()[0] / q_s
+    assert 0.9 < q_star < 1.0, q_star

@@ -91,6 +91,20 @@ def test_both_kn_and_delta_rejected_by_the_library():
     assert b"exactly one" in L.dvm_last_error(None)
 
 
+def test_storage_order_is_validated_by_the_library():
+    import ctypes
+    L = dvm.lib()
+    p = dvm.Params()
+    L.dvm_params_init(p)
+    assert p.storage == dvm.STORAGE["auto"]
+    p.nx, p.ny, p.storage = 4, 4, 3
+    mask = np.zeros((4, 4), np.uint8)
+    ctx = ctypes.c_void_p()
+    st = L.dvm_create(mask.ctypes.data_as(ctypes.c_void_p), ctypes.byref(p), None, ctypes.byref(ctx))
+    assert st == dvm.DVM_EINVAL
+    assert b"storage" in L.dvm_last_error(None)
+
+
 def test_status_strings():
     L = dvm.lib()
     assert L.dvm_status_string(0) == b"DVM_OK"
