@@ -19,6 +19,11 @@ Other workloads, one JSON line each:
            dx = H / 100), bottom wall a Weierstrass-Mandelbrot staircase (D = 1.5, eps = 2 %) or smooth,
            cubic 32 x 32 velocities, Kn = 0.1, 1, 10: six instances advanced together; reports
            Q* = Q_rough / Q_smooth per Kn from the converged solves.
+  permeability  Sec. III's curves: three synthetic media 256 x 256 (irregular, square and circular
+           solids, porosity about 0.6, both axes periodic), cubic 32 x 32 velocities, Kn = 0.02 ... 2:
+           21 instances advanced together.  Extras: k_inf extrapolated from Kn = 0.005, 0.01, 0.02
+           solved on the media refined twice (512 x 512, Gauss-Hermite 12 x 12), then H* and
+           k_a / k_inf against Kn* per medium.
 
 The sweep kernel of every launch is chosen by the library's autotuner before the timed region.
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
@@ -42,6 +47,10 @@ import numpy as np  # noqa: E402
 
 KNS = (0.1, 1.0, 10.0)
 COUETTE_GAP = 100  # cells across the mean gap H of the Couette channels (500 columns at aspect 5)
+PERM_FIT_KNS = (0.005, 0.01, 0.02)  # k_inf is extrapolated to Kn = 0 from these (refined grid)
+PERM_KNS = (0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0)
+PERM_FIT_QUAD = ("gh", 12, 0.0)
+PERM_FIT_REFINE = 2
 POROUS_KNS = (0.05, 0.5, 5.0)
 METRICS = {
     "rough": "DVM cell-velocity updates/s (rough channel 128x128, 32x32 velocities, Kn 0.1/1/10)",
@@ -50,6 +59,7 @@ METRICS = {
     "adjoint": "adjoint sweep cell-velocity updates/s (porous 256x256 phi 0.5, cubic 32x32, Kn 1, FP64)",
     "couette": "DVM cell-velocity updates/s (Couette, WM-rough and smooth 500-column channels, cubic 32x32, "
                "Kn 0.1/1/10)",
+    "permeability": "DVM cell-velocity updates/s (3 porous media 256x256 x 7 Kn in 0.02-2, cubic 32x32)",
 }
 METRIC = METRICS["rough"]
 UNIT = "updates/s"
@@ -93,6 +103,10 @@ WORKLOAD_TEXT = {
     "couette": "Couette flow, top plate U = 1, no force, x1 periodic, 500 columns (aspect 5, dx = H/100): "
                "Weierstrass-Mandelbrot staircase bottom (D 1.5, gamma 1.5, n1 -4, eps 2%, truncated at the "
                "grid Nyquist frequency) and smooth plates, cubic 32x32 velocities |v|<=4, Kn 0.1/1/10 batched",
+    "permeability": "three seeded periodic media 256x256, porosity about 0.6 (irregular: thresholded "
+                    "Gaussian-filtered noise, width 20 cells; squares: sides 32-80; disks: radii 20-48), cubic "
+                    "32x32 velocities |v|<=4, Kn 0.02/0.05/0.1/0.2/0.5/1/2, force-driven (F=1); 21 instances "
+                    "batched",
 }
 
 
@@ -118,6 +132,12 @@ def instances(workload="rough"):
             _INSTANCES[workload] = [inputs.porous_instance(kn) for kn in POROUS_KNS]
         elif workload == "batched":
             _INSTANCES[workload] = inputs.batched_instances(64)
+        elif workload == "permeability":
+            masks = {kind: inputs.medium_mask(kind, 256) for kind in inputs.MEDIA}
+            _INSTANCES[workload] = [
+                inputs.Instance(f"{kind}256_phi0.6_cubic32_kn{kn:g}", masks[kind][0], True, True, kn, ("cubic", 32, 4.0),
+                                {"porosity": masks[kind][1], "medium": kind})
+                for kind in inputs.MEDIA for kn in PERM_KNS]
         elif workload == "couette":
             _INSTANCES[workload] = [inputs.couette_instance(kn, gap_cells=COUETTE_GAP, rough=rough)
                                     for rough in (True, False) for kn in KNS]
@@ -342,9 +362,12 @@ def run_ours(args, rank, world, local_rank):
     }
 
     if not args.skip_extras:
-        big = args.workload == "batched"
+        big = args.workload in ("batched", "permeability")
         out["e2e"] = e2e(args, insts, stream, dvm, torch, sweeps=10 if big else 50, reps=1 if big else 3)
-        out["converge"] = converge(results, insts, torch, max_iter=10000 if big else 200000)
+        if args.workload == "permeability":
+            out["curves"] = curves(results, insts, torch)
+        else:
+            out["converge"] = converge(results, insts, torch, max_iter=10000 if big else 200000)
     if rank == 0 and not args.skip_extras:
         out["cpu_baseline"] = cpu_baseline(insts, args.workload)
     for r in results.values():
@@ -411,6 +434,53 @@ def converge(results, insts, torch, max_iter=200000):
             out[prec]["batched_Q"] = bq
         if any(i.extra.get("top_u", 0.0) != 0.0 for i in insts):
             out[prec]["Q_star"] = couette_q_star(insts, bq)
+    return out
+
+
+def curves(results, insts, torch, max_iter=200000):
+    """Sec. III: the timed batch (curve points) converged in one run; the fit points of every medium
+    (refined grid, Gauss-Hermite velocities) as a second batch; then per medium k_inf, H* and
+    k_a / k_inf against Kn*.  The Knudsen number solved on both grids shows their agreement."""
+    from paper_1704_03126_gb300 import inputs
+    from paper_1704_03126_gb300 import permeability as perm
+    out = {}
+    for prec, r in results.items():
+        tol = 1e-10 if prec == "fp64" else 1e-6
+        for s in r["solvers"]:
+            s.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status = r["batch"].run(tol=tol, max_iter=max_iter)
+        dt = time.perf_counter() - t0
+        fit_masks, fit_kns, owners = [], [], []
+        for kind in inputs.MEDIA:
+            m = next(i.mask for i in insts if i.extra.get("medium") == kind)
+            for kn in PERM_FIT_KNS:
+                fit_masks.append(inputs.refine_mask(m, PERM_FIT_REFINE))
+                fit_kns.append(kn)
+                owners.append(kind)
+        t0 = time.perf_counter()
+        fka, fit_iters, fit_status = perm.solve_batch(fit_masks, fit_kns, PERM_FIT_QUAD, prec, tol, max_iter)
+        dt_fit = time.perf_counter() - t0
+        media = {}
+        for kind in inputs.MEDIA:
+            idx = [i for i, inst in enumerate(insts) if inst.extra.get("medium") == kind]
+            ka = {insts[i].kn: r["solvers"][i].flowrate()[1] for i in idx}
+            iters = {insts[i].kn: r["solvers"][i].info()["iterations"] for i in idx}
+            fsel = [j for j, o in enumerate(owners) if o == kind]
+            res = perm.curve_from_values(PERM_KNS, [ka[k] for k in PERM_KNS], [fit_kns[j] for j in fsel],
+                                         [fka[j] for j in fsel], insts[idx[0]].extra["porosity"])
+            res["iterations"] = {f"{k:g}": iters[k] for k in sorted(iters)}
+            res["fit_iterations"] = {f"{fit_kns[j]:g}": fit_iters[j] for j in fsel}
+            both = sorted(set(PERM_KNS) & set(PERM_FIT_KNS))
+            res["grid_check"] = {f"{k:g}": {"coarse_cubic32": ka[k], "refined_gh12": fka[fsel[PERM_FIT_KNS.index(k)]]}
+                                 for k in both}
+            media[kind] = res
+        out[prec] = {"tol": tol, "max_iter": max_iter, "curve_batch_s": dt, "fit_batch_s": dt_fit,
+                     "instances": len(insts) + len(fit_kns),
+                     "converged": int((np.asarray(status) == 0).sum()) + sum(s == 0 for s in fit_status),
+                     "fit": f"k_inf from Kn {PERM_FIT_KNS} on the media refined {PERM_FIT_REFINE}x, {PERM_FIT_QUAD}",
+                     "media": media}
     return out
 
 

@@ -7,7 +7,7 @@ be fed from it.
 The paper's own geometries are a Weierstrass-Mandelbrot rough wall (Sec. II, Eq. WM) and three
 porous media shown only as images (Sec. III, Fig. 4).  The generators below make stand-ins with
 the same structure: a staircase wall on a Cartesian grid (Sec. II.A, "stair case") and periodic
-cells of non-overlapping disks.
+cells of irregular, square or circular solids.
 """
 from __future__ import annotations
 
@@ -105,6 +105,87 @@ def porous_disks_mask(n: int = 256, porosity: float = 0.6, rmin: int = 8, rmax: 
     return mask, float(1.0 - mask.mean())
 
 
+def porous_squares_mask(n: int = 256, porosity: float = 0.6, smin: int = 12, smax: int = 36, seed: int = 2,
+                        gap: int = 2, max_reject: int = 100000):
+    """Periodic n x n cell of non-overlapping axis-aligned square solids (the shape of medium 2 of Sec. III).
+
+    Squares with integer side U{smin..smax} and lower-left cell U{0..n-1}^2 are added in sequence (both
+    axes periodic); a square is rejected when one of its cells lies within `gap` cells (max norm) of an
+    earlier square.  Adding stops when the gas fraction reaches the target.  Returns (mask, porosity).
+    """
+    rng = SplitMix64(seed)
+    mask = np.zeros((n, n), dtype=np.uint8)
+    halo = np.zeros((n, n), dtype=bool)  # earlier squares dilated by gap
+    rejects = 0
+    while (1.0 - mask.mean()) > porosity:
+        side = rng.randint(smin, smax)
+        x0 = rng.randint(0, n - 1)
+        y0 = rng.randint(0, n - 1)
+        xs = (x0 + np.arange(side)) % n
+        ys = (y0 + np.arange(side)) % n
+        if halo[np.ix_(ys, xs)].any():
+            rejects += 1
+            if rejects > max_reject:
+                raise ValueError("porous_squares_mask: cannot reach the target porosity")
+            continue
+        rejects = 0
+        mask[np.ix_(ys, xs)] = 1
+        hx = (x0 - gap + np.arange(side + 2 * gap)) % n
+        hy = (y0 - gap + np.arange(side + 2 * gap)) % n
+        halo[np.ix_(hy, hx)] = True
+    return mask, float(1.0 - mask.mean())
+
+
+def porous_irregular_mask(n: int = 256, porosity: float = 0.6, corr: float = 10.0, seed: int = 3):
+    """Periodic n x n cell of irregular solids (the kind of medium 1 of Sec. III): a Gaussian-filtered
+    field of SplitMix64 uniforms (periodic, filter width `corr` cells) thresholded so that the gas
+    fraction is the target; gas cells are the field's lowest values.  Raises ValueError when the gas
+    does not connect across the cell along x1.  Returns (mask, porosity)."""
+    rng = SplitMix64(seed)
+    noise = np.array([rng.uniform() for _ in range(n * n)]).reshape(n, n) - 0.5
+    k = np.fft.fftfreq(n)
+    kern = np.exp(-2.0 * (math.pi * corr) ** 2 * (k[:, None] ** 2 + k[None, :] ** 2))
+    field = np.real(np.fft.ifft2(np.fft.fft2(noise) * kern))
+    order = np.argsort(field, axis=None, kind="stable")
+    mask = np.ones(n * n, dtype=np.uint8)
+    mask[order[: int(round(porosity * n * n))]] = 0
+    mask = mask.reshape(n, n)
+    if not percolates_x(mask):
+        raise ValueError("porous_irregular_mask: the gas does not connect along x1; try another seed")
+    return mask, float(1.0 - mask.mean())
+
+
+def percolates_x(mask: np.ndarray, periodic_y: bool = True) -> bool:
+    """Whether the gas of a cell periodic along x1 contains a path that winds once around x1.
+
+    Breadth-first search over gas cells with 4-neighbours, tracking the unwrapped x1 coordinate of each
+    visit: reaching a cell again at an unwrapped position differing by a multiple of nx closes such a path.
+    """
+    ny, nx = mask.shape
+    seen = np.full((ny, nx), np.iinfo(np.int64).min, dtype=np.int64)
+    for sj, si in zip(*np.nonzero(mask == 0)):
+        if seen[sj, si] != np.iinfo(np.int64).min:
+            continue
+        seen[sj, si] = si
+        queue = [(sj, si, si)]
+        while queue:
+            j, i, u = queue.pop()
+            for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+                jj, uu = j + dj, u + di
+                if not periodic_y and (jj < 0 or jj >= ny):
+                    continue
+                jj %= ny
+                ii = uu % nx
+                if mask[jj, ii]:
+                    continue
+                if seen[jj, ii] == np.iinfo(np.int64).min:
+                    seen[jj, ii] = uu
+                    queue.append((jj, ii, uu))
+                elif seen[jj, ii] != uu:
+                    return True
+    return False
+
+
 def wm_roughness(x: np.ndarray, D: float = 1.5, gamma: float = 1.5, n1: int = -4, n_max: int = 8) -> np.ndarray:
     """Weierstrass-Mandelbrot profile of Eq. (WM) with unit scale A: sum over n = n1 .. n_max of
     cos(2 pi gamma^n x) / gamma^((2 - D) n), x in units of H.  The paper sums to infinity; a grid
@@ -185,6 +266,38 @@ def porous_instance(kn: float, n: int = 256, nv: int = 48, porosity: float = 0.6
     mask, phi = porous_disks_mask(n, porosity, rmin, rmax, seed)
     return Instance(f"porous{n}_phi{porosity:g}_s{seed}_cubic{nv}_kn{kn:g}", mask, True, True, kn,
                     ("cubic", nv, 4.0), {"porosity": phi, "seed": seed})
+
+
+MEDIA = ("irregular", "squares", "disks")
+
+
+def medium_mask(kind: str, n: int = 256, porosity: float = 0.6):
+    """The three synthetic media standing in for media 1-3 of Sec. III (irregular, square and circular
+    solids), n x n cells over the height H, periodic in both axes, a dozen grains or fewer (pores of
+    about 0.1 H); feature sizes scale with n / 256.  Grains are added until the gas fraction is at or
+    below `porosity`; the achieved value is returned with the mask."""
+    f = n / 256.0
+    if kind == "irregular":
+        return porous_irregular_mask(n, porosity, corr=20.0 * f, seed=3)
+    if kind == "squares":
+        return porous_squares_mask(n, porosity, max(3, int(round(32 * f))), max(4, int(round(80 * f))), seed=2,
+                                   gap=max(1, int(round(4 * f))))
+    if kind == "disks":
+        return porous_disks_mask(n, porosity, max(3, int(round(20 * f))), max(4, int(round(48 * f))), seed=1,
+                                 gap=max(1, int(round(2 * f))))
+    raise ValueError(f"unknown medium {kind!r}")
+
+
+def refine_mask(mask: np.ndarray, factor: int) -> np.ndarray:
+    """The same staircase geometry on a grid `factor` times finer: every cell becomes factor x factor."""
+    return np.kron(np.asarray(mask, dtype=np.uint8), np.ones((factor, factor), dtype=np.uint8))
+
+
+def medium_instance(kind: str, kn: float, n: int = 256, nv: int = 32, porosity: float = 0.6) -> Instance:
+    """Force-driven (Poiseuille) flow through one synthetic medium, cubic nv x nv velocities."""
+    mask, phi = medium_mask(kind, n, porosity)
+    return Instance(f"{kind}{n}_phi{porosity:g}_cubic{nv}_kn{kn:g}", mask, True, True, kn, ("cubic", nv, 4.0),
+                    {"porosity": phi, "medium": kind})
 
 
 def batched_instances(count: int = 64, seed0: int = 0):

@@ -525,3 +525,36 @@ def test_paper_size_couette_channels():
     rough.solve(tol=1e-6, max_iter=20000)
     q_star = rough.flowrate()[0] / q_s
     assert 0.9 < q_star < 1.0, q_star
+
+
+# ------------------------------------------------------------------ permeability curves (Sec. III)
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_permeability_curve_matches_oracle(precision):
+    """k_a at every Knudsen number of a 48 x 48 disk medium (curve points, cubic 12^2 velocities) and
+    of the same medium refined twice (fit points, Gauss-Hermite 8^2), each set one batch on the GPU,
+    against the oracle's k_a = sqrt(4/pi) Q Kn on the same grids; the same k_inf and Kn* from the
+    oracle's values.  FP32 storage: the slow small-Kn solves amplify rounding (bound 2e-4)."""
+    from paper_1704_03126_gb300 import permeability as perm
+    mask, phi = inputs.medium_mask("disks", 48)
+    quad, fit_quad = ("cubic", 12, 4.0), ("gh", 8, 0.0)
+    kns, fit = (0.5, 2.0), (0.05, 0.1, 0.2)
+    res = perm.permeability_curve(mask, kns, fit, quad=quad, fit_quad=fit_quad, fit_refine=2, precision=precision)
+    assert all(s == 0 for s in res["status"].values())
+    ora = {}
+    fine = inputs.refine_mask(mask, 2)
+    for kn in kns + fit:
+        m, q = (fine, fit_quad) if kn in fit else (mask, quad)
+        r = oracle.solve(oracle.Problem.make(m, True, True, dvm.kn_to_delta(kn), q), tol=1e-12, max_iter=200000)
+        assert r["converged"]
+        ora[kn] = perm.apparent_permeability(r["Q"], kn)
+    tol = 1e-9 if precision == "fp64" else 2e-4
+    for kn, ka in zip(res["kn"] + res["fit_kn"], res["k_a"] + res["fit_k_a"]):
+        assert abs(ka - ora[kn]) < tol * ora[kn], (kn, ka, ora[kn])
+    k_inf = perm.intrinsic_permeability(fit, [ora[k] for k in fit])
+    assert abs(res["k_inf"] - k_inf) < 10 * tol * k_inf
+    assert np.allclose(res["kn_star"], perm.equivalent_knudsen(kns, k_inf, phi), rtol=10 * tol)
+    assert abs(res["phi"] - phi) < 1e-15
+    # slip adds flow: k_a exceeds k_inf and grows with Kn over this range
+    assert all(r > 1.0 for r in res["k_a_over_k_inf"])
+    assert res["k_a"][1] > res["k_a"][0]
