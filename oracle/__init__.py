@@ -46,6 +46,7 @@ class _Problem(ctypes.Structure):
         ("mask", ctypes.c_void_p), ("delta", ctypes.c_void_p),
         ("nv", ctypes.c_int), ("xv", ctypes.c_void_p), ("wv", ctypes.c_void_p),
         ("alpha", ctypes.c_double), ("force", ctypes.c_double), ("top_u", ctypes.c_double),
+        ("dy", ctypes.c_void_p),
     ]
 
 
@@ -113,9 +114,13 @@ class Problem:
     force: float = 1.0
     ly: float = 1.0
     top_u: float = 0.0          # speed of the plate beyond the last row (Couette flow), 0 = at rest
+    dy: np.ndarray = None       # row heights [ny] (x2 spacing), or None for square cells ly / ny
+    dx1: float = None           # x1 spacing when dy is given
 
     @staticmethod
-    def make(mask, periodic_x, periodic_y, delta, quad=("gh", 8, 5.0), alpha=1.0, force=1.0, ly=1.0, top_u=0.0):
+    def make(mask, periodic_x, periodic_y, delta, quad=("gh", 8, 5.0), alpha=1.0, force=1.0, ly=1.0, top_u=0.0,
+             dy=None, dx1=None):
+        """dy: row heights (then ly = sum dy and dx1, the x1 spacing, must be given)."""
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         ny, nx = mask.shape
         d = np.broadcast_to(np.asarray(delta, dtype=np.float64), (ny, nx))
@@ -124,8 +129,14 @@ class Problem:
         xv, wv = quadrature(kind, n, vmax)
         if top_u != 0.0 and periodic_y:
             raise ValueError("a moving top plate needs a non-periodic x2 axis")
+        if dy is not None:
+            dy = np.ascontiguousarray(dy, dtype=np.float64)
+            if dy.shape != (ny,) or not np.all(dy > 0) or dx1 is None or not dx1 > 0:
+                raise ValueError("dy needs ny positive row heights and a positive x1 spacing dx1")
+            ly = float(dy.sum())
+            dx1 = float(dx1)
         return Problem(mask, bool(periodic_x), bool(periodic_y), np.ascontiguousarray(d), xv, wv,
-                       float(alpha), float(force), float(ly), float(top_u))
+                       float(alpha), float(force), float(ly), float(top_u), dy, dx1)
 
     @property
     def nx(self):
@@ -141,7 +152,11 @@ class Problem:
 
     @property
     def dx(self):
-        return self.ly / self.ny
+        """x1 spacing (the square cell size ly / ny unless row heights are given)."""
+        return self.dx1 if self.dy is not None else self.ly / self.ny
+
+    def row_heights(self):
+        return self.dy if self.dy is not None else np.full(self.ny, self.dx)
 
     def velocities(self):
         """Tensor-product table: v1[k], v2[k], W[k] with k = a*nv + b."""
@@ -151,10 +166,11 @@ class Problem:
         return v1, v2, W
 
     def _c(self):
-        self._keep = (self.mask, self.delta, self.xv, self.wv)
+        self._keep = (self.mask, self.delta, self.xv, self.wv, self.dy)
         return _Problem(self.nx, self.ny, int(self.periodic_x), int(self.periodic_y), self.dx,
                         self.mask.ctypes.data, self.delta.ctypes.data, self.nv,
-                        self.xv.ctypes.data, self.wv.ctypes.data, self.alpha, self.force, self.top_u)
+                        self.xv.ctypes.data, self.wv.ctypes.data, self.alpha, self.force, self.top_u,
+                        self.dy.ctypes.data if self.dy is not None else None)
 
 
 def delta_from_kn(kn: float) -> float:
@@ -218,6 +234,7 @@ def adjoint(prob: Problem, h: np.ndarray, c_shift: float, tol: float = 1e-10, ma
 
 
 def flow_rate(prob: Problem, u1: np.ndarray) -> float:
-    """Q = sum_gas u1 dA / Lx (Sec. III)."""
+    """Q = sum_gas u1 dA / Lx (Sec. III), dA = dx dy_j."""
     gas = prob.mask == 0
-    return float(u1[gas].sum() * prob.dx * prob.dx / (prob.nx * prob.dx))
+    dA = prob.dx * prob.row_heights()[:, None] * np.ones((1, prob.nx))
+    return float((u1 * dA)[gas].sum() / (prob.nx * prob.dx))

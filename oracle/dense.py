@@ -15,7 +15,10 @@ Gram matrix of psi: the projection of h onto the collision invariants, which for
 is rho + 2 u.v + tau (|v|^2 - 1) with the moments rho, u, tau of Sec. II.A.  Wall values h_w = alpha rho_w + (1 - alpha) h(mirror v), with
 rho_w = sum_{v.n<0} |v.n| W h / sum_{v.n>0} (v.n) W at the gas cell owning the face; the plate beyond
 the last row may move along x1 with speed U (Couette flow, Eq. diffuse1), adding alpha 2 U v1 to its
-wall value (a source term of the system).
+wall value (a source term of the system).  Rows may have unequal heights (x2 spacing of Sec. II.A):
+each upwind derivative is then the derivative at the cell centre of the polynomial through the
+points the stencil uses (the cell centre, the upstream centres, or the wall face), its weights found
+by solving the small Vandermonde system of that polynomial.
 """
 from __future__ import annotations
 
@@ -33,6 +36,17 @@ def _solid(mask, px, py, i, j):
             return True
         j %= ny
     return bool(mask[j, i])
+
+
+def derivative_weights(offsets):
+    """Weights w with sum_m w_m p(t_m) = p'(0) for every polynomial p of degree len - 1 through the
+    points t_m (t_0 = 0, the cell centre)."""
+    t = np.asarray(offsets, dtype=np.float64)
+    V = np.vander(t, len(t), increasing=True).T  # rows: 1, t, t^2 evaluated at the points
+    rhs = np.zeros(len(t))
+    if len(t) > 1:
+        rhs[1] = 1.0
+    return np.linalg.solve(V, rhs)
 
 
 def collision_kernel(v1, v2, W):
@@ -57,6 +71,7 @@ def assemble(prob):
     B = np.zeros((n + 1, n + 1))
     b = np.zeros(n + 1)
     dx = prob.dx
+    rows = prob.row_heights()
     nv = prob.nv
     Ckern = collision_kernel(v1, v2, W)
     # wall normalisers per side: W (normal +x), E (-x), S (+y), N (-y)
@@ -89,28 +104,36 @@ def assemble(prob):
             for axis in (0, 1):
                 va = v1[k] if axis == 0 else v2[k]
                 s = 1 if va > 0 else -1
-                ca = abs(va) / dx
                 di, dj = (1, 0) if axis == 0 else (0, 1)
                 side = ("W" if s > 0 else "E") if axis == 0 else ("S" if s > 0 else "N")
                 i1, j1 = i - s * di, j - s * dj
                 i2, j2 = i - 2 * s * di, j - 2 * s * dj
+                # cell sizes along the axis at the cell and its two upstream neighbours
+                size = (lambda jj: dx) if axis == 0 else (lambda jj: rows[jj % ny])
+                h0, h1, h2 = size(j), size(j1), size(j2)
+                # v_a dh/dx_a = |v_a| (dh/dt at t = 0), t the distance against the flow direction
                 if _solid(mask, px, py, i1, j1):
-                    diag += ca * 2.0
-                    add_wall(row, ca * 2.0, g, side, k)
+                    # the polynomial through the wall face (t = -h0/2) and the cell centre
+                    w = derivative_weights([0.0, -0.5 * h0])
+                    diag += abs(va) * w[0]
+                    add_wall(row, -abs(va) * w[1], g, side, k)
                     if side == "N" and not py and j == ny - 1 and prob.top_u != 0.0:
                         # the moving plate's wall value carries the drift 2 U v1 (Eq. diffuse1)
-                        src += ca * 2.0 * prob.alpha * 2.0 * prob.top_u * v1[k]
+                        src += -abs(va) * w[1] * prob.alpha * 2.0 * prob.top_u * v1[k]
                 elif _solid(mask, px, py, i2, j2):
                     # second cell from a wall: first-order upwind through the gas neighbour
-                    diag += ca
+                    w = derivative_weights([0.0, -0.5 * (h0 + h1)])
+                    diag += abs(va) * w[0]
                     g1 = gid[(i1 % nx, j1 % ny)]
-                    B[row, idx(k, g1)] -= ca
+                    B[row, idx(k, g1)] += abs(va) * w[1]
                 else:
-                    diag += ca * 1.5
+                    t1 = -0.5 * (h0 + h1)
+                    w = derivative_weights([0.0, t1, t1 - 0.5 * (h1 + h2)])
+                    diag += abs(va) * w[0]
                     g1 = gid[(i1 % nx, j1 % ny)]
                     g2 = gid[(i2 % nx, j2 % ny)]
-                    B[row, idx(k, g1)] -= ca * 2.0
-                    B[row, idx(k, g2)] -= ca * (-0.5)
+                    B[row, idx(k, g1)] += abs(va) * w[1]
+                    B[row, idx(k, g2)] += abs(va) * w[2]
             B[row, idx(k, g)] += diag
             # collision: -delta M_k(h) at this cell
             for jv in range(K):
@@ -140,7 +163,8 @@ def solve(prob):
         h[:, j, i] = x[np.arange(K) * G + g]
     v1, v2, W = prob.velocities()
     u1 = np.tensordot(W * v1, h, axes=(0, 0))
-    Q = float(u1[prob.mask == 0].sum() * prob.dx * prob.dx / (nx * prob.dx))
+    area = prob.dx * prob.row_heights()[:, None] * np.ones((1, nx))
+    Q = float((u1 * area)[prob.mask == 0].sum() / (nx * prob.dx))
     return dict(h=h, c=float(x[-1]), Q=Q, B=B, b=b, x=x, gas_cells=gas_cells)
 
 

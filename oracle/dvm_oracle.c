@@ -32,6 +32,15 @@
  *             on linear fields.  The quadratic through h0, h(u1) and the wall value would put a
  *             negative weight on the lagged wall value, and the iteration then diverges in narrow
  *             pores (an oscillating mode), so the second cell from a wall is first order.
+ *   spacing   x1 spacing dx is uniform; the rows may have heights dy_j (Sec. II.A: the paper puts 60
+ *             rows across the rough band and 100 above it).  With upstream centre distances
+ *             d1 = (dy_c + dy_u1)/2 and d2 = d1 + (dy_u1 + dy_u2)/2 the three forms become the
+ *             derivative at the cell centre of the Lagrange interpolant through the same points:
+ *             interior kappa = 1/d1 + 1/d2, combo = d2/(d1 (d2-d1)) h(u1) - d1/(d2 (d2-d1)) h(u2);
+ *             first order kappa = 1/d1, combo = h(u1)/d1; next to a wall (face at dy_c/2)
+ *             kappa = 2/dy_c, combo = (2/dy_c) h_w -- per unit length, multiplied by |v2|.  For
+ *             equal heights they are the forms above divided by dx.  Still exact on linear fields.
+ *             Q weights each cell by its area dx dy_j.
  *   moving    the plate beyond the last row (x2 = H, non-periodic x2) may move along x1 with speed
  *             U (Couette flow, Sec. II.A, Eq. diffuse1): its reflected molecules carry the drift
  *             2 U v1 in addition to rho_w; every other wall is at rest (Eq. diffuse2).
@@ -161,6 +170,7 @@ typedef struct {
   double alpha;              /* accommodation: 1 = fully diffuse walls */
   double force;              /* body-force source coefficient F (source F v1) */
   double top_u;              /* speed U along x1 of the plate beyond the last row (Couette), or 0 */
+  const double *dy;          /* row heights [ny] (x2 spacing), or NULL: square cells of size dx */
 } orc_problem;
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
@@ -336,6 +346,26 @@ static void upwind_axis(const orc_problem *p, const double *hk, const double *rh
                         double *kappa, double *combo) {
   int side = (di != 0) ? (s > 0 ? SIDE_W : SIDE_E) : (s > 0 ? SIDE_S : SIDE_N);
   int i1 = i - s * di, j1 = j - s * dj, i2 = i - 2 * s * di, j2 = j - 2 * s * dj;
+  if (p->dy && dj != 0) {
+    /* rows of unequal height: Lagrange forms per unit length, scaled back by dx for the caller's
+     * (|v|/dx) factor */
+    double hc = p->dy[j];
+    if (solid_at(p, i1, j1)) {
+      *kappa = 2.0 / hc * p->dx;
+      *combo = 2.0 / hc * p->dx * wall_value(p, rho_w, h_old, cell_id(p, i, j), side, k);
+      return;
+    }
+    double d1 = 0.5 * (hc + p->dy[wrap(j1, p->ny)]);
+    if (solid_at(p, i2, j2)) {
+      *kappa = p->dx / d1;
+      *combo = p->dx / d1 * hk[cell_id(p, i1, j1)];
+      return;
+    }
+    double d2 = d1 + 0.5 * (p->dy[wrap(j1, p->ny)] + p->dy[wrap(j2, p->ny)]);
+    *kappa = p->dx * (1.0 / d1 + 1.0 / d2);
+    *combo = p->dx * (d2 / (d1 * (d2 - d1)) * hk[cell_id(p, i1, j1)] - d1 / (d2 * (d2 - d1)) * hk[cell_id(p, i2, j2)]);
+    return;
+  }
   if (solid_at(p, i1, j1)) {
     *kappa = 2.0;
     *combo = 2.0 * wall_value(p, rho_w, h_old, cell_id(p, i, j), side, k);
@@ -391,8 +421,8 @@ static double q_flow(const orc_problem *p, const double *u1) {
   size_t ncell = (size_t)p->nx * p->ny;
   double q = 0;
   for (size_t c = 0; c < ncell; ++c)
-    if (!p->mask[c]) q += u1[c];
-  return q * p->dx * p->dx / (p->nx * p->dx);
+    if (!p->mask[c]) q += u1[c] * (p->dy ? p->dy[c / p->nx] : p->dx);
+  return q * p->dx / (p->nx * p->dx);
 }
 
 /* Solve by source iteration from the state in h (zeros for a cold start) and c_shift.
@@ -402,6 +432,9 @@ int orc_solve(const orc_problem *p, double tol, int max_iter, double *h, double 
               double *rho, double *u1, double *u2, double *tau, double *eps_hist,
               orc_result *res) {
   if (p->nx < 2 || p->ny < 2 || p->nv < 2 || (p->nv & 1) || max_iter < 1) return ORC_EINVAL;
+  if (p->dy)
+    for (int j = 0; j < p->ny; ++j)
+      if (!(p->dy[j] > 0.0) || !isfinite(p->dy[j])) return ORC_EINVAL;
   size_t ncell = (size_t)p->nx * p->ny;
   int K = p->nv * p->nv;
   long ngas = 0;
@@ -610,7 +643,7 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
   int K = p->nv * p->nv;
   long ngas = 0;
   for (size_t c = 0; c < ncell; ++c) ngas += !p->mask[c];
-  if (ngas == 0 || max_iter < 1) return ORC_EINVAL;
+  if (ngas == 0 || max_iter < 1 || p->dy) return ORC_EINVAL; /* square cells only */
   double sumW = 0;
   for (int k = 0; k < K; ++k) sumW += p->wv[k / p->nv] * p->wv[k % p->nv];
   double norm_side[4];

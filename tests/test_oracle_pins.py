@@ -303,3 +303,96 @@ def test_wm_roughness_has_the_requested_rms():
     base = heights.mean() - r.mean()
     assert np.max(np.abs(heights - (base + r))) <= dx
     assert mask[-1].sum() == 0  # the top rows are gas: the moving plate lies beyond the last row
+
+
+# ---------------------------------------------------------------- rows of unequal height (Sec. II.A grid)
+
+def _stretched_rows(ny, seed, symmetric=False):
+    """Seeded row heights in [0.4, 1.6] (relative), normalised to H = 1; mirrored when symmetric."""
+    rng = inputs.SplitMix64(seed)
+    h = np.array([0.4 + 1.2 * rng.uniform() for _ in range(ny)])
+    if symmetric:
+        h = 0.5 * (h + h[::-1])
+    return h / h.sum()
+
+
+@pytest.mark.parametrize("quad", [("gh", 8, 0.0), ("nc", 12, 5.0)])
+def test_free_molecular_plates_exact_on_unequal_rows(quad):
+    """delta = 0: h = v1 d / |v2| is linear in x2, and the unequal-row stencils (Lagrange derivatives
+    through the same points) are exact on linear fields, so the discrete solution is exact on any row
+    heights; Q = 1/2 sum W v1^2 / |v2| (midpoint areas integrate a linear profile exactly)."""
+    ny = 24
+    dy = _stretched_rows(ny, 11)
+    p = oracle.Problem.make(inputs.plates_mask(4, ny), True, False, 0.0, quad, dy=dy, dx1=0.03)
+    r = oracle.solve(p, tol=0.0, max_iter=600)
+    v1, v2, W = p.velocities()
+    y = np.cumsum(dy) - 0.5 * dy
+    d = np.where(v2[:, None] > 0, y[None, :], 1.0 - y[None, :])
+    h_exact = v1[:, None] * d / np.abs(v2)[:, None]
+    assert np.max(np.abs(r["h"][:, :, 0] - h_exact)) < 1e-10 * np.abs(h_exact).max()
+    q_exact = 0.5 * np.sum(W * v1 * v1 / np.abs(v2))
+    assert abs(r["Q"] - q_exact) < 1e-11 * q_exact
+    assert abs(oracle.flow_rate(p, r["u1"]) - r["Q"]) < 1e-14
+
+
+def test_equal_row_heights_reproduce_square_cells():
+    """Heights all equal to the x1 spacing: the general stencils reduce to the square-cell ones."""
+    mask = inputs.rough_channel_mask(24)
+    ny = mask.shape[0]
+    a = oracle.solve(oracle.Problem.make(mask, True, False, 1.3, ("nc", 8, 4.0)), tol=1e-13, max_iter=100000)
+    b = oracle.solve(oracle.Problem.make(mask, True, False, 1.3, ("nc", 8, 4.0), dy=np.full(ny, 1.0 / ny),
+                                         dx1=1.0 / ny), tol=1e-13, max_iter=100000)
+    assert abs(a["Q"] - b["Q"]) < 1e-12 * abs(a["Q"])
+    assert np.nanmax(np.abs(a["u1"] - b["u1"])) < 1e-11
+
+
+def _unequal_row_cases():
+    notch = np.zeros((8, 4), np.uint8)
+    notch[0:2, 1] = 1
+    notch[7, 2:4] = 1
+    return [
+        ("plates_gh6", np.zeros((7, 3), np.uint8), True, False, 0.7, ("gh", 6, 0.0), 1.0, 0.0),
+        ("notched_nc6", notch, True, False, 3.0, ("nc", 6, 4.0), 1.0, 0.0),
+        ("notched_gh6_alpha0.6", notch, True, False, 1.0, ("gh", 6, 0.0), 0.6, 0.0),
+        ("couette_notched_cubic6", notch, True, False, 1.5, ("cubic", 6, 4.0), 1.0, 1.0),
+        ("periodic_rows_block_gh6", np.pad(np.ones((2, 2), np.uint8), 2), True, True, 2.0, ("gh", 6, 0.0), 1.0, 0.0),
+    ]
+
+
+@pytest.mark.parametrize("case", _unequal_row_cases(), ids=lambda c: c[0])
+def test_unequal_rows_iteration_matches_dense_solve(case):
+    """The iteration (closed-form Lagrange weights in C) and the dense solve (weights from a
+    Vandermonde solve) reach the same fixed point on rows of unequal height."""
+    name, mask, px, py, delta, quad, alpha, top_u = case
+    dy = _stretched_rows(mask.shape[0], 5)
+    p = oracle.Problem.make(mask, px, py, delta, quad, alpha=alpha, force=0.0 if top_u else 1.0, top_u=top_u,
+                            dy=dy, dx1=0.11)
+    ds = dense.solve(p)
+    r = oracle.solve(p, tol=1e-14, max_iter=400000)
+    assert r["converged"]
+    assert abs(r["Q"] - ds["Q"]) < 1e-11 * abs(ds["Q"])
+    assert np.max(np.abs(r["h"] - ds["h"])) < 1e-10 * max(1.0, np.abs(ds["h"]).max())
+
+
+@pytest.mark.parametrize("kn", [0.1, 1.0])
+def test_plane_couette_on_symmetric_unequal_rows(kn):
+    """Rows mirrored about the mid-plane keep the mirror symmetry of the Couette argument, so
+    Q = U H m0 m2 and u1(x2) + u1(H - x2) = 2 U m0 m2 hold on them too."""
+    ny = 20
+    dy = _stretched_rows(ny, 3, symmetric=True)
+    p = oracle.Problem.make(np.zeros((ny, 3), np.uint8), True, False, oracle.delta_from_kn(kn), ("gh", 8, 0.0),
+                            force=0.0, top_u=1.0, dy=dy, dx1=0.05)
+    m0, m2 = float(p.wv.sum()), float((p.wv * p.xv ** 2).sum())
+    r = oracle.solve(p, tol=1e-13, max_iter=400000)
+    assert r["converged"]
+    assert abs(r["Q"] - m0 * m2) < 1e-10
+    u1 = r["u1"][:, 0]
+    assert np.max(np.abs(u1 + u1[::-1] - 2.0 * m0 * m2)) < 1e-10
+
+
+def test_unequal_rows_have_no_oracle_adjoint():
+    p = oracle.Problem.make(np.zeros((6, 3), np.uint8), True, False, 1.0, ("gh", 4, 0.0), dy=_stretched_rows(6, 1),
+                            dx1=0.1)
+    r = oracle.solve(p, tol=1e-10)
+    with pytest.raises(ValueError):
+        oracle.adjoint(p, r["h"], r["c"])
