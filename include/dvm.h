@@ -99,6 +99,16 @@ typedef struct {
                                  only and has no adjoint (DVM_EINVAL there). */
   int storage;                /* dvm_storage; the width limits of the sweeps (nx <= 256 rows, 512
                                  columns) apply to the stored x1 axis */
+  double dx1;                 /* x1 spacing; 0 = square cells (ly / ny).  Cells are dx1 x (ly / ny)
+                                 rectangles otherwise.  Q and k_a keep their definitions (Sec. III). */
+  const double *row_heights;  /* host double [ny], read by dvm_create only, or NULL: the heights of the
+                                 rows along x2 (Sec. II.A: the paper resolves the rough band of its
+                                 Couette channel with 60 rows and the rest with 100), all > 0; ly is then
+                                 their sum and dx1 must be > 0.  Each upwind difference along x2 becomes
+                                 the derivative at the cell centre of the polynomial through the same
+                                 points (exact on linear fields, like the equal-row forms).  Needs the
+                                 transposed storage (DVM_STORAGE_AS_GIVEN gives DVM_EINVAL) and runs on
+                                 the column sweep only; no adjoint.  The adjoint needs square cells. */
 } dvm_params;
 
 /* The transport sweep kernel (both compute the same update; see dvm_set_schedule; nx below is the
@@ -115,7 +125,7 @@ typedef enum { DVM_SWEEP_AUTO = 0, DVM_SWEEP_ROWS = 1, DVM_SWEEP_COLUMNS = 2 } d
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
  * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape, plates at rest,
- * automatic storage. */
+ * automatic storage, square cells, equal rows. */
 dvm_status dvm_params_init(dvm_params *params);
 
 /* Build a solver for one geometry.

@@ -29,7 +29,10 @@ struct dvm_ctx {
   // the longer axis; the caller's cell (i, j) is stored at (j, i) and its x1 is the stored x2
   bool tr = false;
   int unx = 0, uny = 0;
-  double dx = 0.0;
+  double dxs = 0.0, dys = 0.0;     // stored x reference spacing and stored y spacing
+  bool square = true;              // square cells (the adjoint's case)
+  bool nux = false;                // stored x spacing varies by column (the caller's unequal rows)
+  double *d_xwidth = nullptr;      // nux: stored column widths / dxs
   bool fp64 = true, store_h = false, uniform = true;
   double delta = 0.0, kn = 0.0;
   std::vector<double> x1, w1;
@@ -54,7 +57,7 @@ struct dvm_ctx {
   double alpha = 1.0;              // accommodation
   double top_u = 0.0;              // speed of the plate beyond the last row (Couette flow)
   int nwall = 0;
-  int *d_wall_slot = nullptr;      // alpha < 1: [ncell][4] face slots
+  int *d_wall_slot = nullptr;      // alpha < 1: [ncell][4] face slots (freed with the context)
   void *d_wbuf = nullptr;          // alpha < 1: incident values at the wall faces, two parities
   dvm_batch *self = nullptr;       // batch of this context alone (built on first use)
   DeviceState *h_state = nullptr;  // pinned
@@ -99,6 +102,10 @@ inline size_t stored_cell(const dvm_ctx *c, size_t ucell) {
   return (ucell % c->unx) * (size_t)c->nx + ucell / c->unx;
 }
 
+// Features that only the column sweep's special variant implements: accommodation < 1, a moving
+// plate, columns of unequal width.
+inline bool needs_special(const dvm_ctx *c) { return c->alpha < 1.0 || c->top_u != 0.0 || c->nux; }
+
 #define DVM_CUDA(ctx, call)                                                                     \
   do {                                                                                          \
     cudaError_t e_ = (call);                                                                    \
@@ -111,7 +118,6 @@ constexpr int kFinBlock = 256;
 template <typename T>
 void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T> &inv) {
   const int half = c->half, gq = c->gq;
-  const double dx = c->dx;
   vel.assign((size_t)c->ngroups * kNumVelFields * kLanes, T(0));
   inv.assign((size_t)c->ngroups * kInvRows * kLanes, T(0));  // row 9 stays 0 (solid cells)
   const double kap[3] = {1.5, 1.0, 2.0};  // interior, second cell from a wall, next to a wall
@@ -125,7 +131,7 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
       const double v1 = s1 * c->x1[half + a], v2 = s2 * c->x1[half + b];
       const double W = valid ? c->w1[half + a] * c->w1[half + b] : 0.0;
       const double e = v1 * v1 + v2 * v2 - 1.0;
-      const double cx = std::fabs(v1) / dx, cy = std::fabs(v2) / dx;
+      const double cx = std::fabs(v1) / c->dxs, cy = std::fabs(v2) / c->dys;
       const double z = valid ? 1.0 : 0.0;
       const double f[kNumVelFields] = {v1, v2, e, cx, cy, W, W * v1, W * v2, W * (v1 * v1 + v2 * v2),
                                        std::fabs(v1) * W, std::fabs(v2) * W,
@@ -205,7 +211,8 @@ bool resolve_schedule(int nx_max, int kind, int v, Schedule *out, std::string *w
       return false;
     }
     if (specular) {
-      *why = "the row sweep supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)";
+      *why = "the row sweep supports fixed, fully diffuse walls on equal rows only (accommodation = 1, no moving "
+             "plate, no row heights)";
       return false;
     }
     if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16) {
@@ -282,6 +289,9 @@ void release_device(dvm_ctx *c) {
   free_dev(c->d_desc);
   free_dev(c->d_sweep_map);
   free_dev(c->d_fin_map);
+  free_dev(c->d_wall_slot);
+  free_dev(c->d_wbuf);
+  free_dev(c->d_xwidth);
   if (c->h_state) cudaFreeHost(c->h_state);
   c->h_state = nullptr;
   if (c->a_graph) cudaGraphExecDestroy(c->a_graph);
@@ -391,7 +401,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   bool spec = false;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(c0, DVM_EINVAL, "null context in batch");
-    spec = spec || ctxs[i]->alpha < 1.0 || ctxs[i]->top_u != 0.0;
+    spec = spec || needs_special(ctxs[i]);
     if (ctxs[i]->fp64 != c0->fp64 || ctxs[i]->store_h != c0->store_h)
       return fail(c0, DVM_EINVAL, "batched contexts must share precision and store_distribution");
     if (ctxs[i]->device != c0->device) return fail(c0, DVM_EINVAL, "batched contexts must share a device");
@@ -403,7 +413,8 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   if (force) {
     sched = *force;
     if (spec && sched.kind == DVM_SWEEP_ROWS)
-      return fail(c0, DVM_EINVAL, "the row sweep supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)");
+      return fail(c0, DVM_EINVAL, "the row sweep supports fixed, fully diffuse walls on equal rows only (accommodation = 1, "
+                                  "no moving plate, no row heights)");
   } else {
     std::string why;
     if (!resolve_schedule(nx_max, c0->sched_kind, c0->sched_v, &sched, &why, spec)) return fail(c0, DVM_EINVAL, why);
@@ -423,7 +434,8 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   b->cw = 1;
   for (int i = 0; i < n; ++i) {
     b->cw = std::max(b->cw, ctxs[i]->cw);
-    b->uniform = b->uniform && ctxs[i]->uniform;
+    // the 1/denominator tables hold one value per stencil class: unequal columns need the per-cell form
+    b->uniform = b->uniform && ctxs[i]->uniform && !ctxs[i]->nux;
   }
   if (!cols && sched.v > 0) b->cw = sched.v;
   b->warps = 1;
@@ -663,19 +675,40 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   if (P.sweep_warps < 0 || P.sweep_warps > kMaxWarps) return fail(nullptr, DVM_EINVAL, "sweep_warps must be 0..32");
   if (P.storage != DVM_STORAGE_AUTO && P.storage != DVM_STORAGE_AS_GIVEN && P.storage != DVM_STORAGE_TRANSPOSED)
     return fail(nullptr, DVM_EINVAL, "storage must be DVM_STORAGE_AUTO, _AS_GIVEN or _TRANSPOSED");
+  if (!(P.dx1 >= 0.0) || !std::isfinite(P.dx1)) return fail(nullptr, DVM_EINVAL, "dx1 must be finite and >= 0");
+  double ly = P.ly;
+  if (P.row_heights) {
+    if (!(P.dx1 > 0.0)) return fail(nullptr, DVM_EINVAL, "row heights need the x1 spacing dx1 > 0");
+    if (P.storage == DVM_STORAGE_AS_GIVEN)
+      return fail(nullptr, DVM_EINVAL, "row heights need the transposed storage (DVM_STORAGE_AUTO or _TRANSPOSED)");
+    ly = 0.0;
+    for (int j = 0; j < P.ny; ++j) {
+      if (!(P.row_heights[j] > 0.0) || !std::isfinite(P.row_heights[j]))
+        return fail(nullptr, DVM_EINVAL, "row heights must be finite and > 0");
+      ly += P.row_heights[j];
+    }
+  }
 
   dvm_ctx *c = new (std::nothrow) dvm_ctx();
   if (!c) return fail(nullptr, DVM_ENOMEM, "host allocation failed");
   c->P = P;
   // the sweeps run along the stored x2 (column sweep: one thread per stored column; row sweep: rows in
   // flight across the stored x1), so a grid wider than tall is stored transposed by default
-  c->tr = P.storage == DVM_STORAGE_TRANSPOSED || (P.storage == DVM_STORAGE_AUTO && P.nx > P.ny);
+  // (row heights: the caller's x2 becomes the stored x1, along which every sweep thread owns a column)
+  c->tr = P.storage == DVM_STORAGE_TRANSPOSED || (P.storage == DVM_STORAGE_AUTO && (P.nx > P.ny || P.row_heights));
   c->unx = P.nx;
   c->uny = P.ny;
   c->nx = c->tr ? P.ny : P.nx;
   c->ny = c->tr ? P.nx : P.ny;
   c->ncell = P.nx * P.ny;
-  c->dx = P.ly / P.ny;
+  {
+    // caller's spacings: x1 uniform (dx1, or square cells ly / ny), x2 the mean row height ly / ny
+    const double udy = ly / P.ny, udx = P.dx1 > 0.0 ? P.dx1 : udy;
+    c->dxs = c->tr ? udy : udx;
+    c->dys = c->tr ? udx : udy;
+    c->nux = P.row_heights != nullptr;
+    c->square = !c->nux && udx == udy;
+  }
   c->fp64 = P.precision == DVM_FP64;
   c->store_h = P.store_distribution != 0;
   c->alpha = P.accommodation;
@@ -819,6 +852,14 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
     CREATE_CUDA(cudaMemset(c->d_wbuf, 0, wbytes));
   }
 
+  if (c->nux) {
+    // stored column i is the caller's row i: its width relative to the mean row height
+    std::vector<double> w(c->nx);
+    for (int i = 0; i < c->nx; ++i) w[i] = P.row_heights[i] / c->dxs;
+    CREATE_CUDA(cudaMalloc(&c->d_xwidth, sizeof(double) * c->nx));
+    CREATE_CUDA(cudaMemcpy(c->d_xwidth, w.data(), sizeof(double) * c->nx, cudaMemcpyHostToDevice));
+  }
+
   // launch maps of a single-instance launch
   std::vector<int> smap(c->ngroups), fmap;
   for (int g = 0; g < c->ngroups; ++g) smap[g] = g;
@@ -840,9 +881,13 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   D.groups_per_quadrant = c->gq;
   D.n_gas = c->geo.n_gas;
   D.fin_nblocks = fin_nblocks;
-  D.dx = c->dx;
+  D.dx = c->dxs;
+  D.dy = c->dys;
   D.flow_axis = c->tr ? 1 : 0;
-  D.dA_over_Lx = D.dx / c->unx;  // dx^2 / Lx with the caller's Lx = unx dx
+  // Q = sum u1 dx1 dy / (unx dx1) = sum u1 dy / unx, dy the caller's row height (stored: the column
+  // width dxs xwidth[i] when the grid is stored transposed)
+  D.dA_over_Lx = (c->tr ? c->dxs : c->dys) / c->unx;
+  D.xwidth = c->d_xwidth;
   D.delta = delta;
   D.force = P.force;
   D.alpha = c->alpha;
@@ -1081,7 +1126,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   if (!c->a_graph) {
     Schedule sc;
     std::string why;
-    if (!resolve_schedule(c->nx, c->sched_kind, c->sched_v, &sc, &why, c->alpha < 1.0 || c->top_u != 0.0)) return fail(c, DVM_EINVAL, why);
+    if (!resolve_schedule(c->nx, c->sched_kind, c->sched_v, &sc, &why, needs_special(c))) return fail(c, DVM_EINVAL, why);
     const bool cols = sc.kind == DVM_SWEEP_COLUMNS;
     const int parts = cols ? cols_parts(c->fp64, sc.v) : 1;
     std::vector<int> amap;
@@ -1128,6 +1173,7 @@ dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta
   if (!c->d_h) return fail(c, DVM_ESTATE, "dvm_adjoint needs the forward distribution (store_distribution = 1)");
   if (c->alpha < 1.0 || c->top_u != 0.0)
     return fail(c, DVM_EINVAL, "dvm_adjoint supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)");
+  if (!c->square) return fail(c, DVM_EINVAL, "dvm_adjoint supports square cells only (no dx1, no row heights)");
   DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
   if (c->h_state->iter < 1) return fail(c, DVM_ESTATE, "dvm_adjoint needs a forward solve first");
@@ -1229,7 +1275,7 @@ dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column) {
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (threads_per_column < 0 || !resolve_schedule(ctx->nx, kind, threads_per_column, &sc, &why, ctx->alpha < 1.0 || ctx->top_u != 0.0))
+  if (threads_per_column < 0 || !resolve_schedule(ctx->nx, kind, threads_per_column, &sc, &why, needs_special(ctx)))
     return fail(ctx, DVM_EINVAL, why.empty() ? "bad threads_per_column" : why);
   ctx->sched_kind = sc.kind;
   ctx->sched_v = sc.v;
@@ -1249,7 +1295,7 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, ctx->alpha < 1.0 || ctx->top_u != 0.0))
+  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, needs_special(ctx)))
     return fail(const_cast<dvm_ctx *>(ctx), DVM_EINVAL, why);
   if (kind) *kind = sc.kind;
   if (threads_per_column) *threads_per_column = (sc.kind == DVM_SWEEP_ROWS && sc.v == 0) ? ctx->cw : sc.v;
@@ -1262,7 +1308,7 @@ dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_co
   bool spec = false;
   for (dvm_ctx *c : batch->ctxs) {
     nx_max = std::max(nx_max, c->nx);
-    spec = spec || c->alpha < 1.0 || c->top_u != 0.0;
+    spec = spec || needs_special(c);
   }
   Schedule sc;
   std::string why;
@@ -1286,7 +1332,7 @@ dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *thre
   bool spec = false;
   for (dvm_ctx *c : batch->ctxs) {
     nx_max = std::max(nx_max, c->nx);
-    spec = spec || c->alpha < 1.0 || c->top_u != 0.0;
+    spec = spec || needs_special(c);
   }
   std::vector<Schedule> cands;
   {

@@ -80,7 +80,7 @@ __host__ __device__ inline float class_a2(int cls) { return cls == kFull ? -0.5f
 
 // Per-lane velocity table fields ([group][field][lane], in the sweep precision).
 enum : int {
-  kV1 = 0, kV2, kE2m1, kCx, kCy,   // v1, v2, |v|^2 - 1, |v1|/dx, |v2|/dx
+  kV1 = 0, kV2, kE2m1, kCx, kCy,   // v1, v2, |v|^2 - 1, |v1|/dx, |v2|/dy
   kW0, kW1, kW2, kW3,              // W, W v1, W v2, W |v|^2 (moment weights; W = 0 on padded lanes)
   kWnx, kWny,                      // |v1| W, |v2| W (incident wall flux weights)
   kZ0, kZ1, kZ2, kZ3,              // 1, v1, v2, |v|^2 (adjoint moments; 0 on padded lanes)
@@ -122,8 +122,10 @@ struct InstanceDesc {
   int fp32;             // 1 = FP32 storage (enables the noise-floor exit of the stopping test)
   int flow_axis;        // 0: the force, the moving plate's drift, Q and the stopping test are along x1;
                         // 1: along x2 (the caller's grid stored transposed: its x1 is this grid's x2)
-  double dx;            // cell size
-  double dA_over_Lx;    // dx^2 / (length of the grid along the flow axis)
+  double dx;            // cell size along x (the mean column width when columns differ)
+  double dy;            // cell size along y
+  double dA_over_Lx;    // cell area / length of the grid along the flow axis (times xwidth[i] if set)
+  const double *xwidth; // [nx] column widths / dx, or nullptr (equal columns)
   double delta;         // uniform collision rate
   double force;         // F
   double alpha;         // accommodation: wall value alpha rho_w + (1 - alpha) h(mirror v), Eq. (diffuse2)

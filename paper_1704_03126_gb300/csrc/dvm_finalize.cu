@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
       const double uf = D->flow_axis ? u2 : u1;  // velocity along the flow
       du = fabs(uf - D->u1prev[cell]);
       ua = fabs(uf);
-      uq = uf;
+      uq = D->xwidth ? uf * D->xwidth[cell % D->nx] : uf;  // area-weighted for unequal columns
       D->u1prev[cell] = uf;
       if (!isfinite(rho) || !isfinite(u1) || !isfinite(u2) || !isfinite(tau)) bad = 1.0;
     }

@@ -63,7 +63,7 @@ struct ColsG {
 };
 
 // per-pair constant fields in shared memory ([VB / 2][kCstFields] pairs): v1, v2, |v|^2 - 1, |v1|/dx,
-// |v2|/dx, the moment weight w (W forward, 1 on real lanes for the adjoint), the adjoint's W, and
+// |v2|/dy, the moment weight w (W forward, 1 on real lanes for the adjoint), the adjoint's W, and
 // the products w v1, w v2, w (|v|^2 - 1) that let FP64 accumulate each moment with one FMA
 enum : int { kCV1 = 0, kCV2, kCE, kCCx, kCCy, kCWm, kCWr, kCWv1, kCWv2, kCWe, kCPad0, kCPad1, kCstFields };
 static_assert(kCstFields == kColsCstFields, "shared-memory layout");
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   __syncthreads();
 
   const T sshift = ADJ ? T(0) : static_cast<T>(st->s);
-  const T dx = static_cast<T>(D->dx);
+  const T dx = static_cast<T>(D->dx), dy = static_cast<T>(D->dy);
   const SweepRec<T> *__restrict__ rec = static_cast<const SweepRec<T> *>(D->rec) + (size_t)quad * ncell;
   T *seamx = static_cast<T *>(D->seam_x) + (size_t)g * ny * 2 * kLanes + l0;
   T *seamy = static_cast<T *>(D->seam_y) + (size_t)g * nx * 2 * kLanes + l0;
@@ -205,6 +205,27 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   // 2 U v1) adds 4 alpha U v1 to the y combination of the cells under it (forward only)
   const T top_term = static_cast<T>(4.0 * D->alpha * D->top_u);
   const T one_m_alpha2 = static_cast<T>(2.0 * (1.0 - D->alpha));
+  // Columns of unequal width (the caller's rows of Sec. II.A stored transposed; forward only).  The x
+  // stencil of this thread's column i is the derivative at its centre of the polynomial through the
+  // points the class uses, widths w relative to dx: upstream centre distances d1 = (w_i + w_u1)/2 and
+  // d2 = d1 + (w_u1 + w_u2)/2; interior kappa = 1/d1 + 1/d2 with weights d2/(d1 (d2 - d1)) on h(u1)
+  // and -d1/(d2 (d2 - d1)) on h(u2); first order kappa = weight = 1/d1; next to a wall (face at w_i/2)
+  // kappa = 2/w_i, the wall terms (2 alpha rho_w, the specular part, the plate's drift) times 1/w_i.
+  const bool nux = SPEC && !ADJ && D->xwidth != nullptr;
+  T nk_full = T(1.5), na1_full = T(2), na2_full = T(-0.5), nk_near = T(1), nwsc = T(1);
+  if (nux && p < nx) {
+    const int i = xneg ? nx - 1 - p : p, sgn = xneg ? -1 : 1;
+    // an upstream column beyond a closed x end belongs to a wall-class cell, whose stencil does not
+    // use it: read column i instead
+    auto col = [&](int c) { return (c >= 0 && c < nx) ? c : (px ? ((c % nx) + nx) % nx : i); };
+    const double w0 = D->xwidth[i], w1 = D->xwidth[col(i - sgn)], w2 = D->xwidth[col(i - 2 * sgn)];
+    const double d1 = 0.5 * (w0 + w1), d2 = d1 + 0.5 * (w1 + w2);
+    nk_full = static_cast<T>(1.0 / d1 + 1.0 / d2);
+    na1_full = static_cast<T>(d2 / (d1 * (d2 - d1)));
+    na2_full = static_cast<T>(-d1 / (d2 * (d2 - d1)));
+    nk_near = static_cast<T>(1.0 / d1);
+    nwsc = static_cast<T>(1.0 / w0);
+  }
   const int gi = g % D->groups_per_quadrant, gq = D->groups_per_quadrant;
   T *wbuf_wr = nullptr;
   const T *wbuf_rd = nullptr;
@@ -344,6 +365,22 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           xw = r.xw;
           yw = r.yw;
         }
+        T xsc = T(1);  // scale of the x wall terms (unequal columns)
+        if (nux && !(code & kSolid)) {
+          const int clx = (code >> kClsXShift) & 3;
+          if (clx == kFull) {
+            ax1 = na1_full;
+            ax2 = na2_full;
+          } else if (clx == kNear) {
+            ax1 = nk_near;
+            ax2 = T(0);
+          } else {
+            ax1 = T(0);
+            ax2 = T(0);
+            xsc = nwsc;
+            xw *= xsc;
+          }
+        }
         if (q == 0) {
           if (py) {
             const T *ys = ysr + (size_t)(v * ncol + p) * 2 * G;
@@ -395,7 +432,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
             const int slot = D->wall_slot[(size_t)cell * 4 + (xneg ? kE : kW)];
             if (slot >= 0) {  // always: every wall-class face has a slot
               load_vec(wbuf_rd + wface(slot, (quad >> 1) & 1), u1, sshift);
-              ax1 = one_m_alpha2;  // x combination 2 alpha rho_w + 2 (1 - alpha) h(mirror v)
+              ax1 = one_m_alpha2 * xsc;  // x combination 2 alpha rho_w + 2 (1 - alpha) h(mirror v)
             }
           }
           if (((code >> kClsYShift) & 3u) == (uint32_t)kWall) {
@@ -414,7 +451,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         T mwy = T(0), mwx = T(0);
         if constexpr (SPEC && !ADJ) {
           if (code & kTopWall) mwy = top_term;
-          if (code & kTopWallX) mwx = top_term;
+          if (code & kTopWallX) mwx = top_term * xsc;
         }
         const T2 smwy = Q::splat(mwy), smwx = Q::splat(mwx);
         const T2 sA = Q::splat(r.A), sB = Q::splat(r.B), sC = Q::splat(r.C), sD = Q::splat(r.D);
@@ -425,7 +462,8 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         T2 skx = zero2, sky = zero2, sdl = zero2;
         if (!UNIF) {
           const int clx = (code >> kClsXShift) & 3, cly = (code >> kClsYShift) & 3;
-          skx = Q::splat(clx == kFull ? T(1.5) : (clx == kNear ? T(1.0) : T(2.0)));
+          if (nux) skx = Q::splat(clx == kFull ? nk_full : (clx == kNear ? nk_near : T(2) * nwsc));
+          else skx = Q::splat(clx == kFull ? T(1.5) : (clx == kNear ? T(1.0) : T(2.0)));
           sky = Q::splat(cly == kFull ? T(1.5) : (cly == kNear ? T(1.0) : T(2.0)));
           sdl = Q::splat(T(r.delta));
         }
@@ -511,9 +549,10 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           fx += __shfl_xor_sync(0xffffffffu, fx, off);
           fy += __shfl_xor_sync(0xffffffffu, fy, off);
         }
-        const T scale = ADJ ? T(2) : dx;
-        if (v == 0 && fxf) red_add(&facc[(size_t)cell * 4 + sidex], static_cast<double>(fx * scale));
-        if (v == 0 && fyf) red_add(&facc[(size_t)cell * 4 + sidey], static_cast<double>(fy * scale));
+        // (|v_a|/d_a) W h summed, times d_a: the incident flux sum |v_a| W h
+        const T scx = ADJ ? T(2) : dx, scy = ADJ ? T(2) : dy;
+        if (v == 0 && fxf) red_add(&facc[(size_t)cell * 4 + sidex], static_cast<double>(fx * scx));
+        if (v == 0 && fyf) red_add(&facc[(size_t)cell * 4 + sidey], static_cast<double>(fy * scy));
         if (spec && fxf) {
           const int slot = D->wall_slot[(size_t)cell * 4 + sidex];
           if (slot >= 0) store_vec(wbuf_wr + wface(slot, (quad >> 1) & 1), hy2);

@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("quad", Quad), ("accommodation", ctypes.c_double), ("precision", ctypes.c_int),
         ("force", ctypes.c_double), ("store_distribution", ctypes.c_int), ("sweep_warps", ctypes.c_int),
         ("top_wall_u1", ctypes.c_double), ("storage", ctypes.c_int),
+        ("dx1", ctypes.c_double), ("row_heights", ctypes.c_void_p),
     ]
 
 
@@ -124,12 +125,14 @@ class Solver:
     walls reflect the rest specularly (column sweep only; no adjoint).  top_wall_u1: speed of the plate
     beyond the last row (Couette flow; column sweep only; no adjoint).  storage: "auto" (the library
     stores a grid wider than tall transposed, so that its sweeps walk the long axis), "as_given" or
-    "transposed"; arguments and results keep the [ny][nx] layout either way.
+    "transposed"; arguments and results keep the [ny][nx] layout either way.  dx1: x1 spacing (0 = square
+    cells ly / ny); row_heights: [ny] heights of the rows along x2 (ly becomes their sum; needs dx1 > 0,
+    runs on the column sweep, stored transposed; no adjoint).
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
                  precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
-                 schedule=None, accommodation=1.0, top_wall_u1=0.0, storage="auto"):
+                 schedule=None, accommodation=1.0, top_wall_u1=0.0, storage="auto", dx1=0.0, row_heights=None):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -153,6 +156,14 @@ class Solver:
         if storage not in STORAGE:
             raise ValueError(f"storage must be one of {sorted(STORAGE)}")
         p.storage = STORAGE[storage]
+        p.dx1 = float(dx1)
+        rows = None
+        if row_heights is not None:
+            rows = np.ascontiguousarray(row_heights, dtype=np.float64)
+            if rows.shape != (mask.shape[0],):
+                raise ValueError("row_heights must have one entry per row")
+            p.row_heights = rows.ctypes.data
+        self._row_heights = rows  # keeps the array that params points to alive
         p.store_distribution = int(bool(store_distribution))
         p.sweep_warps = int(sweep_warps)
         self.params = p

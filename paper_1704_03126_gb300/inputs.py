@@ -219,6 +219,29 @@ def couette_rough_mask(gap_cells: int = 100, aspect: float = 5.0, eps: float = 0
     return mask, ny * dx
 
 
+def couette_paper_grid(nx: int = 1500, band_rows: int = 60, rest_rows: int = 100, aspect: float = 5.0,
+                       eps: float = 0.02, D: float = 1.5, gamma: float = 1.5, n1: int = -4):
+    """The Couette channel of Sec. II on the paper's grid: nx equal columns over aspect * H, the rough
+    band min r <= x2 < max r split into band_rows equal rows and max r <= x2 <= H into rest_rows.
+
+    r is Eq. (WM) sampled at the column centres, truncated at the columns' Nyquist frequency, shifted
+    to zero mean (the bottom plate's mean position is x2 = 0, the top plate at x2 = H = 1) and scaled to
+    rms eps H.  A cell of the band is solid when its centre lies below r.  Returns (mask [ny][nx], row
+    heights [ny] bottom to top, dx1); the grid spans x2 from min r to 1.
+    """
+    dx1 = aspect / nx
+    x = (np.arange(nx) + 0.5) * dx1
+    n_max = int(math.floor(math.log(1.0 / (2.0 * dx1)) / math.log(gamma)))
+    r = wm_roughness(x, D, gamma, n1, n_max)
+    r -= r.mean()
+    r *= eps / math.sqrt(float(np.mean(r * r)))
+    lo, hi = float(r.min()), float(r.max())
+    dy = np.concatenate([np.full(band_rows, (hi - lo) / band_rows), np.full(rest_rows, (1.0 - hi) / rest_rows)])
+    yc = lo + np.cumsum(dy) - 0.5 * dy
+    mask = (yc[:, None] < r[None, :]).astype(np.uint8)
+    return mask, dy, dx1
+
+
 def couette_instance(kn: float, gap_cells: int = 100, aspect: float = 5.0, eps: float = 0.02, nv: int = 32,
                      rough: bool = True) -> Instance:
     """Couette flow of Sec. II: smooth top plate moving with U = 1 (in units of v_m), bottom plate at

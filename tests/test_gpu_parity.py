@@ -558,3 +558,111 @@ def test_permeability_curve_matches_oracle(precision):
     # slip adds flow: k_a exceeds k_inf and grows with Kn over this range
     assert all(r > 1.0 for r in res["k_a_over_k_inf"])
     assert res["k_a"][1] > res["k_a"][0]
+
+
+# ------------------------------------------------------------------ rows of unequal height (Sec. II.A grid)
+
+def _stretched_rows(ny, seed):
+    rng = inputs.SplitMix64(seed)
+    h = np.array([0.4 + 1.2 * rng.uniform() for _ in range(ny)])
+    return h / h.sum()
+
+
+def _notch(nx, ny):
+    m = np.zeros((ny, nx), np.uint8)
+    m[0:2, nx // 3] = 1
+    m[ny - 1, nx // 2: nx // 2 + 2] = 1
+    return m
+
+
+UNEQUAL_CASES = [
+    # name, mask, periodic_x, periodic_y, kn, quad, alpha, top_u
+    ("plates_gh8", np.zeros((18, 5), np.uint8), True, False, 0.3, ("gh", 8, 0.0), 1.0, 0.0),
+    ("notched_nc8", _notch(9, 14), True, False, 1.0, ("nc", 8, 4.0), 1.0, 0.0),
+    ("couette_notched_cubic8_a0.7", _notch(9, 14), True, False, 0.5, ("cubic", 8, 4.0), 0.7, 1.0),
+    ("periodic_rows_block_gh6", np.pad(np.ones((3, 3), np.uint8), 3), True, True, 1.0, ("gh", 6, 0.0), 1.0, 0.0),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("schedule", SCHEDULES[1:], ids=SCHED_IDS[1:])
+@pytest.mark.parametrize("case", UNEQUAL_CASES, ids=[c[0] for c in UNEQUAL_CASES])
+def test_unequal_rows_match_oracle(case, schedule, precision):
+    """Rows of seeded unequal heights (0.4 to 1.6 relative), x1 spacing 0.07: the library stores the
+    grid transposed, each column-sweep thread owning one of the caller's rows with its own stencil."""
+    name, mask, px, py, kn, quad, alpha, top_u = case
+    dy = _stretched_rows(mask.shape[0], 21)
+    force = 0.0 if top_u else 1.0
+    sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision=precision, schedule=schedule, accommodation=alpha,
+                     top_wall_u1=top_u, force=force, dx1=0.07, row_heights=dy)
+    assert sol.info()["transposed"]
+    sol.solve(tol=1e-12 if precision == "fp64" else 1e-6, max_iter=200000)
+    orc = oracle.solve(oracle.Problem.make(mask, px, py, dvm.kn_to_delta(kn), quad, alpha=alpha, force=force,
+                                           top_u=top_u, dy=dy, dx1=0.07), tol=1e-12, max_iter=200000)
+    assert orc["converged"]
+    _compare(sol, orc, mask, precision)
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES, ids=SCHED_IDS)
+def test_rectangular_cells_match_oracle(schedule):
+    """Equal rows of height ly / ny with a different x1 spacing: every kernel, either storage."""
+    mask = _notch(12, 10)
+    ny = mask.shape[0]
+    for storage in ("as_given", "transposed"):
+        sol = dvm.Solver(mask, True, False, kn=0.7, quad=("nc", 8, 4.0), precision="fp64", schedule=schedule,
+                         dx1=0.043, storage=storage)
+        sol.solve(tol=1e-12, max_iter=200000)
+        orc = oracle.solve(oracle.Problem.make(mask, True, False, dvm.kn_to_delta(0.7), ("nc", 8, 4.0),
+                                               dy=np.full(ny, 1.0 / ny), dx1=0.043), tol=1e-12, max_iter=200000)
+        _compare(sol, orc, mask, "fp64")
+
+
+def test_paper_grid_couette_matches_oracle():
+    """The Couette channel on the paper's kind of grid, reduced: 60 columns (aspect 5), 8 equal rows
+    across the WM band and 12 above it, cubic 8 x 8 velocities, Kn = 1, FP64 and FP32."""
+    mask, dy, dx1 = inputs.couette_paper_grid(60, 8, 12)
+    quad = ("cubic", 8, 4.0)
+    orc = oracle.solve(oracle.Problem.make(mask, True, False, dvm.kn_to_delta(1.0), quad, force=0.0, top_u=1.0,
+                                           dy=dy, dx1=dx1), tol=1e-12, max_iter=200000)
+    assert orc["converged"]
+    for precision in ("fp64", "fp32"):
+        sol = dvm.Solver(mask, True, False, kn=1.0, quad=quad, precision=precision, force=0.0, top_wall_u1=1.0,
+                         dx1=dx1, row_heights=dy)
+        sol.solve(tol=1e-12 if precision == "fp64" else 1e-6, max_iter=200000)
+        _compare(sol, orc, mask, precision)
+
+
+def test_paper_size_couette_grid_runs():
+    """1500 columns, 60 + 100 rows (the paper's grid), cubic 32 x 32, Kn = 1, FP32: the rough channel
+    converges with 0.9 < Q_r / Q_s < 1 against smooth plates of 100 equal rows at the same x1 spacing,
+    whose Q is U H m0 m2."""
+    quad = ("cubic", 32, 4.0)
+    x, w = oracle.quadrature("cubic", 32, 4.0)
+    m0m2 = float(w.sum() * (w * x * x).sum())
+    mask, dy, dx1 = inputs.couette_paper_grid()
+    rough = dvm.Solver(mask, True, False, kn=1.0, quad=quad, precision="fp32", force=0.0, top_wall_u1=1.0,
+                       dx1=dx1, row_heights=dy)
+    st, iters, est = rough.solve(tol=1e-6, max_iter=20000)
+    smooth = dvm.Solver(inputs.plates_mask(1500, 100), True, False, kn=1.0, quad=quad, precision="fp32", force=0.0,
+                        top_wall_u1=1.0, dx1=dx1)
+    smooth.solve(tol=1e-6, max_iter=20000)
+    q_s = smooth.flowrate()[0]
+    assert abs(q_s - m0m2) < 2e-5
+    assert 0.9 < rough.flowrate()[0] / q_s < 1.0
+
+
+def test_unequal_rows_restrictions():
+    dy = _stretched_rows(8, 2)
+    mask = np.zeros((8, 4), np.uint8)
+    with pytest.raises(dvm.DvmError) as ei:
+        dvm.Solver(mask, True, False, kn=1.0, quad=("gh", 4, 0.0), dx1=0.1, row_heights=dy, storage="as_given")
+    assert ei.value.status == dvm.DVM_EINVAL
+    sol = dvm.Solver(mask, True, False, kn=1.0, quad=("gh", 4, 0.0), dx1=0.1, row_heights=dy, store_distribution=True)
+    assert sol.schedule()[0] == "columns"
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.set_schedule("rows")
+    assert ei.value.status == dvm.DVM_EINVAL
+    sol.solve(tol=1e-10)
+    with pytest.raises(dvm.DvmError) as ei:
+        sol.adjoint()
+    assert ei.value.status == dvm.DVM_EINVAL

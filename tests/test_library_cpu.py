@@ -71,6 +71,10 @@ def test_library_rejects_invalid_grids():
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, accommodation=1.5),  # accommodation outside [0, 1]
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, accommodation=-0.1),
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, periodic_y=True, top_wall_u1=1.0),  # moving plate, periodic x2
+    dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, row_heights=np.full(4, 0.25)),      # row heights without dx1
+    dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, dx1=0.1, row_heights=np.array([0.3, 0.3, 0.0, 0.4])),
+    dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, dx1=0.1, row_heights=np.full(4, 0.25), storage="as_given"),
+    dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, dx1=-0.1),                           # negative x1 spacing
 ])
 def test_create_rejects_invalid_parameters(kwargs):
     with pytest.raises(dvm.DvmError) as ei:
