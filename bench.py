@@ -15,9 +15,10 @@ Other workloads, one JSON line each:
            compared with 64 plain solves.
   adjoint  porous 256 x 256 (porosity 0.5), cubic 32 x 32, Kn = 1, FP64: one step = one transposed
            (adjoint) sweep; gradient checked against central differences of forward solves.
-  couette  Couette flow of Sec. II: top plate moving with U = 1, no force, 500 columns (aspect 5,
-           dx = H / 100), bottom wall a Weierstrass-Mandelbrot staircase (D = 1.5, eps = 2 %) or smooth,
-           cubic 32 x 32 velocities, Kn = 0.1, 1, 10: six instances advanced together; reports
+  couette  Couette flow of Sec. II on the paper's grid: top plate moving with U = 1, no force, 1500
+           columns (aspect 5, dx1 = H / 300); bottom wall a Weierstrass-Mandelbrot staircase (D = 1.5,
+           eps = 2 %) resolved by 60 rows across its band and 100 above, or smooth (100 rows); cubic
+           32 x 32 velocities, Kn = 0.1, 1, 10: six instances advanced together; reports
            Q* = Q_rough / Q_smooth per Kn from the converged solves.
   permeability  Sec. III's curves: three synthetic media 256 x 256 (irregular, square and circular
            solids, porosity about 0.6, both axes periodic), cubic 32 x 32 velocities, Kn = 0.02 ... 2:
@@ -46,7 +47,6 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 KNS = (0.1, 1.0, 10.0)
-COUETTE_GAP = 100  # cells across the mean gap H of the Couette channels (500 columns at aspect 5)
 PERM_FIT_KNS = (0.005, 0.01, 0.02)  # k_inf is extrapolated to Kn = 0 from these (refined grid)
 PERM_KNS = (0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0)
 PERM_FIT_QUAD = ("gh", 12, 0.0)
@@ -57,8 +57,8 @@ METRICS = {
     "porous": "DVM cell-velocity updates/s (porous 256x256 phi 0.6, cubic 48x48 velocities, Kn 0.05/0.5/5)",
     "batched": "DVM cell-velocity updates/s (64 mixed instances, one batched launch per kernel)",
     "adjoint": "adjoint sweep cell-velocity updates/s (porous 256x256 phi 0.5, cubic 32x32, Kn 1, FP64)",
-    "couette": "DVM cell-velocity updates/s (Couette, WM-rough and smooth 500-column channels, cubic 32x32, "
-               "Kn 0.1/1/10)",
+    "couette": "DVM cell-velocity updates/s (Couette on the paper's grid, 1500 x (60+100) WM-rough and "
+               "1500 x 100 smooth, cubic 32x32, Kn 0.1/1/10)",
     "permeability": "DVM cell-velocity updates/s (3 porous media 256x256 x 7 Kn in 0.02-2, cubic 32x32)",
 }
 METRIC = METRICS["rough"]
@@ -100,9 +100,10 @@ WORKLOAD_TEXT = {
                "velocities; one launch per kernel per sweep",
     "adjoint": "periodic disk medium 256x256 (porosity 0.5, seed 1), cubic 32x32 velocities, Kn 1, FP64; "
                "transposed sweeps of the adjoint iteration at the converged forward state",
-    "couette": "Couette flow, top plate U = 1, no force, x1 periodic, 500 columns (aspect 5, dx = H/100): "
+    "couette": "Couette flow, top plate U = 1, no force, x1 periodic, 1500 columns (aspect 5, dx1 = H/300): "
                "Weierstrass-Mandelbrot staircase bottom (D 1.5, gamma 1.5, n1 -4, eps 2%, truncated at the "
-               "grid Nyquist frequency) and smooth plates, cubic 32x32 velocities |v|<=4, Kn 0.1/1/10 batched",
+               "grid Nyquist frequency, zero mean) on 60 rows across its band + 100 rows above, and smooth "
+               "plates on 100 rows; cubic 32x32 velocities |v|<=4, Kn 0.1/1/10 batched",
     "permeability": "three seeded periodic media 256x256, porosity about 0.6 (irregular: thresholded "
                     "Gaussian-filtered noise, width 20 cells; squares: sides 32-80; disks: radii 20-48), cubic "
                     "32x32 velocities |v|<=4, Kn 0.02/0.05/0.1/0.2/0.5/1/2, force-driven (F=1); 21 instances "
@@ -139,7 +140,7 @@ def instances(workload="rough"):
                                 {"porosity": masks[kind][1], "medium": kind})
                 for kind in inputs.MEDIA for kn in PERM_KNS]
         elif workload == "couette":
-            _INSTANCES[workload] = [inputs.couette_instance(kn, gap_cells=COUETTE_GAP, rough=rough)
+            _INSTANCES[workload] = [inputs.couette_instance(kn, rough=rough, grid="paper")
                                     for rough in (True, False) for kn in KNS]
         else:
             _INSTANCES[workload] = [inputs.porous_instance(1.0, nv=32, porosity=0.5, seed=1)]
@@ -147,9 +148,12 @@ def instances(workload="rough"):
 
 
 def drive(inst):
-    """Grid height, body force and top-plate speed of an instance (force-driven flow unless it says)."""
+    """Grid, body force and top-plate speed of an instance (square cells, force-driven flow unless it
+    says otherwise)."""
     x = inst.extra
-    return {"ly": float(x.get("ly", 1.0)), "force": float(x.get("force", 1.0)), "top_wall_u1": float(x.get("top_u", 0.0))}
+    return {"ly": float(x.get("ly", 1.0)), "force": float(x.get("force", 1.0)),
+            "top_wall_u1": float(x.get("top_u", 0.0)), "dx1": float(x.get("dx1", 0.0)),
+            "row_heights": x.get("row_heights")}
 
 
 def solver(dvm, inst, precision, stream):
@@ -159,8 +163,12 @@ def solver(dvm, inst, precision, stream):
 
 def oracle_problem(oracle, inst):
     d = drive(inst)
+    rows = d["row_heights"]
+    if rows is None and d["dx1"] > 0.0:
+        rows = np.full(inst.mask.shape[0], d["ly"] / inst.mask.shape[0])
     return oracle.Problem.make(inst.mask, inst.periodic_x, inst.periodic_y, oracle.delta_from_kn(inst.kn), inst.quad,
-                               force=d["force"], ly=d["ly"], top_u=d["top_wall_u1"])
+                               force=d["force"], ly=d["ly"], top_u=d["top_wall_u1"], dy=rows,
+                               dx1=d["dx1"] if rows is not None else None)
 
 
 def apply_schedule(batch, spec):

@@ -243,9 +243,23 @@ def couette_paper_grid(nx: int = 1500, band_rows: int = 60, rest_rows: int = 100
 
 
 def couette_instance(kn: float, gap_cells: int = 100, aspect: float = 5.0, eps: float = 0.02, nv: int = 32,
-                     rough: bool = True) -> Instance:
+                     rough: bool = True, grid: str = "square") -> Instance:
     """Couette flow of Sec. II: smooth top plate moving with U = 1 (in units of v_m), bottom plate at
-    rest, rough (WM staircase) or smooth, x1 periodic, no body force; cubic nv x nv velocities."""
+    rest, rough (WM staircase) or smooth, x1 periodic, no body force; cubic nv x nv velocities.
+
+    grid "square": square cells, gap_cells across the mean gap.  grid "paper": the paper's grid, 1500
+    columns and 60 + 100 rows (couette_paper_grid) for the rough channel, 1500 x 100 equal rows for
+    the smooth one (x1 spacing H / 300)."""
+    if grid == "paper":
+        nx = 1500
+        if rough:
+            mask, dy, dx1 = couette_paper_grid(nx, 60, 100, aspect, eps)
+        else:
+            mask, dy, dx1 = plates_mask(nx, 100), np.full(100, 0.01), aspect / nx
+        name = f"couette{'_wm' if rough else '_smooth'}{nx}x{mask.shape[0]}_paper_cubic{nv}_kn{kn:g}"
+        return Instance(name, mask, True, False, kn, ("cubic", nv, 4.0),
+                        {"ly": float(dy.sum()), "top_u": 1.0, "force": 0.0, "eps": eps if rough else 0.0,
+                         "dx1": dx1, "row_heights": dy})
     if rough:
         mask, ly = couette_rough_mask(gap_cells, aspect, eps)
     else:
