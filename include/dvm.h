@@ -109,6 +109,13 @@ typedef struct {
                                  points (exact on linear fields, like the equal-row forms).  Needs the
                                  transposed storage (DVM_STORAGE_AS_GIVEN gives DVM_EINVAL) and runs on
                                  the column sweep only; no adjoint.  The adjoint needs square cells. */
+  int anderson_depth;         /* 0 = plain source iteration (Eq. iteration, the paper's).  1..8: Anderson
+                                 mixing of that depth (Walker & Ni 2011, type II) of the projected state
+                                 the sweeps start from -- moments, wall-face fluxes, periodic seam values,
+                                 the mass shift -- three more kernels per sweep; same fixed point, far
+                                 fewer sweeps where the plain iteration converges slowly (small Kn).
+                                 Needs accommodation = 1.  Extra memory (2 depth + 3) doubles per state
+                                 element (8 per cell plus the seams). */
 } dvm_params;
 
 /* The transport sweep kernel (both compute the same update; see dvm_set_schedule; nx below is the

@@ -33,6 +33,13 @@ struct dvm_ctx {
   bool square = true;              // square cells (the adjoint's case)
   bool nux = false;                // stored x spacing varies by column (the caller's unequal rows)
   double *d_xwidth = nullptr;      // nux: stored column widths / dxs
+  // Anderson mixing (dvm_params.anderson_depth > 0): the device descriptor and its buffers
+  int aa_m = 0;
+  long long aa_n = 0;
+  AndersonDesc *d_aa = nullptr;
+  double *d_aa_buf = nullptr;      // x, fp, gp [n] | dF, dG [m][n] | red [kAARed] | gram [m][m] | gamma [m]
+  int *d_aa_meta = nullptr;
+  unsigned char *d_wallface = nullptr;
   bool fp64 = true, store_h = false, uniform = true;
   double delta = 0.0, kn = 0.0;
   std::vector<double> x1, w1;
@@ -84,6 +91,7 @@ struct dvm_batch {
   cudaGraphExec_t g_sweep = nullptr; // one sweep kernel (timed single sweeps)
   cudaGraphExec_t g_fin = nullptr;   // the two finalize kernels of that sweep
   int m = 1;
+  bool anderson = false;             // some member mixes its iterates (3 more kernels per sweep)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timed = false;
 };
@@ -292,6 +300,10 @@ void release_device(dvm_ctx *c) {
   free_dev(c->d_wall_slot);
   free_dev(c->d_wbuf);
   free_dev(c->d_xwidth);
+  free_dev(c->d_aa);
+  free_dev(c->d_aa_buf);
+  free_dev(c->d_aa_meta);
+  free_dev(c->d_wallface);
   if (c->h_state) cudaFreeHost(c->h_state);
   c->h_state = nullptr;
   if (c->a_graph) cudaGraphExecDestroy(c->a_graph);
@@ -321,6 +333,13 @@ dvm_status reset_state(dvm_ctx *c) {
   if (c->d_h) DVM_CUDA(c, cudaMemsetAsync(c->d_h, 0, ts * c->ngroups * (size_t)c->ncell * kLanes, c->stream));
   if (c->d_wbuf)
     DVM_CUDA(c, cudaMemsetAsync(c->d_wbuf, 0, ts * 2 * (size_t)std::max(c->nwall, 1) * 2 * c->gq * kLanes, c->stream));
+  if (c->d_aa) {
+    // the mixing restarts from the state of h = 0 (x = 0) with an empty history
+    DVM_CUDA(c, cudaMemsetAsync(c->d_aa_buf, 0, sizeof(double) * (size_t)c->aa_n, c->stream));
+    DVM_CUDA(c, cudaMemsetAsync(c->d_aa_buf + (size_t)(3 + 2 * c->aa_m) * c->aa_n, 0, sizeof(double) * kAARed,
+                                c->stream));
+    DVM_CUDA(c, cudaMemsetAsync(c->d_aa_meta, 0, sizeof(int) * 3, c->stream));
+  }
   DVM_CUDA(c, launch_reset(c->d_desc, c->ncell, c->fp64, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
   return DVM_OK;
@@ -345,6 +364,8 @@ LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const in
   L.ninst = ninst;
   L.warps = warps;
   L.cw = cw;
+  L.anderson = 0;
+  L.aa_blocks = 0;
   return L;
 }
 
@@ -486,6 +507,14 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
 #undef BATCH_CUDA
   LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw, b->cols_v, spec);
+  {
+    long long aa_max = 0;
+    for (int i = 0; i < n; ++i) aa_max = std::max(aa_max, ctxs[i]->aa_n);
+    b->anderson = aa_max > 0;
+    L.anderson = b->anderson ? 1 : 0;
+    // about 8 elements per thread, at most 1024 blocks per instance
+    L.aa_blocks = (int)std::min<long long>(1024, std::max<long long>(1, (aa_max + 2047) / 2048));
+  }
   b->m = iters_per_graph(upd);
   dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->uniform, b->m, true, true,
                                 &b->g_many);
@@ -676,6 +705,10 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   if (P.storage != DVM_STORAGE_AUTO && P.storage != DVM_STORAGE_AS_GIVEN && P.storage != DVM_STORAGE_TRANSPOSED)
     return fail(nullptr, DVM_EINVAL, "storage must be DVM_STORAGE_AUTO, _AS_GIVEN or _TRANSPOSED");
   if (!(P.dx1 >= 0.0) || !std::isfinite(P.dx1)) return fail(nullptr, DVM_EINVAL, "dx1 must be finite and >= 0");
+  if (P.anderson_depth < 0 || P.anderson_depth > kAAMaxDepth)
+    return fail(nullptr, DVM_EINVAL, "anderson_depth must be 0.." + std::to_string(kAAMaxDepth));
+  if (P.anderson_depth > 0 && P.accommodation < 1.0)
+    return fail(nullptr, DVM_EINVAL, "Anderson mixing needs fully diffuse walls (accommodation = 1)");
   double ly = P.ly;
   if (P.row_heights) {
     if (!(P.dx1 > 0.0)) return fail(nullptr, DVM_EINVAL, "row heights need the x1 spacing dx1 > 0");
@@ -852,6 +885,41 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
     CREATE_CUDA(cudaMemset(c->d_wbuf, 0, wbytes));
   }
 
+  if (P.anderson_depth > 0) {
+    AndersonDesc A{};
+    A.m = c->aa_m = P.anderson_depth;
+    A.n_mom = 4 * (long long)ncell;
+    A.n_wall = 4 * (long long)ncell;
+    const bool spx = c->tr ? P.periodic_y : P.periodic_x, spy = c->tr ? P.periodic_x : P.periodic_y;
+    A.n_sx = spx ? (long long)c->ngroups * c->ny * 2 * kLanes : 0;
+    A.n_sy = spy ? (long long)c->ngroups * c->nx * 2 * kLanes : 0;
+    A.n = c->aa_n = A.n_mom + A.n_wall + A.n_sx + A.n_sy + 1;
+    const size_t nbuf = (size_t)(3 + 2 * A.m) * A.n + kAARed + (size_t)A.m * A.m + A.m;
+    CREATE_CUDA(cudaMalloc(&c->d_aa_buf, sizeof(double) * nbuf));
+    CREATE_CUDA(cudaMemset(c->d_aa_buf, 0, sizeof(double) * nbuf));
+    CREATE_CUDA(cudaMalloc(&c->d_aa_meta, sizeof(int) * 3));
+    CREATE_CUDA(cudaMemset(c->d_aa_meta, 0, sizeof(int) * 3));
+    std::vector<unsigned char> wf(ncell * 4, 0);
+    for (size_t k = 0; k < c->geo.hw_src.size(); ++k)
+      if (c->geo.hw_src[k] >= 0) wf[c->geo.hw_src[k]] = 1;
+    CREATE_CUDA(cudaMalloc(&c->d_wallface, ncell * 4));
+    CREATE_CUDA(cudaMemcpy(c->d_wallface, wf.data(), ncell * 4, cudaMemcpyHostToDevice));
+    double *b = c->d_aa_buf;
+    A.x = b;
+    A.fp = b + A.n;
+    A.gp = b + 2 * A.n;
+    A.dF = b + 3 * A.n;
+    A.dG = b + (size_t)(3 + A.m) * A.n;
+    A.red = b + (size_t)(3 + 2 * A.m) * A.n;
+    A.gram = A.red + kAARed;
+    A.flow_comp = c->tr ? 2 : 1;
+    A.gamma = A.gram + A.m * A.m;
+    A.meta = c->d_aa_meta;
+    A.wallface = c->d_wallface;
+    CREATE_CUDA(cudaMalloc(&c->d_aa, sizeof(AndersonDesc)));
+    CREATE_CUDA(cudaMemcpy(c->d_aa, &A, sizeof(AndersonDesc), cudaMemcpyHostToDevice));
+  }
+
   if (c->nux) {
     // stored column i is the caller's row i: its width relative to the mean row height
     std::vector<double> w(c->nx);
@@ -888,6 +956,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   // width dxs xwidth[i] when the grid is stored transposed)
   D.dA_over_Lx = (c->tr ? c->dxs : c->dys) / c->unx;
   D.xwidth = c->d_xwidth;
+  D.aa = c->d_aa;
   D.delta = delta;
   D.force = P.force;
   D.alpha = c->alpha;
@@ -1114,6 +1183,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   A.mom_fwd = c->d_mom;
   A.state_fwd = c->d_state;
   A.grad = c->a_grad;
+  A.aa = nullptr;  // the adjoint iteration is not mixed
   DVM_CUDA(c, cudaMemcpyAsync(c->a_desc, &A, sizeof(InstanceDesc), cudaMemcpyHostToDevice, c->stream));
   DVM_CUDA(c, cudaMemsetAsync(c->a_acc, 0, sizeof(double) * 4 * ncell, c->stream));
   DVM_CUDA(c, cudaMemsetAsync(c->a_flux, 0, sizeof(double) * 8 * ncell, c->stream));
@@ -1269,7 +1339,7 @@ dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *fina
   return DVM_OK;
 }
 
-int dvm_batch_kernels_per_sweep(const dvm_batch *batch) { return batch ? 3 : 0; }
+int dvm_batch_kernels_per_sweep(const dvm_batch *batch) { return batch ? (batch->anderson ? 6 : 3) : 0; }
 
 dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column) {
   if (!ctx) return DVM_EINVAL;

@@ -110,6 +110,32 @@ struct DeviceState {
   double mu;       // bordering multiplier of the transposed system
   double kappa;    // (mu - sum lambda) / (n_gas sum W), added to the next right-hand side
   double lam_acc, dz_acc, seam_acc;
+  // Anderson mixing only: the stopping test uses the plain residual f = G(x) - x at the mixed iterate
+  double aa_res;       // |f| / |g| over the flow velocity of the gas cells (L2)
+  double aa_rho;       // running estimate of the plain contraction, max |dG| / |dx| over the differences
+  double aa_est;       // aa_res / (1 - aa_rho): the distance to the fixed point
+  double aa_res_min;   // smallest aa_res since the solve was armed
+  int aa_iter_min;     // sweep of that minimum
+};
+
+// Anderson mixing of the source iteration (dvm_anderson.cu), one per instance that uses it.  The
+// state vector is [moments 4 ncell | wall-face fluxes 4 ncell | x seam | y seam | c].
+constexpr int kAAMaxDepth = 8;
+// reduction slots: dF_new . dF_j [kAAMaxDepth], dF_j . f [kAAMaxDepth], then over the flow velocity
+// |f|^2, |g|^2, |dG_new|^2, |dG_new - dF_new|^2
+constexpr int kAARed = 2 * kAAMaxDepth + 4;
+struct AndersonDesc {
+  int m;                          // depth: differences kept (1..kAAMaxDepth)
+  long long n_mom, n_wall, n_sx, n_sy, n;  // segment lengths (seams 0 on closed axes) and the total
+  const unsigned char *wallface;  // [4 ncell] 1 where (cell, side) is a wall face
+  double *x;                      // [n] the state the running sweep started from
+  double *fp, *gp;                // [n] f = g - x and g of the latest iteration
+  double *dF, *dG;                // [m][n] differences of consecutive f and g (a ring)
+  double *red;                    // [kAARed] reduction slots
+  double *gram;                   // [m][m] dF_i . dF_j
+  double *gamma;                  // [m] mixing coefficients
+  int *meta;                      // [3] columns held, next ring slot, iterations gathered
+  int flow_comp;                  // moment index of the flow velocity (1: u1, 2: u2 when stored transposed)
 };
 
 struct InstanceDesc {
@@ -159,6 +185,7 @@ struct InstanceDesc {
   const double *mom_fwd;       // forward moments [ncell][4]
   const DeviceState *state_fwd;
   double *grad;                // [ncell] dQ / d delta_c
+  AndersonDesc *aa;            // Anderson mixing state (device), or nullptr: plain source iteration
 };
 
 // Launch descriptor shared by the kernels of one (possibly batched) iteration.
@@ -172,6 +199,8 @@ struct LaunchDesc {
   int cols_v;                // 0: row-wavefront sweep; 1, 2, 4: column sweep with that many threads per
                              // column (the block's velocity set is split among them)
   int specular;              // 1: some instance has accommodation < 1 or a moving plate (column sweep only)
+  int anderson;              // 1: some instance mixes its iterates (dvm_anderson.cu)
+  int aa_blocks;             // blocks per instance of the mixing kernels
 };
 
 #ifdef __CUDACC__

@@ -197,24 +197,30 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
       st->eps_ring[n & 3] = eps;
       double est = INFINITY;
       int done = 0, status = 0;
-      if (n >= 5) {
-        double r = back > 0.0 ? pow(eps / back, 0.25) : 0.0;
-        if (r > 0.9999) r = 0.9999;
-        est = eps / (1.0 - r);
-        if (est < st->tol) {
-          done = 1;
-          status = 0;
+      if (D->aa) {
+        // mixed iterates: the estimate from the plain residual (dvm_anderson.cu), and the same FP32
+        // noise-floor exit on that residual
+        est = st->aa_est;
+        if (n >= 5 && est < st->tol) done = 1;
+        if (st->aa_res < st->aa_res_min) {
+          st->aa_res_min = st->aa_res;
+          st->aa_iter_min = n;
         }
-      }
-      // With FP32 storage the change per sweep stalls at the rounding noise floor, where the rate
-      // estimate says nothing: below tol, 16 sweeps without a new smallest eps also end the iteration.
-      if (eps < st->eps_min) {
-        st->eps_min = eps;
-        st->iter_min = n;
-      }
-      if (!done && D->fp32 && n >= 5 && eps < st->tol && n - st->iter_min >= 16) {
-        done = 1;
-        status = 0;
+        if (!done && D->fp32 && n >= 5 && st->aa_res < st->tol && n - st->aa_iter_min >= 16) done = 1;
+      } else {
+        if (n >= 5) {
+          double r = back > 0.0 ? pow(eps / back, 0.25) : 0.0;
+          if (r > 0.9999) r = 0.9999;
+          est = eps / (1.0 - r);
+          if (est < st->tol) done = 1;
+        }
+        // With FP32 storage the change per sweep stalls at the rounding noise floor, where the rate
+        // estimate says nothing: below tol, 16 sweeps without a new smallest eps also end the iteration.
+        if (eps < st->eps_min) {
+          st->eps_min = eps;
+          st->iter_min = n;
+        }
+        if (!done && D->fp32 && n >= 5 && eps < st->tol && n - st->iter_min >= 16) done = 1;
       }
       if (!done && n >= st->max_iter) {
         done = 1;
@@ -279,6 +285,9 @@ __global__ void reset_kernel(const InstanceDesc *D) {
     st->eps_min = INFINITY;
     st->iter_min = 0;
     st->mass_acc = st->du_acc = st->u_acc = st->q_acc = 0.0;
+    st->aa_res = st->aa_est = st->aa_res_min = INFINITY;
+    st->aa_rho = 0.0;
+    st->aa_iter_min = 0;
   }
 }
 
@@ -286,6 +295,8 @@ __global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
   st->tol = tol;
   st->eps_min = INFINITY;
   st->iter_min = st->iter;
+  st->aa_res_min = INFINITY;
+  st->aa_iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;
@@ -305,6 +316,8 @@ __global__ void arm_all_kernel(const InstanceDesc *descs, int n, double tol, int
   st->tol = tol;
   st->eps_min = INFINITY;
   st->iter_min = st->iter;
+  st->aa_res_min = INFINITY;
+  st->aa_iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;
@@ -324,6 +337,10 @@ cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStr
   fin1_kernel<<<nblocks, kFinBlock, 0, stream>>>(L);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (L.anderson) {
+    e = launch_anderson(L, fp64, stream);
+    if (e != cudaSuccess) return e;
+  }
   if (fp64)
     fin2_kernel<double><<<nblocks, kFinBlock, 0, stream>>>(L);
   else

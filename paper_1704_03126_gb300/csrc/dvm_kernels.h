@@ -94,8 +94,10 @@ cudaError_t launch_adjoint_finalize(const LaunchDesc &L, int fin_blocks, int sea
 cudaError_t launch_adjoint_reset(const InstanceDesc *adj_dev, int ncell, bool fp64, cudaStream_t stream);
 cudaError_t launch_adjoint_gradient(const InstanceDesc *adj_dev, int ncell, bool fp64, cudaStream_t stream);
 
-// Finalize: mean-density projection, moments, residual, flow rate, next sweep records.
+// Finalize: mean-density projection, (Anderson mixing,) moments, residual, flow rate, next sweep records.
 cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream);
+// Anderson mixing between the projection and the record writer (instances with a mixing state).
+cudaError_t launch_anderson(const LaunchDesc &L, bool fp64, cudaStream_t stream);
 // Reset an instance to h = 0 (records, accumulators and state; arrays are cleared by the caller).
 cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
 // Arm every instance of a launch for `count` more sweeps (device-relative; one launch).

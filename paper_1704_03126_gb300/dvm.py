@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
         ("quad", Quad), ("accommodation", ctypes.c_double), ("precision", ctypes.c_int),
         ("force", ctypes.c_double), ("store_distribution", ctypes.c_int), ("sweep_warps", ctypes.c_int),
         ("top_wall_u1", ctypes.c_double), ("storage", ctypes.c_int),
-        ("dx1", ctypes.c_double), ("row_heights", ctypes.c_void_p),
+        ("dx1", ctypes.c_double), ("row_heights", ctypes.c_void_p), ("anderson_depth", ctypes.c_int),
     ]
 
 
@@ -127,12 +127,14 @@ class Solver:
     stores a grid wider than tall transposed, so that its sweeps walk the long axis), "as_given" or
     "transposed"; arguments and results keep the [ny][nx] layout either way.  dx1: x1 spacing (0 = square
     cells ly / ny); row_heights: [ny] heights of the rows along x2 (ly becomes their sum; needs dx1 > 0,
-    runs on the column sweep, stored transposed; no adjoint).
+    runs on the column sweep, stored transposed; no adjoint).  anderson: depth of the Anderson mixing of
+    the source iteration (0 = plain; 1..8; accommodation 1 only).
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
                  precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
-                 schedule=None, accommodation=1.0, top_wall_u1=0.0, storage="auto", dx1=0.0, row_heights=None):
+                 schedule=None, accommodation=1.0, top_wall_u1=0.0, storage="auto", dx1=0.0, row_heights=None,
+                 anderson=0):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -157,6 +159,7 @@ class Solver:
             raise ValueError(f"storage must be one of {sorted(STORAGE)}")
         p.storage = STORAGE[storage]
         p.dx1 = float(dx1)
+        p.anderson_depth = int(anderson)
         rows = None
         if row_heights is not None:
             rows = np.ascontiguousarray(row_heights, dtype=np.float64)
