@@ -51,6 +51,7 @@ PERM_FIT_KNS = (0.005, 0.01, 0.02)  # k_inf is extrapolated to Kn = 0 from these
 PERM_KNS = (0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0)
 PERM_FIT_QUAD = ("gh", 12, 0.0)
 PERM_FIT_REFINE = 2
+ANDERSON_DEPTH = 6  # depth of the mixed iteration reported beside the plain one (time to converge)
 POROUS_KNS = (0.05, 0.5, 5.0)
 METRICS = {
     "rough": "DVM cell-velocity updates/s (rough channel 128x128, 32x32 velocities, Kn 0.1/1/10)",
@@ -156,9 +157,9 @@ def drive(inst):
             "row_heights": x.get("row_heights")}
 
 
-def solver(dvm, inst, precision, stream):
+def solver(dvm, inst, precision, stream, anderson=0):
     return dvm.Solver(inst.mask, inst.periodic_x, inst.periodic_y, kn=inst.kn, quad=inst.quad,
-                      precision=precision, stream=stream, **drive(inst))
+                      precision=precision, stream=stream, anderson=anderson, **drive(inst))
 
 
 def oracle_problem(oracle, inst):
@@ -375,7 +376,8 @@ def run_ours(args, rank, world, local_rank):
         if args.workload == "permeability":
             out["curves"] = curves(results, insts, torch)
         else:
-            out["converge"] = converge(results, insts, torch, max_iter=10000 if big else 200000)
+            out["converge"] = converge(results, insts, torch, max_iter=10000 if big else 200000, dvm=dvm,
+                                       stream=stream.cuda_stream)
     if rank == 0 and not args.skip_extras:
         out["cpu_baseline"] = cpu_baseline(insts, args.workload)
     for r in results.values():
@@ -409,9 +411,10 @@ def e2e(args, insts, stream, dvm, torch, sweeps=50, reps=3):
                     f"dvm_destroy; {reps} repetitions"}
 
 
-def converge(results, insts, torch, max_iter=200000):
+def converge(results, insts, torch, max_iter=200000, dvm=None, stream=None):
     """Time to converge: each instance alone (plain, automatic sweep kernel) vs all of them batched
-    (the timed launch), from h = 0, to the same tolerance."""
+    (the timed launch), from h = 0, to the same tolerance; for up to six instances also the batch with
+    mixed iterates (Anderson depth ANDERSON_DEPTH)."""
     out = {}
     for prec, r in results.items():
         t = 1e-10 if prec == "fp64" else 1e-6
@@ -437,6 +440,22 @@ def converge(results, insts, torch, max_iter=200000):
                      "converged_plain": sum(v["status"] == 0 for v in per.values()),
                      "converged_batched": int((np.asarray(status) == 0).sum()), "instances": len(insts),
                      "max_rel_dQ_batched_vs_plain": max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(bq, pq))}
+        # the batched run again with mixed iterates (an extension of the paper's plain iteration)
+        if len(insts) <= 6 and dvm is not None:
+            aa = [solver(dvm, s_inst, prec, stream, anderson=ANDERSON_DEPTH) for s_inst in insts]
+            ab = dvm.Batch(aa)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st_aa = ab.run(tol=t, max_iter=max_iter)
+            t_aa = time.perf_counter() - t0
+            out[prec]["anderson"] = {
+                "depth": ANDERSON_DEPTH, "batched_total_s": t_aa,
+                "converged": int((np.asarray(st_aa) == 0).sum()),
+                "iterations": [s.info()["iterations"] for s in aa],
+                "max_rel_dQ_vs_plain": max(abs(s.flowrate()[0] - b) / max(abs(b), 1e-300) for s, b in zip(aa, pq))}
+            ab.close()
+            for s in aa:
+                s.close()
         if len(insts) <= 6:
             out[prec]["plain"] = per
             out[prec]["batched_Q"] = bq
@@ -470,6 +489,11 @@ def curves(results, insts, torch, max_iter=200000):
         t0 = time.perf_counter()
         fka, fit_iters, fit_status = perm.solve_batch(fit_masks, fit_kns, PERM_FIT_QUAD, prec, tol, max_iter)
         dt_fit = time.perf_counter() - t0
+        # the same fit solves with mixed iterates (an extension of the paper's plain iteration)
+        t0 = time.perf_counter()
+        fka_aa, fit_iters_aa, fit_status_aa = perm.solve_batch(fit_masks, fit_kns, PERM_FIT_QUAD, prec, tol, max_iter,
+                                                               anderson=ANDERSON_DEPTH)
+        dt_fit_aa = time.perf_counter() - t0
         media = {}
         for kind in inputs.MEDIA:
             idx = [i for i, inst in enumerate(insts) if inst.extra.get("medium") == kind]
@@ -480,11 +504,15 @@ def curves(results, insts, torch, max_iter=200000):
                                          [fka[j] for j in fsel], insts[idx[0]].extra["porosity"])
             res["iterations"] = {f"{k:g}": iters[k] for k in sorted(iters)}
             res["fit_iterations"] = {f"{fit_kns[j]:g}": fit_iters[j] for j in fsel}
+            res["fit_iterations_anderson"] = {f"{fit_kns[j]:g}": fit_iters_aa[j] for j in fsel}
+            res["fit_k_a_anderson_max_rel_diff"] = max(abs(fka_aa[j] - fka[j]) / abs(fka[j]) for j in fsel)
             both = sorted(set(PERM_KNS) & set(PERM_FIT_KNS))
             res["grid_check"] = {f"{k:g}": {"coarse_cubic32": ka[k], "refined_gh12": fka[fsel[PERM_FIT_KNS.index(k)]]}
                                  for k in both}
             media[kind] = res
         out[prec] = {"tol": tol, "max_iter": max_iter, "curve_batch_s": dt, "fit_batch_s": dt_fit,
+                     "fit_batch_anderson_s": dt_fit_aa, "anderson_depth": ANDERSON_DEPTH,
+                     "fit_converged_anderson": sum(s == 0 for s in fit_status_aa),
                      "instances": len(insts) + len(fit_kns),
                      "converged": int((np.asarray(status) == 0).sum()) + sum(s == 0 for s in fit_status),
                      "fit": f"k_inf from Kn {PERM_FIT_KNS} on the media refined {PERM_FIT_REFINE}x, {PERM_FIT_QUAD}",

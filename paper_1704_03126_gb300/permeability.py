@@ -61,15 +61,17 @@ def equivalent_knudsen(kn, k_inf: float, phi: float):
     return np.asarray(kn, dtype=np.float64) / characteristic_length(k_inf, phi)
 
 
-def solve_batch(masks, kns, quad, precision="fp32", tol=None, max_iter=200000, schedule="autotune", stream=None):
+def solve_batch(masks, kns, quad, precision="fp32", tol=None, max_iter=200000, schedule="autotune", stream=None,
+                anderson=0):
     """Force-driven flow through each (mask, Kn) pair (both axes periodic, H = 1), all advanced as one
-    batch on the GPU from h = 0 until every stopping test passes.  Returns (k_a, iterations, status)
-    lists in the order of the pairs."""
+    batch on the GPU from h = 0 until every stopping test passes (anderson > 0: mixed iterates of that
+    depth).  Returns (k_a, iterations, status) lists in the order of the pairs."""
     from . import dvm
 
     if tol is None:
         tol = 1e-10 if precision == "fp64" else 1e-6
-    sols = [dvm.Solver(m, True, True, kn=k, quad=quad, precision=precision, stream=stream) for m, k in zip(masks, kns)]
+    sols = [dvm.Solver(m, True, True, kn=k, quad=quad, precision=precision, stream=stream, anderson=anderson)
+            for m, k in zip(masks, kns)]
     batch = dvm.Batch(sols)
     try:
         if schedule == "autotune":
@@ -100,7 +102,7 @@ def curve_from_values(kns, kas, fit_kns, fit_kas, phi):
 
 def permeability_curve(mask, kns, fit_kns=(0.005, 0.01, 0.02), quad=("cubic", 32, 4.0),
                        fit_quad=("gh", 12, 0.0), fit_refine=2, precision="fp32", porosity=None, tol=None,
-                       max_iter=200000, schedule="autotune", stream=None):
+                       max_iter=200000, schedule="autotune", stream=None, anderson=0):
     """k_a(Kn), k_inf and k_a / k_inf against Kn* for the force-driven flow through one periodic medium.
 
     mask: uint8 [ny][nx], both axes periodic, height H = 1.  kns: the Knudsen numbers of the curve,
@@ -108,6 +110,7 @@ def permeability_curve(mask, kns, fit_kns=(0.005, 0.01, 0.02), quad=("cubic", 32
     mask refined `fit_refine` times with `fit_quad`.  Each set runs as one batch (`dvm.Batch`; the
     sweep kernel picked by the library's autotuner unless schedule is "none").  Returns a dict with
     the Knudsen numbers, k_a, k_inf, phi, H*, Kn*, the ratios and the solves' iterations and statuses.
+    anderson: depth of the mixed iteration for every solve (0 = plain).
     """
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     phi = float(1.0 - mask.mean()) if porosity is None else float(porosity)
@@ -115,8 +118,9 @@ def permeability_curve(mask, kns, fit_kns=(0.005, 0.01, 0.02), quad=("cubic", 32
     fit = sorted(float(k) for k in fit_kns)
     fine = refine_mask(mask, fit_refine) if fit_refine > 1 else mask
     fka, fit_iters, fit_status = solve_batch([fine] * len(fit), fit, fit_quad, precision, tol, max_iter, schedule,
-                                             stream)
-    ka, iters, status = solve_batch([mask] * len(kns), kns, quad, precision, tol, max_iter, schedule, stream)
+                                             stream, anderson)
+    ka, iters, status = solve_batch([mask] * len(kns), kns, quad, precision, tol, max_iter, schedule, stream,
+                                    anderson)
     out = curve_from_values(kns, ka, fit, fka, phi)
     out["iterations"] = {f"{k:g}": i for k, i in zip(fit + kns, fit_iters + iters)}
     out["status"] = {f"{k:g}": s for k, s in zip(fit + kns, fit_status + status)}
