@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--schedule", default="autotune",
                     help="sweep kernel: autotune, rows, rows<cw> (chunk width), columns1, columns2, columns4")
     ap.add_argument("--fd-cells", type=int, default=16, help="adjoint workload: cells checked by central differences")
+    ap.add_argument("--anderson", type=int, default=0,
+                    help="mix the timed iterates with Anderson mixing of this depth (0 = the paper's plain iteration)")
     return ap.parse_args()
 
 
@@ -267,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
     upd = updates_per_step(insts)
 
     def make(precision):
-        return [solver(dvm, inst, precision, stream.cuda_stream) for inst in insts]
+        return [solver(dvm, inst, precision, stream.cuda_stream, anderson=args.anderson) for inst in insts]
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -353,10 +355,10 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic", "config": workload_config(args.precision, args.workload),
+        "data": "synthetic", "config": dict(workload_config(args.precision, args.workload), anderson_depth=args.anderson),
         "roofline": roofline(args.precision),
         "clocks": clocks,
-        # per step: the arming kernel, the sweep and the two finalize kernels
+        # per step: the arming kernel, the sweep and the two finalize kernels (and three mixing kernels)
         "gpu_launches": args.steps * (main["kernels_per_step"] + 1),
     }
     other = "fp64" if args.precision == "fp32" else "fp32"
