@@ -90,7 +90,8 @@ def parse():
                     help="sweep kernel: autotune, rows, rows<cw> (chunk width), columns1, columns2, columns4")
     ap.add_argument("--fd-cells", type=int, default=16, help="adjoint workload: cells checked by central differences")
     ap.add_argument("--anderson", type=int, default=0,
-                    help="mix the timed iterates with Anderson mixing of this depth (0 = the paper's plain iteration)")
+                    help="mix the timed iterates with Anderson mixing of this depth (0 = the paper's plain "
+                         "iteration; needs --precision fp64, times that precision only)")
     return ap.parse_args()
 
 
@@ -309,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
     results = {}
     sampler = ClockSampler(local_rank)
     sampler.start()
-    single = args.single or args.workload != "rough"
+    single = args.single or args.workload != "rough" or args.anderson > 0
     precisions = [args.precision] + ([] if single else ["fp64" if args.precision == "fp32" else "fp32"])
     schedules = {}
     for precision in precisions:
@@ -442,8 +443,9 @@ def converge(results, insts, torch, max_iter=200000, dvm=None, stream=None):
                      "converged_plain": sum(v["status"] == 0 for v in per.values()),
                      "converged_batched": int((np.asarray(status) == 0).sum()), "instances": len(insts),
                      "max_rel_dQ_batched_vs_plain": max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(bq, pq))}
-        # the batched run again with mixed iterates (an extension of the paper's plain iteration)
-        if len(insts) <= 6 and dvm is not None:
+        # the batched run again with mixed iterates (an extension of the paper's plain iteration; FP64
+        # storage only)
+        if len(insts) <= 6 and dvm is not None and prec == "fp64":
             aa = [solver(dvm, s_inst, prec, stream, anderson=ANDERSON_DEPTH) for s_inst in insts]
             ab = dvm.Batch(aa)
             torch.cuda.synchronize()
@@ -491,11 +493,6 @@ def curves(results, insts, torch, max_iter=200000):
         t0 = time.perf_counter()
         fka, fit_iters, fit_status = perm.solve_batch(fit_masks, fit_kns, PERM_FIT_QUAD, prec, tol, max_iter)
         dt_fit = time.perf_counter() - t0
-        # the same fit solves with mixed iterates (an extension of the paper's plain iteration)
-        t0 = time.perf_counter()
-        fka_aa, fit_iters_aa, fit_status_aa = perm.solve_batch(fit_masks, fit_kns, PERM_FIT_QUAD, prec, tol, max_iter,
-                                                               anderson=ANDERSON_DEPTH)
-        dt_fit_aa = time.perf_counter() - t0
         media = {}
         for kind in inputs.MEDIA:
             idx = [i for i, inst in enumerate(insts) if inst.extra.get("medium") == kind]
@@ -506,15 +503,11 @@ def curves(results, insts, torch, max_iter=200000):
                                          [fka[j] for j in fsel], insts[idx[0]].extra["porosity"])
             res["iterations"] = {f"{k:g}": iters[k] for k in sorted(iters)}
             res["fit_iterations"] = {f"{fit_kns[j]:g}": fit_iters[j] for j in fsel}
-            res["fit_iterations_anderson"] = {f"{fit_kns[j]:g}": fit_iters_aa[j] for j in fsel}
-            res["fit_k_a_anderson_max_rel_diff"] = max(abs(fka_aa[j] - fka[j]) / abs(fka[j]) for j in fsel)
             both = sorted(set(PERM_KNS) & set(PERM_FIT_KNS))
             res["grid_check"] = {f"{k:g}": {"coarse_cubic32": ka[k], "refined_gh12": fka[fsel[PERM_FIT_KNS.index(k)]]}
                                  for k in both}
             media[kind] = res
         out[prec] = {"tol": tol, "max_iter": max_iter, "curve_batch_s": dt, "fit_batch_s": dt_fit,
-                     "fit_batch_anderson_s": dt_fit_aa, "anderson_depth": ANDERSON_DEPTH,
-                     "fit_converged_anderson": sum(s == 0 for s in fit_status_aa),
                      "instances": len(insts) + len(fit_kns),
                      "converged": int((np.asarray(status) == 0).sum()) + sum(s == 0 for s in fit_status),
                      "fit": f"k_inf from Kn {PERM_FIT_KNS} on the media refined {PERM_FIT_REFINE}x, {PERM_FIT_QUAD}",
@@ -713,6 +706,8 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.anderson > 0 and args.precision != "fp64":
+        raise SystemExit("--anderson needs --precision fp64 (mixing runs on FP64 storage only)")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -114,8 +114,10 @@ typedef struct {
                                  the sweeps start from -- moments, wall-face fluxes, periodic seam values,
                                  the mass shift -- three more kernels per sweep; same fixed point, far
                                  fewer sweeps where the plain iteration converges slowly (small Kn).
-                                 Needs accommodation = 1.  Extra memory (2 depth + 3) doubles per state
-                                 element (8 per cell plus the seams). */
+                                 Needs accommodation = 1 and FP64 storage (with FP32 the sweep's rounding,
+                                 about 1e-7 relative, pollutes the mixing history and its residual cannot
+                                 certify the distance to the fixed point).  Extra memory (2 depth + 3)
+                                 doubles per state element (8 per cell plus the seams). */
 } dvm_params;
 
 /* The transport sweep kernel (both compute the same update; see dvm_set_schedule; nx below is the

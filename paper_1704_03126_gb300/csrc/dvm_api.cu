@@ -503,6 +503,9 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   BATCH_CUDA(cudaMemcpyAsync(b->d_descs, descs.data(), sizeof(InstanceDesc) * n, cudaMemcpyHostToDevice, b->stream));
   BATCH_CUDA(cudaMemcpyAsync(b->d_smap, smap.data(), sizeof(int) * smap.size(), cudaMemcpyHostToDevice, b->stream));
   BATCH_CUDA(cudaMemcpyAsync(b->d_fmap, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice, b->stream));
+  // row-sweep launches write only the row-major records: a column-sweep launch starts from a copy
+  if (cols)
+    for (int i = 0; i < n; ++i) BATCH_CUDA(launch_sync_diag(ctxs[i]->d_desc, ctxs[i]->ncell, b->fp64, b->stream));
   BATCH_CUDA(cudaStreamSynchronize(b->stream));
   for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
 #undef BATCH_CUDA
@@ -709,6 +712,8 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
     return fail(nullptr, DVM_EINVAL, "anderson_depth must be 0.." + std::to_string(kAAMaxDepth));
   if (P.anderson_depth > 0 && P.accommodation < 1.0)
     return fail(nullptr, DVM_EINVAL, "Anderson mixing needs fully diffuse walls (accommodation = 1)");
+  if (P.anderson_depth > 0 && P.precision != DVM_FP64)
+    return fail(nullptr, DVM_EINVAL, "Anderson mixing needs FP64 storage (FP32 rounding pollutes its history)");
   double ly = P.ly;
   if (P.row_heights) {
     if (!(P.dx1 > 0.0)) return fail(nullptr, DVM_EINVAL, "row heights need the x1 spacing dx1 > 0");

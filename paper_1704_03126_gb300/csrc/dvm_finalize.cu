@@ -161,7 +161,9 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
           }
         }
         store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
-        if (D->rec_diag)
+        // the diagonal-major copy only feeds the column sweep (rebuilt by sync_diag when a launch
+        // switches to it)
+        if (L.cols_v && D->rec_diag)
           store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
                            diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
                        A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
@@ -198,16 +200,9 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
       double est = INFINITY;
       int done = 0, status = 0;
       if (D->aa) {
-        // mixed iterates: the estimate from the plain residual (dvm_anderson.cu), and the FP32
-        // noise-floor exit on that residual.  Mixing fits the sweep's rounding noise too, so at the
-        // floor the residual wanders and keeps setting marginal minima: only a 10 % improvement counts.
+        // mixed iterates (FP64 storage only): the estimate from the plain residual (dvm_anderson.cu)
         est = st->aa_est;
         if (n >= 5 && est < st->tol) done = 1;
-        if (st->aa_res < 0.9 * st->aa_res_min) {
-          st->aa_res_min = st->aa_res;
-          st->aa_iter_min = n;
-        }
-        if (!done && D->fp32 && n >= 5 && st->aa_res < st->tol && n - st->aa_iter_min >= 16) done = 1;
       } else {
         if (n >= 5) {
           double r = back > 0.0 ? pow(eps / back, 0.25) : 0.0;
@@ -286,9 +281,22 @@ __global__ void reset_kernel(const InstanceDesc *D) {
     st->eps_min = INFINITY;
     st->iter_min = 0;
     st->mass_acc = st->du_acc = st->u_acc = st->q_acc = 0.0;
-    st->aa_res = st->aa_est = st->aa_res_min = INFINITY;
+    st->aa_res = st->aa_est = INFINITY;
     st->aa_rho = 0.0;
-    st->aa_iter_min = 0;
+  }
+}
+
+// Rebuild the diagonal-major records from the row-major ones (all four quadrants).
+template <typename T>
+__global__ void sync_diag_kernel(const InstanceDesc *D) {
+  const int ncell = D->ncell;
+  const SweepRec<T> *rec = static_cast<const SweepRec<T> *>(D->rec);
+  SweepRec<T> *diag = static_cast<SweepRec<T> *>(D->rec_diag);
+  const size_t qs = diag_quadrant_size(D->nx, D->ny);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 4 * ncell; t += gridDim.x * blockDim.x) {
+    const int q = t / ncell, cell = t - q * ncell;
+    diag[q * qs + diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0)] =
+        rec[(size_t)q * ncell + cell];
   }
 }
 
@@ -296,8 +304,6 @@ __global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
   st->tol = tol;
   st->eps_min = INFINITY;
   st->iter_min = st->iter;
-  st->aa_res_min = INFINITY;
-  st->aa_iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;
@@ -317,8 +323,6 @@ __global__ void arm_all_kernel(const InstanceDesc *descs, int n, double tol, int
   st->tol = tol;
   st->eps_min = INFINITY;
   st->iter_min = st->iter;
-  st->aa_res_min = INFINITY;
-  st->aa_iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;
@@ -355,6 +359,15 @@ cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cud
     reset_kernel<double><<<blocks, 256, 0, stream>>>(inst_dev);
   else
     reset_kernel<float><<<blocks, 256, 0, stream>>>(inst_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sync_diag(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream) {
+  const int blocks = (4 * ncell + 255) / 256 < 1024 ? (4 * ncell + 255) / 256 : 1024;
+  if (fp64)
+    sync_diag_kernel<double><<<blocks, 256, 0, stream>>>(inst_dev);
+  else
+    sync_diag_kernel<float><<<blocks, 256, 0, stream>>>(inst_dev);
   return cudaGetLastError();
 }
 

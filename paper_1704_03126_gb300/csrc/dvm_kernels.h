@@ -100,6 +100,8 @@ cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStr
 cudaError_t launch_anderson(const LaunchDesc &L, bool fp64, cudaStream_t stream);
 // Reset an instance to h = 0 (records, accumulators and state; arrays are cleared by the caller).
 cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
+// Rebuild an instance's diagonal-major records from its row-major ones (before column-sweep launches).
+cudaError_t launch_sync_diag(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
 // Arm every instance of a launch for `count` more sweeps (device-relative; one launch).
 cudaError_t launch_arm_all(const InstanceDesc *descs, int n, double tol, int count, cudaStream_t stream);
 // Arm the stopping test of an instance: tol, absolute sweep limit; clears done and status.

@@ -128,7 +128,7 @@ class Solver:
     "transposed"; arguments and results keep the [ny][nx] layout either way.  dx1: x1 spacing (0 = square
     cells ly / ny); row_heights: [ny] heights of the rows along x2 (ly becomes their sum; needs dx1 > 0,
     runs on the column sweep, stored transposed; no adjoint).  anderson: depth of the Anderson mixing of
-    the source iteration (0 = plain; 1..8; accommodation 1 only).
+    the source iteration (0 = plain; 1..8; FP64 storage and accommodation 1 only).
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),

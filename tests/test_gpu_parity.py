@@ -708,26 +708,22 @@ def test_anderson_mixing_reaches_the_oracle_fixed_point(case, schedule, depth):
 
 
 def test_anderson_mixing_cuts_the_sweeps_near_the_continuum():
-    """Plane channel at Kn = 0.05 (delta = 17.7), 96 rows: the plain iteration needs about 5000 sweeps
-    for 1e-11 and 2500 for 1e-6.  Depth-6 mixing reaches the same flow rate in about 1700 sweeps for
-    1e-11 (its late iterates contract about twice as fast per sweep as plain ones) and about 200 for
-    1e-6 (measured).  Its stopping estimate, the plain residual over 1 - rho, stays above the true
-    error."""
+    """Plane channel at Kn = 0.05 (delta = 17.7), 96 rows, FP64: the plain iteration needs about 5000
+    sweeps for 1e-11 and 1600 for 1e-8.  Depth-6 mixing reaches the same flow rate in about 1700 and 250
+    sweeps (measured; its late iterates contract about twice as fast per sweep as plain ones).  Its
+    stopping estimate, the plain residual over 1 - rho, stays above the true error."""
     mask = inputs.plates_mask(4, 96)
     res = {}
-    for precision, tol in (("fp64", 1e-11), ("fp32", 1e-6)):
+    for tol in (1e-11, 1e-8):
         for depth in (0, 6):
-            sol = dvm.Solver(mask, True, False, kn=0.05, quad=("gh", 12, 0.0), precision=precision, anderson=depth)
+            sol = dvm.Solver(mask, True, False, kn=0.05, quad=("gh", 12, 0.0), precision="fp64", anderson=depth)
             st, iters, est = sol.solve(tol=tol, max_iter=200000)
-            res[(precision, depth)] = (iters, sol.flowrate()[0])
-    q64 = res[("fp64", 0)][1]
-    # FP32 storage on this slowly converging case: both FP32 fixed points lie within the 1e-4 bound of
-    # the FP64 one (rounding amplified by 1 / (1 - r))
-    for precision, gain, bound in (("fp64", 2, 1e-10), ("fp32", 5, 1e-4)):
-        plain, mixed = res[(precision, 0)], res[(precision, 6)]
-        assert mixed[0] * gain < plain[0], (precision, plain, mixed)
-        assert abs(mixed[1] - q64) < bound * abs(q64), (precision, plain, mixed)
-        assert abs(plain[1] - q64) < bound * abs(q64), (precision, plain, mixed)
+            res[(tol, depth)] = (iters, sol.flowrate()[0])
+    q = res[(1e-11, 0)][1]
+    for tol, gain in ((1e-11, 2), (1e-8, 4)):
+        plain, mixed = res[(tol, 0)], res[(tol, 6)]
+        assert mixed[0] * gain < plain[0], (tol, plain, mixed)
+        assert abs(mixed[1] - q) < 10 * tol * abs(q), (tol, plain, mixed)
 
 
 def test_anderson_mixing_in_a_batch_with_plain_members():

@@ -78,6 +78,7 @@ def test_library_rejects_invalid_grids():
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=9),                         # mixing depth above 8
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=-1),
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=3, accommodation=0.5),     # mixing with specular walls
+    dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=3, precision="fp32"),      # mixing with FP32 storage
 ])
 def test_create_rejects_invalid_parameters(kwargs):
     with pytest.raises(dvm.DvmError) as ei:
