@@ -301,6 +301,17 @@ const char *dvm_last_error(const dvm_ctx *ctx);
 /* Static name of a status code. */
 const char *dvm_status_string(dvm_status status);
 
+/* Failure detection without a fault.  Every wait inside the sweeps is bounded: a row-sweep warp
+ * waiting for its neighbour's progress word, or a column-sweep block waiting for a TMA stage, gives
+ * up after a fixed spin count, records DVM_ETIMEOUT in the instance state (dvm_solve then returns it)
+ * and returns, leaving the context usable.  This entry point runs one of those wait primitives in a
+ * one-block kernel on a flag that nothing raises: primitive 0 = the row sweep's progress-word wait,
+ * 1 = the column sweep's mbarrier wait.  spin_limit > 0 replaces the sweeps' limit (2^22 spins) to
+ * keep the call short.  Returns DVM_ETIMEOUT (the wait gave up, the expected outcome), DVM_OK (the
+ * flag was seen: impossible unless the primitive is broken), DVM_EINVAL or DVM_ECUDA; seconds (may be
+ * NULL) receives the call's wall time.  The paper has no counterpart. */
+dvm_status dvm_selftest_wait(int primitive, int spin_limit, double *seconds);
+
 /* Release the context and its device memory.  NULL is ignored. */
 void dvm_destroy(dvm_ctx *ctx);
 

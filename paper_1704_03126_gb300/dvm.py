@@ -99,13 +99,14 @@ def lib():
         L.dvm_batch_set_schedule.argtypes = [P, I, I]
         L.dvm_batch_get_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         L.dvm_batch_autotune.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
+        L.dvm_selftest_wait.argtypes = [I, I, ctypes.POINTER(D)]
         for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
                      "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
                      "dvm_moments_noalloc", "dvm_adjoint", "dvm_set_schedule", "dvm_get_schedule",
                      "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune",
-                     "dvm_batch_enqueue", "dvm_batch_check"):
+                     "dvm_batch_enqueue", "dvm_batch_check", "dvm_selftest_wait"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -364,6 +365,14 @@ def batch_solve(solvers, tol=1e-10, max_iter=100000):
     if st not in (DVM_OK, DVM_ENOCONV):
         raise DvmError(st, lib().dvm_last_error(solvers[0]._ctx).decode())
     return per
+
+
+def selftest_wait(primitive: int, spin_limit: int = 0):
+    """Run a sweep wait primitive (0: progress word, 1: mbarrier) on a flag nothing raises:
+    (status, seconds); the expected status is DVM_ETIMEOUT."""
+    sec = ctypes.c_double(0.0)
+    st = lib().dvm_selftest_wait(int(primitive), int(spin_limit), ctypes.byref(sec))
+    return st, sec.value
 
 
 def velocity_grid(kind: str, n: int, vmax: float = 5.0):

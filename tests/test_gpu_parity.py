@@ -743,3 +743,23 @@ def test_anderson_mixing_in_a_batch_with_plain_members():
     it = mixed[0].solve(tol=1e-12, max_iter=100000)[1]
     assert abs(mixed[0].flowrate()[0] - ref[0].flowrate()[0]) < 1e-10 * abs(ref[0].flowrate()[0])
     assert it > 0
+
+
+# ------------------------------------------------------------------ failure detection (bounded waits)
+
+@pytest.mark.parametrize("primitive", [0, 1], ids=["progress_word", "mbarrier"])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(primitive):
+    """A sweep wait primitive on a flag nothing raises gives up after its spin limit (DVM_ETIMEOUT, no
+    fault, no hang); with the sweeps' own limit it ends within seconds (measured 0.27 s for the
+    progress word, 0.33 s for the mbarrier); afterwards a solve on the same device still matches the
+    oracle."""
+    st, sec = dvm.selftest_wait(primitive, 1 << 14)
+    assert st == dvm.DVM_ETIMEOUT and sec < 2.0, (st, sec)
+    st, sec = dvm.selftest_wait(primitive, 0)
+    assert st == dvm.DVM_ETIMEOUT and sec < 5.0, (st, sec)
+    inst = inputs.plates_instance(kn=0.3, nx=4, ny=12, nv=8)
+    sol = dvm.Solver(inst.mask, True, False, kn=inst.kn, quad=inst.quad, precision="fp64")
+    sol.solve(tol=1e-12, max_iter=100000)
+    orc = oracle.solve(oracle.Problem.make(inst.mask, True, False, dvm.kn_to_delta(inst.kn), inst.quad), tol=1e-12,
+                       max_iter=100000)
+    _compare(sol, orc, inst.mask, "fp64")

@@ -117,3 +117,8 @@ def test_status_strings():
     L = dvm.lib()
     assert L.dvm_status_string(0) == b"DVM_OK"
     assert L.dvm_status_string(4) == b"DVM_ENOCONV"
+
+
+def test_selftest_wait_rejects_an_unknown_primitive():
+    st, sec = dvm.selftest_wait(7, 10)
+    assert st == dvm.DVM_EINVAL
