@@ -51,6 +51,7 @@ PERM_FIT_KNS = (0.005, 0.01, 0.02)  # k_inf is extrapolated to Kn = 0 from these
 PERM_KNS = (0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0)
 PERM_FIT_QUAD = ("gh", 12, 0.0)
 PERM_FIT_REFINE = 2
+FD_DIR_CELLS = 1024  # cells of the adjoint workload's directional finite-difference check
 ANDERSON_DEPTH = 6  # depth of the mixed iteration reported beside the plain one (time to converge)
 POROUS_KNS = (0.05, 0.5, 5.0)
 METRICS = {
@@ -618,6 +619,12 @@ def run_adjoint(args, rank, world, local_rank):
     eps_dir = 1e-3
     for sgn in (1.0, -1.0):
         fields.append((base.ravel() * (1.0 + sgn * eps_dir * dirn)).reshape(inst.mask.shape))
+    # one directional difference over FD_DIR_CELLS seeded cells (the adjoint configuration's check size)
+    cells_dir = inputs.sample_gas_cells(inst.mask, FD_DIR_CELLS, seed=11)
+    dirn2 = np.zeros(inst.mask.size)
+    dirn2[cells_dir] = np.random.default_rng(11).standard_normal(len(cells_dir))
+    for sgn in (1.0, -1.0):
+        fields.append((base.ravel() * (1.0 + sgn * eps_dir * dirn2)).reshape(inst.mask.shape))
     qs = []
     t0 = time.perf_counter()
     chunk = 48
@@ -635,8 +642,10 @@ def run_adjoint(args, rank, world, local_rank):
     fd = (qs[0:2 * len(cells):2] - qs[1:2 * len(cells):2]) / (2 * step)
     g = grad.ravel()[cells]
     gscale = np.abs(grad).max()
-    dir_fd = (qs[-2] - qs[-1]) / (2 * eps_dir)
+    dir_fd = (qs[-4] - qs[-3]) / (2 * eps_dir)
     dir_adj = float((grad.ravel() * base.ravel() * dirn).sum())
+    dir2_fd = (qs[-2] - qs[-1]) / (2 * eps_dir)
+    dir2_adj = float((grad.ravel() * base.ravel() * dirn2).sum())
     value = a_iters * upd / (adj_ms / 1e3)
     peaks = {}
     try:
@@ -664,7 +673,9 @@ def run_adjoint(args, rank, world, local_rank):
         "fd_check": {"cells": int(len(cells)), "step": "1e-3 delta", "forward_tol": fd_tol,
                      "max_abs_err_over_max_grad": float(np.abs(fd - g).max() / gscale),
                      "median_rel_err": float(np.median(np.abs(fd - g) / np.maximum(np.abs(g), 1e-300))),
-                     "directional_rel_err": abs(dir_fd - dir_adj) / abs(dir_adj), "seconds": fd_s,
+                     "directional_rel_err": abs(dir_fd - dir_adj) / abs(dir_adj),
+                     "directional_cells": int(len(cells_dir)),
+                     "directional_over_cells_rel_err": abs(dir2_fd - dir2_adj) / abs(dir2_adj), "seconds": fd_s,
                      "solves": len(fields)},
     }
     sol.close()
