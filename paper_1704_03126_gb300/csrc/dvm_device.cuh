@@ -114,6 +114,8 @@ struct DeviceState {
   double aa_res;       // |f| / |g| over the flow velocity of the gas cells (L2)
   double aa_rho;       // running estimate of the plain contraction, max |dG| / |dx| over the differences
   double aa_est;       // aa_res / (1 - aa_rho): the distance to the fixed point
+  double aa_res_min;   // smallest aa_res since the solve was armed (10 % steps)
+  int aa_iter_min;     // sweep of that minimum
 };
 
 // Anderson mixing of the source iteration (dvm_anderson.cu), one per instance that uses it.  The

@@ -200,9 +200,16 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
       double est = INFINITY;
       int done = 0, status = 0;
       if (D->aa) {
-        // mixed iterates (FP64 storage only): the estimate from the plain residual (dvm_anderson.cu)
+        // mixed iterates (FP64 storage only): the estimate from the plain residual (dvm_anderson.cu).
+        // Near the rounding floor the residual stops falling while rho keeps the estimate above a
+        // tight tol: below tol, 32 sweeps without a 10 % smaller residual also end the iteration.
         est = st->aa_est;
         if (n >= 5 && est < st->tol) done = 1;
+        if (st->aa_res < 0.9 * st->aa_res_min) {
+          st->aa_res_min = st->aa_res;
+          st->aa_iter_min = n;
+        }
+        if (!done && n >= 5 && st->aa_res < st->tol && n - st->aa_iter_min >= 32) done = 1;
       } else {
         if (n >= 5) {
           double r = back > 0.0 ? pow(eps / back, 0.25) : 0.0;
@@ -281,8 +288,9 @@ __global__ void reset_kernel(const InstanceDesc *D) {
     st->eps_min = INFINITY;
     st->iter_min = 0;
     st->mass_acc = st->du_acc = st->u_acc = st->q_acc = 0.0;
-    st->aa_res = st->aa_est = INFINITY;
+    st->aa_res = st->aa_est = st->aa_res_min = INFINITY;
     st->aa_rho = 0.0;
+    st->aa_iter_min = 0;
   }
 }
 
@@ -304,6 +312,8 @@ __global__ void arm_kernel(DeviceState *st, double tol, int max_iter_abs) {
   st->tol = tol;
   st->eps_min = INFINITY;
   st->iter_min = st->iter;
+  st->aa_res_min = INFINITY;
+  st->aa_iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;
@@ -323,6 +333,8 @@ __global__ void arm_all_kernel(const InstanceDesc *descs, int n, double tol, int
   st->tol = tol;
   st->eps_min = INFINITY;
   st->iter_min = st->iter;
+  st->aa_res_min = INFINITY;
+  st->aa_iter_min = st->iter;
   st->max_iter = max_iter_abs;
   st->status = 0;
   st->nan_flag = 0;

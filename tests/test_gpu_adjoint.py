@@ -147,3 +147,20 @@ def test_adjoint_gradient_in_either_storage_order(name, schedule, storage):
     scale = np.abs(g_ref).max()
     assert np.abs(grad - g_ref).max() < 1e-8 * scale
     assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)
+
+
+def test_adjoint_after_a_mixed_forward_solve():
+    """Anderson-mixed forward iterates (FP64) converge to the same state, so the adjoint taken there
+    matches the oracle's gradient."""
+    name = "rough24_nc8"
+    _, mask, px, py, delta, quad = next(c for c in CASES if c[0] == name)
+    d = _delta_field(mask, delta, 3)
+    sol = dvm.Solver(mask, px, py, delta=delta, quad=quad, precision="fp64", store_distribution=True, anderson=5)
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=200000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=200000)
+    g_ref, _, _, ok = _oracle_gradient(name)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale
+    assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)

@@ -763,3 +763,32 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(primitive):
     orc = oracle.solve(oracle.Problem.make(inst.mask, True, False, dvm.kn_to_delta(inst.kn), inst.quad), tol=1e-12,
                        max_iter=100000)
     _compare(sol, orc, inst.mask, "fp64")
+
+
+def test_batch_of_mixed_storage_and_spacing_matches_single_solves():
+    """One column-sweep launch holding a grid stored as given (tall), one stored transposed (wide) and
+    one with rows of unequal height: each member reaches its single-solve fixed point."""
+    tall = _notch(8, 14)
+    wide = _notch(20, 9)
+    rows = _notch(9, 12)
+    dy = _stretched_rows(12, 4)
+    specs = [
+        dict(mask=tall, kn=0.6, quad=("gh", 8, 0.0)),
+        dict(mask=wide, kn=1.5, quad=("nc", 8, 4.0)),
+        dict(mask=rows, kn=0.4, quad=("cubic", 8, 4.0), dx1=0.08, row_heights=dy),
+    ]
+    batch, singles = [], []
+    for sp in specs:
+        kw = {k: v for k, v in sp.items() if k not in ("mask", "kn", "quad")}
+        batch.append(dvm.Solver(sp["mask"], True, False, kn=sp["kn"], quad=sp["quad"], precision="fp64", **kw))
+        singles.append(dvm.Solver(sp["mask"], True, False, kn=sp["kn"], quad=sp["quad"], precision="fp64", **kw))
+    assert [s.info()["transposed"] for s in batch] == [False, True, True]
+    b = dvm.Batch(batch)
+    assert b.schedule()[0] == "columns"
+    b.run(tol=1e-12, max_iter=200000)
+    for s, r in zip(batch, singles):
+        r.solve(tol=1e-12, max_iter=200000)
+        assert abs(s.flowrate()[0] - r.flowrate()[0]) < 1e-10 * abs(r.flowrate()[0])
+        fs, fr = s.fields(), r.fields()
+        gas = ~np.isnan(fr["u1"])
+        assert np.abs(fs["u1"][gas] - fr["u1"][gas]).max() < 1e-9
