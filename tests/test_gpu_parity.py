@@ -792,3 +792,14 @@ def test_batch_of_mixed_storage_and_spacing_matches_single_solves():
         fs, fr = s.fields(), r.fields()
         gas = ~np.isnan(fr["u1"])
         assert np.abs(fs["u1"][gas] - fr["u1"][gas]).max() < 1e-9
+
+
+@pytest.mark.parametrize("storage", ["as_given", "transposed"])
+def test_plane_couette_with_partially_specular_plates_on_the_gpu(storage):
+    """Any accommodation leaves the uniform drift invariant, so Q = U H m0 m2 (1/2 for Gauss-Hermite)."""
+    sol = dvm.Solver(inputs.plates_mask(3, 14), True, False, kn=0.5, quad=("gh", 8, 0.0), precision="fp64",
+                     force=0.0, top_wall_u1=1.0, accommodation=0.6, storage=storage)
+    sol.solve(tol=1e-13, max_iter=200000)
+    assert abs(sol.flowrate()[0] - 0.5) < 1e-10
+    u1 = sol.fields()["u1"][:, 0]
+    assert np.max(np.abs(u1 + u1[::-1] - 1.0)) < 1e-9

@@ -254,14 +254,35 @@ def test_plane_couette_flow_rate_is_half(kn, quad):
     p = oracle.Problem.make(np.zeros((ny, 4), np.uint8), True, False, oracle.delta_from_kn(kn), quad,
                             force=0.0, top_u=1.0)
     m0, m2 = float(p.wv.sum()), float((p.wv * p.xv ** 2).sum())
+    r = oracle.solve(p, tol=1e-13, max_iter=400000)
+    assert r["converged"]
+    assert abs(r["Q"] - m0 * m2) < 1e-10
     if quad[0] == "gh":
-        assert abs(m0 * m2 - 0.5) < 1e-14
+        gold = json.load(open(os.path.join(GOLDEN, "couette_smooth_flow_rate.json")))
+        assert abs(m0 * m2 - gold["value"]) < 1e-14
+        assert abs(r["Q"] - gold["value"]) < 1e-10 + gold["abs_uncertainty_for_test"]
+    u1 = r["u1"][:, 0]
+    assert np.max(np.abs(u1 + u1[::-1] - 2.0 * m0 * m2)) < 1e-10
+    assert np.all(np.diff(u1) > 0)  # the shear profile rises towards the moving plate
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.8])
+def test_plane_couette_with_partially_specular_plates(alpha):
+    """The uniform drift 2 (U/2) v1 is also left unchanged by specular reflection (v1 keeps its sign),
+    so the argument above holds for any accommodation: Q = U H m0 m2 and the mirrored profile."""
+    ny = 14
+    p = oracle.Problem.make(np.zeros((ny, 3), np.uint8), True, False, oracle.delta_from_kn(0.5), ("gh", 8, 0.0),
+                            alpha=alpha, force=0.0, top_u=1.0)
+    m0, m2 = float(p.wv.sum()), float((p.wv * p.xv ** 2).sum())
     r = oracle.solve(p, tol=1e-13, max_iter=400000)
     assert r["converged"]
     assert abs(r["Q"] - m0 * m2) < 1e-10
     u1 = r["u1"][:, 0]
     assert np.max(np.abs(u1 + u1[::-1] - 2.0 * m0 * m2)) < 1e-10
-    assert np.all(np.diff(u1) > 0)  # the shear profile rises towards the moving plate
+    # partially specular plates drag less: the slip at each plate grows as alpha falls
+    full = oracle.solve(oracle.Problem.make(np.zeros((ny, 3), np.uint8), True, False, oracle.delta_from_kn(0.5),
+                                            ("gh", 8, 0.0), force=0.0, top_u=1.0), tol=1e-13, max_iter=400000)
+    assert u1[0] > full["u1"][0, 0]
 
 
 @pytest.mark.parametrize("alpha", [1.0, 0.6])
