@@ -10,11 +10,16 @@
  * f = f_eq (1 + h), f_eq = exp(-|v|^2)/pi, delta = sqrt(pi)/(2 Kn) (Eq. BGK), moments
  * rho = int h f_eq, u = int v h f_eq, tau = int |v|^2 h f_eq - rho, diffuse walls (Eq. diffuse2),
  * staircase geometry on a Cartesian mask, periodic inlet/outlet (Sec. II.A; Sec. III for porous
- * media with both axes periodic), the unit body force F v1 driving Poiseuille flow (Sec. III), and
- * the source iteration of Eq. (iteration) with second-order upwind differences.
+ * media with both axes periodic), the unit body force F v1 driving Poiseuille flow (Sec. III), a
+ * moving top plate for Couette flow (Sec. II, Eq. diffuse1), and the source iteration of Eq.
+ * (iteration) with second-order upwind differences (on rows of unequal height if given, Sec. II.A).
+ * Extensions beyond the paper: the adjoint gradient dQ/d delta_c, batched solves with an autotuned
+ * sweep kernel, FP32 storage with FP64 accumulation, Anderson mixing of the iteration, and a
+ * self-test of the bounded device-side waits.
  *
  * Conventions for every call:
- *   - Arrays named [ny][nx] are row-major with the x1 index fastest; row j is at x2 = (j + 1/2) H/ny.
+ *   - Arrays named [ny][nx] are row-major with the x1 index fastest; row j is at x2 = (j + 1/2) H/ny
+ *     (the centre of row j when row heights are given), whatever the storage order (dvm_storage).
  *   - Pointers marked "host" are ordinary host memory; the library never keeps them.
  *   - The library copies every input; outputs are caller-allocated.
  *   - Calls return a dvm_status and never abort; dvm_last_error() describes the last failure on a
