@@ -543,7 +543,40 @@ def cpu_baseline(insts, workload="rough", budget_s=12.0):
     upd = int((inst.mask == 0).sum()) * K * n
     return {"value": upd / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
             "kind": "oracle",
-            "sample": f"{n} source-iteration sweeps of instance {inst.name} (FP64, C + OpenMP), {dt:.1f} s"}
+            "sample": f"{n} source-iteration sweeps of instance {inst.name} (FP64, C + OpenMP), {dt:.1f} s",
+            "one_thread": oracle_one_thread(workload, budget_s / 4)}
+
+
+def oracle_one_thread(workload, budget_s):
+    """The same oracle sample on one host thread (a fresh interpreter with OMP_NUM_THREADS=1)."""
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
+            f"r = bench.cpu_baseline_sample(bench.instances({workload!r}), {workload!r}, {budget_s!r}); "
+            f"print(json.dumps(r))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": str(e)[:200]}
+
+
+def cpu_baseline_sample(insts, workload="rough", budget_s=3.0):
+    """updates/s of the oracle on the sample cpu_baseline uses, with the threads OpenMP is given."""
+    import oracle
+
+    inst = insts[1] if len(insts) in (3, 6) else insts[0]
+    p = oracle_problem(oracle, inst)
+    K = inst.quad[1] ** 2
+    h = np.zeros((K, p.ny, p.nx))
+    t0 = time.perf_counter()
+    oracle.solve(p, tol=0.0, max_iter=1, h0=h, inplace=True)
+    first = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(first, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.solve(p, tol=0.0, max_iter=n, h0=h, inplace=True)
+    dt = time.perf_counter() - t0
+    return {"value": int((inst.mask == 0).sum()) * K * n / dt, "unit": UNIT, "cores": 1,
+            "sample": f"{n} sweeps of instance {inst.name} on one thread, {dt:.1f} s"}
 
 
 def run_adjoint(args, rank, world, local_rank):
