@@ -466,6 +466,7 @@ def converge(results, insts, torch, max_iter=200000, dvm=None, stream=None):
             out[prec]["batched_Q"] = bq
         if any(i.extra.get("top_u", 0.0) != 0.0 for i in insts):
             out[prec]["Q_star"] = couette_q_star(insts, bq)
+            out[prec]["profiles"] = couette_profiles(insts, r["solvers"])
     return out
 
 
@@ -513,6 +514,27 @@ def curves(results, insts, torch, max_iter=200000):
                      "converged": int((np.asarray(status) == 0).sum()) + sum(s == 0 for s in fit_status),
                      "fit": f"k_inf from Kn {PERM_FIT_KNS} on the media refined {PERM_FIT_REFINE}x, {PERM_FIT_QUAD}",
                      "media": media}
+    return out
+
+
+PROFILE_POINTS = (0.02, 0.05, 0.1, 0.25, 0.5, 0.75, 0.9, 0.95, 0.98)
+
+
+def couette_profiles(insts, solvers):
+    """Mean streamwise velocity u1_bar(x2) (average over x1, solid cells as zero; the plate moves at
+    x2 = H = 1, the mean bottom is x2 = 0) at PROFILE_POINTS for Kn 0.1 and 1, the cases of the paper's
+    velocity-profile comparison (Sec. II.B)."""
+    from paper_1704_03126_gb300 import couette
+    out = {}
+    for inst, s in zip(insts, solvers):
+        if inst.kn not in (0.1, 1.0):
+            continue
+        x = inst.extra
+        ly = float(x.get("ly", 1.0))
+        y, ub = couette.mean_profile(s.fields()["u1"], inst.mask, ly, x.get("row_heights"), y0=1.0 - ly)
+        kind = "rough" if x.get("eps", 0.0) > 0.0 else "smooth"
+        out[f"{kind}_kn{inst.kn:g}"] = {"x2": list(PROFILE_POINTS),
+                                         "u1_bar": couette.profile_at(y, ub, PROFILE_POINTS).tolist()}
     return out
 
 

@@ -417,3 +417,25 @@ def test_unequal_rows_have_no_oracle_adjoint():
     r = oracle.solve(p, tol=1e-10)
     with pytest.raises(ValueError):
         oracle.adjoint(p, r["h"], r["c"])
+
+
+def test_couette_mean_profile_integrates_to_the_flow_rate():
+    """The mean streamwise profile (solid cells as zero) integrates to Q over the rows, on equal and on
+    stretched rows over a notched wall; between smooth plates it is mirror-symmetric about m0 m2."""
+    from paper_1704_03126_gb300 import couette
+    notch = np.zeros((10, 6), np.uint8)
+    notch[0:2, 2] = 1
+    for dy in (None, _stretched_rows(10, 9)):
+        kw = dict(dy=dy, dx1=0.1) if dy is not None else {}
+        p = oracle.Problem.make(notch, True, False, 1.2, ("gh", 6, 0.0), force=0.0, top_u=1.0, **kw)
+        r = oracle.solve(p, tol=1e-13, max_iter=200000)
+        y, ub = couette.mean_profile(r["u1"], notch, p.ly, dy)
+        assert abs(float((ub * p.row_heights()).sum()) - r["Q"]) < 1e-13
+        assert np.all(np.diff(y) > 0) and abs(y[-1] + 0.5 * p.row_heights()[-1] - p.ly) < 1e-14
+    p = oracle.Problem.make(np.zeros((12, 3), np.uint8), True, False, 0.8, ("gh", 8, 0.0), force=0.0, top_u=1.0)
+    r = oracle.solve(p, tol=1e-13, max_iter=200000)
+    y, ub = couette.mean_profile(r["u1"], p.mask)
+    m0m2 = float(p.wv.sum() * (p.wv * p.xv ** 2).sum())
+    assert np.max(np.abs(ub + ub[::-1] - 2 * m0m2)) < 1e-10
+    assert abs(couette.profile_at(y, ub, [0.5])[0] - m0m2) < 1e-10
+    assert abs(couette.q_star(0.45, 0.5) - 0.9) < 1e-15
