@@ -122,3 +122,45 @@ def test_status_strings():
 def test_selftest_wait_rejects_an_unknown_primitive():
     st, sec = dvm.selftest_wait(7, 10)
     assert st == dvm.DVM_EINVAL
+
+
+def test_every_entry_point_rejects_null_handles():
+    """No call dereferences a NULL context, batch or output pointer: each returns DVM_EINVAL (checked
+    before any CUDA call, so this runs without a GPU)."""
+    import ctypes
+    L = dvm.lib()
+    P = None
+    d = ctypes.c_double()
+    i = ctypes.c_int()
+    f = ctypes.c_float()
+    calls = {
+        "dvm_reset": (P,),
+        "dvm_set_delta_field": (P, P),
+        "dvm_solve": (P, 1e-6, 10, ctypes.byref(i), ctypes.byref(d)),
+        "dvm_iterate": (P, 1),
+        "dvm_flowrate": (P, ctypes.byref(d), ctypes.byref(d)),
+        "dvm_fields": (P, P, P, P, P),
+        "dvm_get_info": (P, P),
+        "dvm_distribution": (P, P, 0, P),
+        "dvm_quadrature": (P, P, P),
+        "dvm_adjoint": (P, 1e-6, 10, P, P, P),
+        "dvm_set_schedule": (P, 0, 0),
+        "dvm_get_schedule": (P, ctypes.byref(i), ctypes.byref(i)),
+        "dvm_batch_create": (P, 0, P),
+        "dvm_batch_run": (P, 1e-6, 10, P),
+        "dvm_batch_iterate": (P, 1),
+        "dvm_batch_enqueue": (P, 1),
+        "dvm_batch_check": (P,),
+        "dvm_batch_timing": (P, ctypes.byref(f), ctypes.byref(f)),
+        "dvm_batch_set_schedule": (P, 0, 0),
+        "dvm_batch_get_schedule": (P, ctypes.byref(i), ctypes.byref(i)),
+        "dvm_batch_autotune": (P, 1, ctypes.byref(i), ctypes.byref(i), ctypes.byref(f)),
+        "dvm_velocity_grid": (P, P, P),
+        "dvm_params_init": (P,),
+    }
+    for name, args in calls.items():
+        st = getattr(L, name)(*args)
+        assert st == dvm.DVM_EINVAL, (name, st)
+    # destroy functions accept NULL silently
+    L.dvm_destroy(None)
+    L.dvm_batch_destroy(None)
