@@ -762,7 +762,9 @@ def run_reference(args):
         "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config("fp64", args.workload if args.workload != "adjoint" else "rough"),
+        # the same config as our arm's line for this workload (the oracle itself computes in FP64: dtype)
+        "config": dict(workload_config(args.precision, args.workload if args.workload != "adjoint" else "rough"),
+                       anderson_depth=args.anderson),
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} steps, each one FP64 oracle sweep of every instance"},
