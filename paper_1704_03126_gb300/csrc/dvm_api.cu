@@ -687,6 +687,8 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   const dvm_params &P = *params;
   if (P.nx < 2 || P.ny < 2 || P.nx > 65536 || P.ny > 65536)
     return fail(nullptr, DVM_EINVAL, "nx and ny must be in [2, 65536]");
+  // the finalize launch maps hold 16 bits of 256-cell blocks per instance
+  if ((long long)P.nx * P.ny > 65535LL * 256) return fail(nullptr, DVM_EINVAL, "at most 16,776,960 cells");
   if (!(P.ly > 0.0) || !std::isfinite(P.ly)) return fail(nullptr, DVM_EINVAL, "ly must be positive");
   if (!(P.accommodation >= 0.0 && P.accommodation <= 1.0))
     return fail(nullptr, DVM_EINVAL, "accommodation must be in [0, 1]");
@@ -730,6 +732,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   dvm_ctx *c = new (std::nothrow) dvm_ctx();
   if (!c) return fail(nullptr, DVM_ENOMEM, "host allocation failed");
   c->P = P;
+  c->P.row_heights = nullptr;  // the caller's array is read here only
   // the sweeps run along the stored x2 (column sweep: one thread per stored column; row sweep: rows in
   // flight across the stored x1), so a grid wider than tall is stored transposed by default
   // (row heights: the caller's x2 becomes the stored x1, along which every sweep thread owns a column)

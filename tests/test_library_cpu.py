@@ -75,6 +75,7 @@ def test_library_rejects_invalid_grids():
     dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, dx1=0.1, row_heights=np.array([0.3, 0.3, 0.0, 0.4])),
     dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, dx1=0.1, row_heights=np.full(4, 0.25), storage="as_given"),
     dict(mask=np.zeros((4, 8), np.uint8), kn=1.0, dx1=-0.1),                           # negative x1 spacing
+    dict(mask=np.zeros((8, 4096), np.uint8)[:, :2].repeat(2049, axis=1).repeat(512, axis=0), kn=1.0),  # > 16.8 M cells
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=9),                         # mixing depth above 8
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=-1),
     dict(mask=np.zeros((8, 8), np.uint8), kn=1.0, anderson=3, accommodation=0.5),     # mixing with specular walls
