@@ -81,7 +81,7 @@ typedef enum {
 } dvm_storage;
 
 typedef struct {
-  int nx, ny;                 /* cells along x1 (flow) and x2; both >= 2 */
+  int nx, ny;                 /* cells along x1 (flow) and x2; 2..65536 each, nx ny <= 16,776,960 */
   int periodic_x, periodic_y; /* 1 = periodic axis; a non-periodic axis is closed by diffuse walls */
   double ly;                  /* domain height H along x2 (cells are square, size ly/ny); > 0 */
   double kn;                  /* Knudsen number (> 0, +INFINITY allowed for delta = 0), or <= 0 ... */
