@@ -52,3 +52,24 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_bench_builds_each_instance_drive_for_both_sides():
+    """The benchmark hands the library and the oracle the same grid, force and plate speed per
+    instance: square cells for the force-driven workloads, the paper's rows for the Couette one."""
+    import bench
+    import oracle
+    rough = bench.instances("rough")[0]
+    d = bench.drive(rough)
+    assert d == {"ly": 1.0, "force": 1.0, "top_wall_u1": 0.0, "dx1": 0.0, "row_heights": None}
+    p = bench.oracle_problem(oracle, rough)
+    assert p.dy is None and abs(p.dx - 1.0 / 128) < 1e-15
+    cou = bench.instances("couette")
+    rough_c, smooth_c = cou[0], cou[3]
+    d = bench.drive(rough_c)
+    assert d["force"] == 0.0 and d["top_wall_u1"] == 1.0 and abs(d["dx1"] - 1.0 / 300) < 1e-15
+    p = bench.oracle_problem(oracle, rough_c)
+    assert p.dy.shape == (160,) and abs(p.ly - d["row_heights"].sum()) < 1e-15 and p.top_u == 1.0
+    q = bench.couette_q_star(cou, [0.49, 0.48, 0.46, 0.5, 0.5, 0.5])
+    assert set(q) == {"0.1", "1", "10"} and abs(q["10"]["Q_star"] - 0.92) < 1e-15
+    assert bench.updates_per_step(bench.instances("rough")) == 3 * 14720 * 1024
