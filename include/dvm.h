@@ -101,7 +101,7 @@ typedef struct {
                                  non-periodic x2 axis): Couette flow, Sec. II, Eq. (diffuse1) with
                                  U0/v_m = U: its reflected molecules carry the drift 2 U v1.  0 = at rest
                                  (every other wall is at rest).  A moving plate runs on the column sweep
-                                 only and has no adjoint (DVM_EINVAL there). */
+                                 only; its adjoint is that of a plate at rest (a constant source). */
   int storage;                /* dvm_storage; the width limits of the sweeps (nx <= 256 rows, 512
                                  columns) apply to the stored x1 axis */
   double dx1;                 /* x1 spacing; 0 = square cells (ly / ny).  Cells are dx1 x (ly / ny)

@@ -1249,8 +1249,8 @@ dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta
   dvm_ctx *c = ctx;
   if (!(tol > 0.0) || max_iter < 1) return fail(c, DVM_EINVAL, "tol must be > 0 and max_iter >= 1");
   if (!c->d_h) return fail(c, DVM_ESTATE, "dvm_adjoint needs the forward distribution (store_distribution = 1)");
-  if (c->alpha < 1.0 || c->top_u != 0.0)
-    return fail(c, DVM_EINVAL, "dvm_adjoint supports fixed, fully diffuse walls only (accommodation = 1, no moving plate)");
+  // a moving plate only adds a constant source: the transposed operator is the one of a plate at rest
+  if (c->alpha < 1.0) return fail(c, DVM_EINVAL, "dvm_adjoint supports fully diffuse walls only (accommodation = 1)");
   if (!c->square) return fail(c, DVM_EINVAL, "dvm_adjoint supports square cells only (no dx1, no row heights)");
   DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));

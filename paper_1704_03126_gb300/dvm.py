@@ -124,7 +124,7 @@ class Solver:
     torch.cuda.current_stream().cuda_stream) or None.  schedule: None (automatic), or (kind,
     shape) for set_schedule.  accommodation: alpha in [0, 1] of Eq. (diffuse2); below 1 the
     walls reflect the rest specularly (column sweep only; no adjoint).  top_wall_u1: speed of the plate
-    beyond the last row (Couette flow; column sweep only; no adjoint).  storage: "auto" (the library
+    beyond the last row (Couette flow; column sweep only).  storage: "auto" (the library
     stores a grid wider than tall transposed, so that its sweeps walk the long axis), "as_given" or
     "transposed"; arguments and results keep the [ny][nx] layout either way.  dx1: x1 spacing (0 = square
     cells ly / ny); row_heights: [ny] heights of the rows along x2 (ly becomes their sum; needs dx1 > 0,

@@ -164,3 +164,27 @@ def test_adjoint_after_a_mixed_forward_solve():
     scale = np.abs(g_ref).max()
     assert np.abs(grad - g_ref).max() < 1e-8 * scale
     assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)
+
+
+@pytest.mark.parametrize("storage", ["as_given", "transposed"])
+def test_couette_adjoint_matches_oracle(storage):
+    """Gradient of the Couette flow rate (plate moving with U = 1 over a notched wall, no force) with
+    respect to a per-cell collision rate: the GPU adjoint against the oracle's adjoint at its own
+    converged state."""
+    mask = np.zeros((10, 8), np.uint8)
+    mask[0:2, 3] = 1
+    mask[0, 5] = 1
+    d = _delta_field(mask, 1.2, 5)
+    quad = ("cubic", 8, 4.0)
+    sol = dvm.Solver(mask, True, False, delta=1.2, quad=quad, precision="fp64", store_distribution=True, force=0.0,
+                     top_wall_u1=1.0, storage=storage)
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=200000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=200000)
+    p = oracle.Problem.make(mask, True, False, d, quad, force=0.0, top_u=1.0)
+    ref = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_ref, _, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=400000)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale
+    assert abs(q_id) < 1e-14

@@ -454,8 +454,13 @@ def test_moving_plate_restrictions():
         sol.set_schedule("rows")
     assert ei.value.status == dvm.DVM_EINVAL
     sol.solve(tol=1e-10)
+    grad, q_id, iters = sol.adjoint()  # the plate is a constant source: the adjoint is a rest plate's
+    assert np.all(np.isfinite(grad)) and abs(q_id) < 1e-14  # no force: F sum z v1 = 0
+    spec = dvm.Solver(inputs.plates_mask(4, 8), True, False, kn=1.0, quad=("gh", 4, 0.0), force=0.0,
+                      top_wall_u1=1.0, store_distribution=True, accommodation=0.7)
+    spec.solve(tol=1e-10)
     with pytest.raises(dvm.DvmError) as ei:
-        sol.adjoint()
+        spec.adjoint()
     assert ei.value.status == dvm.DVM_EINVAL
 
 

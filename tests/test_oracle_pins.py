@@ -439,3 +439,32 @@ def test_couette_mean_profile_integrates_to_the_flow_rate():
     assert np.max(np.abs(ub + ub[::-1] - 2 * m0m2)) < 1e-10
     assert abs(couette.profile_at(y, ub, [0.5])[0] - m0m2) < 1e-10
     assert abs(couette.q_star(0.45, 0.5) - 0.9) < 1e-15
+
+
+def test_couette_adjoint_matches_dense_transpose_and_differences():
+    """The moving plate only adds a constant source, so the adjoint operator is the one of a plate at
+    rest: the iterative adjoint at the Couette state matches the dense transposed solve and central
+    differences of dense Couette solves (the Q identity is F sum z v1 = 0 here: no force)."""
+    mask = np.zeros((8, 6), np.uint8)
+    mask[0:2, 2] = 1
+    dfield = np.full((8, 6), 1.1)
+    dfield[3, 4] = 0.6
+    p = oracle.Problem.make(mask, True, False, dfield, ("gh", 6, 0.0), force=0.0, top_u=1.0)
+    ds = dense.solve(p)
+    g_dense = dense.adjoint_gradient(p, ds)
+    r = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_it, q_id, iters, ok = oracle.adjoint(p, r["h"], r["c"], tol=1e-13, max_iter=400000)
+    assert ok
+    scale = np.abs(g_dense).max()
+    assert scale > 0.0
+    assert np.max(np.abs(g_it - g_dense)) < 1e-9 * scale
+    assert abs(q_id) < 1e-14
+    for (j, i) in [(3, 4), (6, 1), (2, 3)]:
+        step = 1e-5 * dfield[j, i]
+        qs = []
+        for sgn in (1, -1):
+            d = dfield.copy()
+            d[j, i] += sgn * step
+            qs.append(dense.solve(oracle.Problem.make(mask, True, False, d, ("gh", 6, 0.0), force=0.0,
+                                                       top_u=1.0))["Q"])
+        assert abs((qs[0] - qs[1]) / (2 * step) - g_dense[j, i]) < 1e-6 * scale
