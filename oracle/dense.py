@@ -182,7 +182,8 @@ def adjoint_gradient(prob, sol=None):
     G = len(gas_cells)
     n = K * G
     g = np.zeros(n + 1)
-    dA_over_L = prob.dx * prob.dx / (nx * prob.dx)
+    rows = prob.row_heights()
+    dA_over_L = np.array([prob.dx * rows[j] / (nx * prob.dx) for (i, j) in gas_cells])  # dA = dx dy_j
     for k in range(K):
         g[k * G:(k + 1) * G] = W[k] * v1[k] * dA_over_L
     lam = np.linalg.solve(B.T, g)

@@ -557,6 +557,45 @@ int orc_sweep_selected(const orc_problem *p, const double *h_in, double c_shift,
  * Identity at convergence: Q = F sum z v1.
  */
 
+/* Coefficients of the forward stencil of gas cell (i, j) along one axis (step (di, dj), sign s), in the
+ * normalised form v_a dh/dx_a = (|v_a|/dx) (kap h0 - w1 ref1 - w2 ref2): returns 2 when ref1 is the wall
+ * value (u1 solid), 1 for first order (ref1 = h(u1)), 0 for the interior form (ref1 = h(u1), ref2 =
+ * h(u2)).  Rows of unequal height give the Lagrange forms of upwind_axis scaled by dx. */
+static int stencil_weights(const orc_problem *p, int i, int j, int di, int dj, int s, double *kap, double *w1,
+                           double *w2) {
+  int i1 = i - s * di, j1 = j - s * dj, i2 = i - 2 * s * di, j2 = j - 2 * s * dj;
+  *w2 = 0.0;
+  if (p->dy && dj != 0) {
+    double hc = p->dy[j];
+    if (solid_at(p, i1, j1)) {
+      *kap = *w1 = 2.0 / hc * p->dx;
+      return 2;
+    }
+    double d1 = 0.5 * (hc + p->dy[wrap(j1, p->ny)]);
+    if (solid_at(p, i2, j2)) {
+      *kap = *w1 = p->dx / d1;
+      return 1;
+    }
+    double d2 = d1 + 0.5 * (p->dy[wrap(j1, p->ny)] + p->dy[wrap(j2, p->ny)]);
+    *kap = p->dx * (1.0 / d1 + 1.0 / d2);
+    *w1 = p->dx * d2 / (d1 * (d2 - d1));
+    *w2 = -p->dx * d1 / (d2 * (d2 - d1));
+    return 0;
+  }
+  if (solid_at(p, i1, j1)) {
+    *kap = *w1 = 2.0;
+    return 2;
+  }
+  if (solid_at(p, i2, j2)) {
+    *kap = *w1 = 1.0;
+    return 1;
+  }
+  *kap = 1.5;
+  *w1 = 2.0;
+  *w2 = -0.5;
+  return 0;
+}
+
 /* Push form of the transposed upwind sweep for velocity k: acc holds lambda'_k on entry and is
  * consumed; z (output) gets T_k^{-T} lambda'_k.  Contributions through lagged references (wrapped
  * seam cells and wall values) go to lam_new (the L^T z part). */
@@ -576,12 +615,11 @@ static void adjoint_sweep_velocity(const orc_problem *p, int k, double *acc, dou
       if (p->mask[c]) continue;
       /* diagonal of the forward row for this cell */
       double diag = p->delta[c];
-      double kap[2];
+      double kap[2], w1[2], w2[2];
+      int cls[2];
       for (int ax = 0; ax < 2; ++ax) {
         int di = ax == 0, dj = ax == 1, s = ax == 0 ? s1 : s2;
-        if (solid_at(p, i - s * di, j - s * dj)) kap[ax] = 2.0;
-        else if (solid_at(p, i - 2 * s * di, j - 2 * s * dj)) kap[ax] = 1.0;
-        else kap[ax] = 1.5;
+        cls[ax] = stencil_weights(p, i, j, di, dj, s, &kap[ax], &w1[ax], &w2[ax]);
         diag += cxy[ax] * kap[ax];
       }
       double z = acc[c] / diag;
@@ -597,17 +635,17 @@ static void adjoint_sweep_velocity(const orc_problem *p, int k, double *acc, dou
         double ref_coef[2];
         int wrapped1 = (ax == 0) ? (i1 < 0 || i1 >= p->nx) : (j1 < 0 || j1 >= p->ny);
         int wrapped2 = (ax == 0) ? (i2 < 0 || i2 >= p->nx) : (j2 < 0 || j2 >= p->ny);
-        if (solid_at(p, i1, j1)) {
-          ref_cell[0] = c; ref_is_wall[0] = 1; ref_wrapped[0] = 0; ref_coef[0] = 2.0; nref = 1;
-        } else if (solid_at(p, i2, j2)) {
+        if (cls[ax] == 2) {
+          ref_cell[0] = c; ref_is_wall[0] = 1; ref_wrapped[0] = 0; ref_coef[0] = w1[ax]; nref = 1;
+        } else if (cls[ax] == 1) {
           ref_cell[0] = cell_id(p, i1, j1); ref_is_wall[0] = 0; ref_wrapped[0] = wrapped1;
-          ref_coef[0] = 1.0;
+          ref_coef[0] = w1[ax];
           nref = 1;
         } else {
           ref_cell[0] = cell_id(p, i1, j1); ref_is_wall[0] = 0; ref_wrapped[0] = wrapped1;
-          ref_coef[0] = 2.0;
+          ref_coef[0] = w1[ax];
           ref_cell[1] = cell_id(p, i2, j2); ref_is_wall[1] = 0; ref_wrapped[1] = wrapped2;
-          ref_coef[1] = -0.5;
+          ref_coef[1] = w2[ax];
           nref = 2;
         }
         for (int r = 0; r < nref; ++r) {
@@ -643,7 +681,7 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
   int K = p->nv * p->nv;
   long ngas = 0;
   for (size_t c = 0; c < ncell; ++c) ngas += !p->mask[c];
-  if (ngas == 0 || max_iter < 1 || p->dy) return ORC_EINVAL; /* square cells only */
+  if (ngas == 0 || max_iter < 1) return ORC_EINVAL;
   double sumW = 0;
   for (int k = 0; k < K; ++k) sumW += p->wv[k / p->nv] * p->wv[k % p->nv];
   double norm_side[4];
@@ -674,7 +712,7 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
     return acoef ? ORC_EINVAL : ORC_ENOMEM;
   }
   collision_coefficients(p, ginv, rho, u1, u2, tau, acoef);
-  double dA_over_L = p->dx * p->dx / (p->nx * p->dx);
+  /* g = W v1 dA / L per cell: dA = dx dy_j, L = nx dx */
   double mu = 0.0;
   double eps_ring[4] = {0, 0, 0, 0}; /* slot n % 4 holds eps_{n-4} */
   int status = ORC_ENOCONV, n;
@@ -711,7 +749,8 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
         double v1 = p->xv[k / p->nv], v2 = p->xv[k % p->nv];
         double W = p->wv[k / p->nv] * p->wv[k % p->nv];
         lam_new[(size_t)k * ncell + c] +=
-            d * W * (GZ[0] + GZ[1] * v1 + GZ[2] * v2 + GZ[3] * (v1 * v1 + v2 * v2)) + W * v1 * dA_over_L;
+            d * W * (GZ[0] + GZ[1] * v1 + GZ[2] * v2 + GZ[3] * (v1 * v1 + v2 * v2)) +
+            W * v1 * (p->dy ? p->dy[c / p->nx] : p->dx) / p->nx;
       }
     }
     mu -= dz;

@@ -411,14 +411,6 @@ def test_plane_couette_on_symmetric_unequal_rows(kn):
     assert np.max(np.abs(u1 + u1[::-1] - 2.0 * m0 * m2)) < 1e-10
 
 
-def test_unequal_rows_have_no_oracle_adjoint():
-    p = oracle.Problem.make(np.zeros((6, 3), np.uint8), True, False, 1.0, ("gh", 4, 0.0), dy=_stretched_rows(6, 1),
-                            dx1=0.1)
-    r = oracle.solve(p, tol=1e-10)
-    with pytest.raises(ValueError):
-        oracle.adjoint(p, r["h"], r["c"])
-
-
 def test_couette_mean_profile_integrates_to_the_flow_rate():
     """The mean streamwise profile (solid cells as zero) integrates to Q over the rows, on equal and on
     stretched rows over a notched wall; between smooth plates it is mirror-symmetric about m0 m2."""
@@ -467,4 +459,36 @@ def test_couette_adjoint_matches_dense_transpose_and_differences():
             d[j, i] += sgn * step
             qs.append(dense.solve(oracle.Problem.make(mask, True, False, d, ("gh", 6, 0.0), force=0.0,
                                                        top_u=1.0))["Q"])
+        assert abs((qs[0] - qs[1]) / (2 * step) - g_dense[j, i]) < 1e-6 * scale
+
+
+@pytest.mark.parametrize("top_u", [0.0, 1.0])
+def test_adjoint_on_unequal_rows_matches_dense_transpose(top_u):
+    """The adjoint on rows of unequal height (the forward Lagrange weights transposed, the flow-rate
+    functional weighted by the row heights) matches the dense transposed solve and central
+    differences of dense solves."""
+    mask = np.zeros((9, 5), np.uint8)
+    mask[0:2, 2] = 1
+    mask[8, 3] = 1
+    dy = _stretched_rows(9, 13)
+    dfield = np.full((9, 5), 1.3)
+    dfield[4, 1] = 0.7
+    kw = dict(dy=dy, dx1=0.09, force=0.0 if top_u else 1.0, top_u=top_u)
+    p = oracle.Problem.make(mask, True, False, dfield, ("gh", 6, 0.0), **kw)
+    ds = dense.solve(p)
+    g_dense = dense.adjoint_gradient(p, ds)
+    r = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_it, q_id, iters, ok = oracle.adjoint(p, r["h"], r["c"], tol=1e-13, max_iter=400000)
+    assert ok
+    scale = np.abs(g_dense).max()
+    assert np.max(np.abs(g_it - g_dense)) < 1e-9 * scale
+    if not top_u:
+        assert abs(q_id - r["Q"]) < 1e-10 * abs(r["Q"])  # Q = F sum z v1
+    for (j, i) in [(4, 1), (0, 0), (7, 4)]:
+        step = 1e-5 * dfield[j, i]
+        qs = []
+        for sgn in (1, -1):
+            d = dfield.copy()
+            d[j, i] += sgn * step
+            qs.append(dense.solve(oracle.Problem.make(mask, True, False, d, ("gh", 6, 0.0), **kw))["Q"])
         assert abs((qs[0] - qs[1]) / (2 * step) - g_dense[j, i]) < 1e-6 * scale
