@@ -326,6 +326,37 @@ def test_wm_roughness_has_the_requested_rms():
     assert mask[-1].sum() == 0  # the top rows are gas: the moving plate lies beyond the last row
 
 
+def test_wm_profile_sum_against_an_independent_series():
+    """Eq. (WM) as a plain loop over its terms (unit A) equals the generator's vectorised sum, and each
+    term's amplitude gamma^((D - 2) n) falls with the frequency for D < 2."""
+    x = np.linspace(0.0, 5.0, 37)
+    ref = np.zeros_like(x)
+    for n in range(-4, 7):
+        ref += [math.cos(2 * math.pi * 1.5 ** n * xi) * 1.5 ** (-(2 - 1.5) * n) for xi in x]
+    assert np.max(np.abs(inputs.wm_roughness(x, 1.5, 1.5, -4, 6) - ref)) < 1e-12
+    assert 1.5 ** (-(2 - 1.5) * 6) < 1.5 ** (-(2 - 1.5) * -4)
+
+
+def test_paper_grid_couette_generator():
+    """Sec. II.A's grid: 1500 equal columns over aspect 5, 60 equal rows across the band of the zero-mean
+    WM profile scaled to rms eps H, 100 equal rows above it up to the plate at x2 = H; a band cell is
+    solid exactly when its centre lies below the profile, and no cell above the band is solid."""
+    mask, dy, dx1 = inputs.couette_paper_grid()
+    assert mask.shape == (160, 1500) and abs(dx1 - 5.0 / 1500) < 1e-15
+    x = (np.arange(1500) + 0.5) * dx1
+    r = inputs.wm_roughness(x, n_max=int(math.floor(math.log(1.0 / (2 * dx1)) / math.log(1.5))))
+    r -= r.mean()
+    r *= 0.02 / math.sqrt(np.mean(r * r))
+    assert abs(math.sqrt(np.mean(r * r)) - 0.02) < 1e-15 and abs(r.mean()) < 1e-15
+    lo, hi = r.min(), r.max()
+    assert np.allclose(dy[:60], (hi - lo) / 60, rtol=0, atol=1e-15)
+    assert np.allclose(dy[60:], (1.0 - hi) / 100, rtol=0, atol=1e-15)
+    assert abs(lo + dy.sum() - 1.0) < 1e-13  # the grid spans min r .. H
+    yc = lo + np.cumsum(dy) - 0.5 * dy
+    assert np.array_equal(mask, (yc[:, None] < r[None, :]).astype(np.uint8))
+    assert mask[60:].sum() == 0 and mask[0].sum() > 0
+
+
 # ---------------------------------------------------------------- rows of unequal height (Sec. II.A grid)
 
 def _stretched_rows(ny, seed, symmetric=False):
