@@ -165,3 +165,33 @@ def test_every_entry_point_rejects_null_handles():
     # destroy functions accept NULL silently
     L.dvm_destroy(None)
     L.dvm_batch_destroy(None)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets of dvm_params, dvm_info
+    and dvm_quad as a C compiler lays them out from include/dvm.h."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"dvm_params": dvm.Params, "dvm_info": dvm.Info, "dvm_quad": dvm.Quad}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dvm.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", include, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert c_layout[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert c_layout[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
