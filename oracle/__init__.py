@@ -46,7 +46,7 @@ class _Problem(ctypes.Structure):
         ("mask", ctypes.c_void_p), ("delta", ctypes.c_void_p),
         ("nv", ctypes.c_int), ("xv", ctypes.c_void_p), ("wv", ctypes.c_void_p),
         ("alpha", ctypes.c_double), ("force", ctypes.c_double), ("top_u", ctypes.c_double),
-        ("dy", ctypes.c_void_p),
+        ("dy", ctypes.c_void_p), ("collision", ctypes.c_int),
     ]
 
 
@@ -116,11 +116,17 @@ class Problem:
     top_u: float = 0.0          # speed of the plate beyond the last row (Couette flow), 0 = at rest
     dy: np.ndarray = None       # row heights [ny] (x2 spacing), or None for square cells ly / ny
     dx1: float = None           # x1 spacing when dy is given
+    # "projection": L = delta psi . G^{-1} m, the projection onto the collision invariants in the
+    # quadrature inner product (default); "literal": Eq. BGK as printed, delta [rho + 2 u.v + tau (|v|^2 - 1)]
+    # with the quadrature moments.  They agree for a quadrature exact on psi_i psi_j f_eq.
+    collision: str = "projection"
 
     @staticmethod
     def make(mask, periodic_x, periodic_y, delta, quad=("gh", 8, 5.0), alpha=1.0, force=1.0, ly=1.0, top_u=0.0,
-             dy=None, dx1=None):
+             dy=None, dx1=None, collision="projection"):
         """dy: row heights (then ly = sum dy and dx1, the x1 spacing, must be given)."""
+        if collision not in ("projection", "literal"):
+            raise ValueError(f"unknown collision reading {collision!r}")
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         ny, nx = mask.shape
         d = np.broadcast_to(np.asarray(delta, dtype=np.float64), (ny, nx))
@@ -136,7 +142,7 @@ class Problem:
             ly = float(dy.sum())
             dx1 = float(dx1)
         return Problem(mask, bool(periodic_x), bool(periodic_y), np.ascontiguousarray(d), xv, wv,
-                       float(alpha), float(force), float(ly), float(top_u), dy, dx1)
+                       float(alpha), float(force), float(ly), float(top_u), dy, dx1, collision)
 
     @property
     def nx(self):
@@ -170,7 +176,8 @@ class Problem:
         return _Problem(self.nx, self.ny, int(self.periodic_x), int(self.periodic_y), self.dx,
                         self.mask.ctypes.data, self.delta.ctypes.data, self.nv,
                         self.xv.ctypes.data, self.wv.ctypes.data, self.alpha, self.force, self.top_u,
-                        self.dy.ctypes.data if self.dy is not None else None)
+                        self.dy.ctypes.data if self.dy is not None else None,
+                        1 if self.collision == "literal" else 0)
 
 
 def delta_from_kn(kn: float) -> float:

@@ -49,8 +49,16 @@ def derivative_weights(offsets):
     return np.linalg.solve(V, rhs)
 
 
-def collision_kernel(v1, v2, W):
-    """C[k, j] = W_j psi(v_k)^T G^{-1} psi(v_j): M_k(h) = sum_j C[k, j] h_j."""
+def collision_kernel(v1, v2, W, collision="projection"):
+    """C[k, j] with M_k(h) = sum_j C[k, j] h_j.
+
+    projection: C[k, j] = W_j psi(v_k)^T G^{-1} psi(v_j) (the W-orthogonal projection onto the
+    collision invariants); literal: Eq. BGK as printed, rho + 2 u.v_k + tau (|v_k|^2 - 1) with
+    rho = sum W h, u = sum W v h, tau = sum W (|v|^2 - 1) h, i.e.
+    C[k, j] = W_j [1 + 2 v_k . v_j + (|v_k|^2 - 1)(|v_j|^2 - 1)]."""
+    if collision == "literal":
+        e = v1 * v1 + v2 * v2 - 1.0
+        return (1.0 + 2.0 * (np.outer(v1, v1) + np.outer(v2, v2)) + np.outer(e, e)) * W[None, :]
     psi = np.stack([np.ones_like(v1), v1, v2, v1 * v1 + v2 * v2])  # [4][K]
     G = (psi * W[None, :]) @ psi.T
     return (psi.T @ np.linalg.inv(G) @ psi) * W[None, :]
@@ -73,7 +81,7 @@ def assemble(prob):
     dx = prob.dx
     rows = prob.row_heights()
     nv = prob.nv
-    Ckern = collision_kernel(v1, v2, W)
+    Ckern = collision_kernel(v1, v2, W, getattr(prob, "collision", "projection"))
     # wall normalisers per side: W (normal +x), E (-x), S (+y), N (-y)
     normal = {"W": (1.0, 0.0), "E": (-1.0, 0.0), "S": (0.0, 1.0), "N": (0.0, -1.0)}
     vn = {s: v1 * nxy[0] + v2 * nxy[1] for s, nxy in normal.items()}
@@ -187,7 +195,7 @@ def adjoint_gradient(prob, sol=None):
     for k in range(K):
         g[k * G:(k + 1) * G] = W[k] * v1[k] * dA_over_L
     lam = np.linalg.solve(B.T, g)
-    Ckern = collision_kernel(v1, v2, W)
+    Ckern = collision_kernel(v1, v2, W, getattr(prob, "collision", "projection"))
     grad = np.zeros((ny, nx))
     c = x[-1]
     for gi, (i, j) in enumerate(gas_cells):

@@ -171,6 +171,8 @@ typedef struct {
   double force;              /* body-force source coefficient F (source F v1) */
   double top_u;              /* speed U along x1 of the plate beyond the last row (Couette), or 0 */
   const double *dy;          /* row heights [ny] (x2 spacing), or NULL: square cells of size dx */
+  int collision;             /* 0: projection onto the collision invariants (default); 1: Eq. BGK as
+                                printed, delta [rho + 2 u.v + tau (|v|^2 - 1)] with quadrature moments */
 } orc_problem;
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
@@ -248,15 +250,22 @@ static int gram_inverse(const orc_problem *p, double ginv[16]) {
   return 1;
 }
 
-/* Collision coefficients a = G^{-1} m of every gas cell from the moments (m = rho, u1, u2, tau + rho). */
+/* Collision coefficients a of every gas cell in the basis psi = (1, v1, v2, |v|^2), so that
+ * L = delta sum_i a_i psi_i(v):
+ *   projection (collision = 0): a = G^{-1} m with m = (rho, u1, u2, tau + rho);
+ *   literal    (collision = 1): Eq. BGK as printed, rho + 2 u.v + tau (|v|^2 - 1), i.e.
+ *                               a = (rho - tau, 2 u1, 2 u2, tau).
+ * The two coincide when the quadrature integrates psi_i psi_j f_eq exactly. */
 static void collision_coefficients(const orc_problem *p, const double ginv[16], const double *rho,
                                    const double *u1, const double *u2, const double *tau, double *a) {
   size_t ncell = (size_t)p->nx * p->ny;
   for (size_t c = 0; c < ncell; ++c) {
     double m[4] = {rho[c], u1[c], u2[c], tau[c] + rho[c]};
+    double lit[4] = {rho[c] - tau[c], 2.0 * u1[c], 2.0 * u2[c], tau[c]};
     for (int i = 0; i < 4; ++i) {
       double s = 0;
       for (int j = 0; j < 4; ++j) s += ginv[i * 4 + j] * m[j];
+      if (p->collision == 1) s = lit[i];
       a[c * 4 + i] = p->mask[c] ? 0.0 : s;
     }
   }
@@ -681,7 +690,8 @@ int orc_adjoint(const orc_problem *p, const double *h, double c_shift, double to
   int K = p->nv * p->nv;
   long ngas = 0;
   for (size_t c = 0; c < ncell; ++c) ngas += !p->mask[c];
-  if (ngas == 0 || max_iter < 1) return ORC_EINVAL;
+  /* the transposed collision below is that of the projection (collision = 0) */
+  if (ngas == 0 || max_iter < 1 || p->collision != 0) return ORC_EINVAL;
   double sumW = 0;
   for (int k = 0; k < K; ++k) sumW += p->wv[k / p->nv] * p->wv[k % p->nv];
   double norm_side[4];
