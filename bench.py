@@ -1,18 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the DVM source iteration (linearized BGK, arXiv:1704.03126 Sec. II.A) on GB300.
 
-Default workload (--workload rough): force-driven flow through the rough channel -- 128 x 128 cells,
-periodic along x1, diffuse plates with one 26 x 32 block per wall, 32 x 32 trapezoid velocities on
-[-5, 5]^2 -- at Kn = 0.1, 1 and 10, the three instances advanced together.  One step = one source
-iteration of all three (transport sweep with fused moments and wall fluxes, mass projection,
-residual, flow rate), i.e. 3 x 14720 gas cells x 1024 velocities = 45.2 M cell-velocity updates.
+Default workload (--workload batched): 64 seeded instances -- sides 64 to 256, rough channels or
+periodic disk media, Kn log-uniform in [0.01, 10], cubic velocity grids of 16 to 48 nodes per axis
+(Eq. nonuniform_v) -- advanced together, FP32 storage with FP64 moments.  One step = one source
+iteration of every instance (transport sweep with fused moments and wall fluxes, mass projection,
+residual, flow rate).  The same JSON line carries, under "workloads", the rough channel (FP32 and FP64)
+and the porous medium, each with its own roofline, end-to-end rate, time to converge and oracle
+baseline.
 
-Other workloads, one JSON line each:
+  rough    force-driven flow through the rough channel -- 128 x 128 cells, periodic along x1, diffuse
+           plates with one 26 x 32 block per wall, 32 x 32 trapezoid velocities on [-5, 5]^2 -- at
+           Kn = 0.1, 1 and 10, the three instances advanced together (45.2 M updates per step).
+Other workloads (--workload), one JSON line each:
   porous   periodic disk medium 256 x 256 (porosity 0.6, radii 8-20), cubic 48 x 48 velocities,
            Kn = 0.05, 0.5, 5 advanced together (FP32 storage).
-  batched  64 mixed instances (sides 64-256, rough or porous, Kn log-uniform in [0.01, 10], cubic
-           16-48 velocities) in one launch per kernel, sweep kernel picked by the autotuner;
-           compared with 64 plain solves.
   adjoint  porous 256 x 256 (porosity 0.5), cubic 32 x 32, Kn = 1, FP64: one step = one transposed
            (adjoint) sweep; gradient checked against central differences of forward solves.
   couette  Couette flow of Sec. II on the paper's grid: top plate moving with U = 1, no force, 1500
@@ -66,13 +68,14 @@ METRICS = {
 }
 METRIC = METRICS["rough"]
 UNIT = "updates/s"
-# FP32 / FP64 operations per interior cell-velocity update of the sweep kernel:
-# right-hand side 3 FMA, two upwind combinations 2 x (FMA + MUL), update 2 FMA + MUL, moments 4 FMA
-FLOPS_PER_UPDATE = 25
-# DRAM bytes (read + write) of one sweep-kernel launch, from an ncu capture of this benchmark's command
-# (profiles/sweep_fp32_rough128x3_kn0.1-1-10.md), keyed by (workload, precision, kernel, shape); other
-# launch configurations report null
-NCU_TRAFFIC = {("rough", "fp32", "rows", 8): 14.35e6}
+# FP32 / FP64 floating-point operations per interior cell-velocity update of the sweep kernel, counted
+# from its source: right-hand side 3 FMA, two upwind combinations 2 x 2 FMA, update FMA + MUL, moments
+# 4 FMA (FMA = 2 flops): 25.  The ncu instruction counts of the sweep (profiles/) confirm the count.
+FLOPS_PER_UPDATE = {"fp32": 25, "fp64": 25}
+# DRAM bytes (read + write) of one sweep-kernel launch from ncu, keyed by (workload, precision, kernel,
+# shape), each with the hash of the sweep kernels' sources it was measured on (kernel_source_hash);
+# a figure whose hash no longer matches is reported as null
+NCU_TRAFFIC = {}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -87,7 +90,7 @@ def parse():
     ap.add_argument("--single", action="store_true", help="time only the selected precision")
     ap.add_argument("--min-warmup-s", type=float, default=1.0,
                     help="keep warming up for at least this long (clock sampling); 0 for profiling")
-    ap.add_argument("--workload", default="rough", choices=sorted(METRICS))
+    ap.add_argument("--workload", default="batched", choices=sorted(METRICS))
     ap.add_argument("--schedule", default="autotune",
                     help="sweep kernel: autotune, rows, rows<cw> (chunk width), columns1, columns2, columns4")
     ap.add_argument("--fd-cells", type=int, default=16, help="adjoint workload: cells checked by central differences")
@@ -211,13 +214,34 @@ def updates_per_step(insts):
 
 # ------------------------------------------------------------------------------ clocks
 
+def physical_gpu_id(cuda_index):
+    """The nvidia-smi --id of CUDA device `cuda_index`: "GPU-<uuid>" from torch's device properties,
+    else the PCI bus id, else the index itself."""
+    try:
+        import torch
+        props = torch.cuda.get_device_properties(cuda_index)
+        uuid = str(getattr(props, "uuid", "") or "")
+        if uuid:
+            return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        bus = getattr(props, "pci_bus_id", None)
+        if bus is not None:
+            dom = getattr(props, "pci_domain_id", 0)
+            dev = getattr(props, "pci_device_id", 0)
+            return f"{dom:08x}:{bus:02x}:{dev:02x}.0"
+    except Exception:
+        pass
+    return str(cuda_index)
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.gpu = gpu_index
+        # nvidia-smi numbers the GPUs of the whole machine and ignores CUDA_VISIBLE_DEVICES: name the
+        # device by its UUID (from the CUDA runtime, which sees only the visible GPUs)
+        self.gpu = physical_gpu_id(gpu_index)
         self.proc = None
         # raw samples go to a scratch file; the JSON line carries their summary
         self.path = os.path.join(tempfile.gettempdir(), f"dvm_bench_clocks_{os.getpid()}.csv")
@@ -254,10 +278,72 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "gpu_id": self.gpu}
 
 
 # ------------------------------------------------------------------------------ our arm
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def device_peaks(dvm):
+    """FMA ceilings measured live on this GPU (dvm_probe_peaks, about 0.2 s each) and its L2 size."""
+    out = {}
+    for kind in ("fp32", "fp32x2", "fp64"):
+        tf, l2, sms = dvm.probe_peaks(kind, 0.2)
+        out[kind] = tf
+    out["l2_bytes"] = l2
+    out["sms"] = sms
+    return out
+
+
+def kernel_source_hash():
+    """Hash of the sweep kernels' sources: a recorded DRAM-traffic figure holds only for this hash."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1704_03126_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.startswith("dvm_sweep") or name in ("dvm_device.cuh", "dvm_kernels.h"):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def roofline(upd, sweep_ms, fin_ms, prec, sched, hbm_gbs, alu_peaks, workload):
+    """Roofline of the dominant kernel (the sweep) for one launch of `upd` cell-velocity updates.
+
+    bound hbm, "effective, fused": the algorithmic bytes of the method per update -- the source
+    iteration writes h^{n+1} once and reads it once for its moments, 2 s bytes (s = 4 FP32, 8 FP64) --
+    over the sweep kernel's CUDA-event time, against the measured HBM copy bandwidth.  The fused kernel
+    keeps h on chip, so its DRAM traffic (`traffic`, from ncu) is far below those bytes; the ALU fraction
+    against the measured FMA rate is given beside it."""
+    bpu = 8 if prec == "fp32" else 16
+    achieved = upd * bpu / (sweep_ms / 1e3) / 1e9
+    kname = (f"sweep_kernel, chunk width {sched['shape']}" if sched["kernel"] == "rows"
+             else f"cols_kernel, {sched['shape']} thread(s) per column")
+    rec = NCU_TRAFFIC.get((workload, prec, sched["kernel"], sched["shape"]))
+    src = kernel_source_hash()
+    traffic = rec["bytes"] if rec is not None and rec["src"] == src else None
+    alu_key = "fp32" if prec == "fp32" else "fp64"
+    alu_ach = FLOPS_PER_UPDATE[prec] * upd / (sweep_ms / 1e3) / 1e12
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+            "traffic": traffic,
+            "basis": f"effective, fused: {bpu} B per cell-velocity update (write + read of h that a non-fused "
+                     f"iteration needs) x {upd} updates per launch / sweep-kernel CUDA-event time; peak = "
+                     f"MEASURED_PEAKS hbm_gbs (of measured)",
+            "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of this kernel build"
+                             if traffic is not None else
+                             "null: no ncu capture of this launch configuration for the current kernel sources"),
+            "kernel": f"{kname} ({prec})", "schedule": sched, "sweep_ms": sweep_ms, "finalize_ms": fin_ms,
+            "updates_per_launch": upd, "kernel_src": src,
+            "alu": {"achieved": alu_ach, "peak": alu_peaks[alu_key], "unit": "TFLOP/s",
+                    "frac": alu_ach / alu_peaks[alu_key], "flops_per_update": FLOPS_PER_UPDATE[prec],
+                    "peak_note": f"{alu_key.upper()} FMA chains measured live by dvm_probe_peaks (of measured)"}}
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -269,15 +355,13 @@ def run_ours(args, rank, world, local_rank):
     # private stream): the solvers, the L2 flush and the CUDA events all run on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    insts = instances(args.workload)
-    upd = updates_per_step(insts)
-
-    def make(precision):
-        return [solver(dvm, inst, precision, stream.cuda_stream, anderson=args.anderson) for inst in insts]
-
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peaks = load_peaks()
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    alu = device_peaks(dvm)
+    torch.cuda.synchronize()
 
-    def timed_steps(batch, steps, warmup, sampler=None):
+    def timed_steps(batch, steps, warmup):
         t_end = time.perf_counter() + args.min_warmup_s
         w = 0
         while w < warmup or time.perf_counter() < t_end:  # at least `warmup` steps and ~1 s of load
@@ -308,92 +392,88 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         total = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-        return total, sweep_ms, fin_ms, w
+        return total, float(np.mean(sweep_ms)), float(np.mean(fin_ms)), w
 
-    results = {}
+    def measure(workload, precision, steps, warmup, sampler=None):
+        insts = instances(workload)
+        upd = updates_per_step(insts)
+        solvers = [solver(dvm, inst, precision, stream.cuda_stream, anderson=args.anderson) for inst in insts]
+        batch = dvm.Batch(solvers)
+        sched = apply_schedule(batch, args.schedule)
+        total_ms, sweep_ms, fin_ms, wsteps = timed_steps(batch, steps, warmup)
+        clocks = sampler.stop() if sampler is not None else None
+        total_ms = max_over_ranks(total_ms, world, device="cuda")
+        return dict(workload=workload, precision=precision, insts=insts, upd=upd, solvers=solvers, batch=batch,
+                    sched=sched, total_ms=total_ms, sweep_ms=sweep_ms, fin_ms=fin_ms, warmup_steps=wsteps,
+                    kernels_per_step=batch.kernels_per_sweep(), steps=steps, clocks=clocks,
+                    value=job_value(world, steps, upd, total_ms),
+                    roofline=roofline(upd, sweep_ms, fin_ms, precision, sched, hbm_gbs, alu, workload))
+
+    def close(m):
+        m["batch"].close()
+        for s in m["solvers"]:
+            s.close()
+
+    def extras(m, cpu=True, budget_s=12.0):
+        """e2e, time to converge, the CPU oracle beside it."""
+        big = len(m["insts"]) > 6
+        r = {}
+        r["e2e"] = e2e(args, m["insts"], m["precision"], stream, dvm, torch, sweeps=10 if big else 50,
+                       reps=1 if big else 3)
+        if m["workload"] == "permeability":
+            r["curves"] = curves({m["precision"]: m}, m["insts"], torch)
+        else:
+            r["converge"] = converge({m["precision"]: m}, m["insts"], torch, max_iter=10000 if big else 200000,
+                                     dvm=dvm, stream=stream.cuda_stream)
+        if cpu and rank == 0:
+            r["cpu_baseline"] = cpu_baseline(m["insts"], m["workload"], budget_s=budget_s)
+        return r
+
     sampler = ClockSampler(local_rank)
     sampler.start()
-    single = args.single or args.workload != "rough" or args.anderson > 0
-    precisions = [args.precision] + ([] if single else ["fp64" if args.precision == "fp32" else "fp32"])
-    schedules = {}
-    for precision in precisions:
-        solvers = make(precision)
-        batch = dvm.Batch(solvers)
-        schedules[precision] = apply_schedule(batch, args.schedule)
-        total_ms, sweep_ms, fin_ms, wsteps = timed_steps(batch, args.steps, args.warmup)
-        total_ms = max_over_ranks(total_ms, world, device="cuda")
-        results[precision] = dict(total_ms=total_ms, sweep_ms=float(np.mean(sweep_ms)),
-                                  fin_ms=float(np.mean(fin_ms)), warmup_steps=wsteps,
-                                  kernels_per_step=batch.kernels_per_sweep(), batch=batch, solvers=solvers)
-        if precision == args.precision:
-            clocks = sampler.stop()
-    main = results[args.precision]
-    ms_per_step = main["total_ms"] / args.steps
-    value = job_value(world, args.steps, upd, main["total_ms"])
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    # FP32: 152 SMs x 128 FMA lanes; FP64 on GB300: 2 FMA per SM per clock (measured 1.9); 2 flops per FMA
-    peak = {"fp32": 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12, "fp64": 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12}
-
-    def roofline(prec):
-        r = results[prec]
-        achieved = FLOPS_PER_UPDATE * upd / (r["sweep_ms"] / 1e3) / 1e12
-        sc = schedules[prec]
-        kname = (f"sweep_kernel, chunk width {sc['shape']}" if sc["kernel"] == "rows"
-                 else f"cols_kernel, {sc['shape']} thread(s) per column")
-        traffic = NCU_TRAFFIC.get((args.workload, prec, sc["kernel"], sc["shape"]))
-        return {"bound": "alu", "achieved": achieved, "peak": peak[prec], "unit": "TFLOP/s",
-                "frac": achieved / peak[prec], "traffic": traffic,
-                "traffic_per_update_bytes": None if traffic is None else traffic / upd,
-                "kernel": f"{kname} ({prec})", "schedule": sc, "flops_per_update": FLOPS_PER_UPDATE,
-                "peak_note": ("FP32 FMA units x max SM clock" if prec == "fp32"
-                              else "FP64 units (2 FMA/SM/clk) x max SM clock") + ", derived (of unit counts)",
-                "sweep_ms": r["sweep_ms"], "finalize_ms": r["fin_ms"]}
-
+    main = measure(args.workload, args.precision, args.steps, args.warmup, sampler)
     out = {
-        "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic", "config": dict(workload_config(args.precision, args.workload), anderson_depth=args.anderson),
-        "roofline": roofline(args.precision),
-        "clocks": clocks,
+        "metric": METRICS[args.workload], "value": main["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["total_ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": dict(workload_config(args.precision, args.workload), anderson_depth=args.anderson),
+        "roofline": main["roofline"],
+        "clocks": main["clocks"],
         # per step: the arming kernel, the sweep and the two finalize kernels (and three mixing kernels)
         "gpu_launches": args.steps * (main["kernels_per_step"] + 1),
+        "device_peaks_measured": alu,
     }
-    other = "fp64" if args.precision == "fp32" else "fp32"
-    if other in results:
-        out[other] = {"value": world * args.steps * upd / (results[other]["total_ms"] / 1e3),
-                      "ms_per_step": results[other]["total_ms"] / args.steps, "roofline": roofline(other)}
-    hbm = float(peaks.get("hbm_gbs", 6762.6)) * 1e9
-    vals = {p: world * args.steps * upd / (results[p]["total_ms"] / 1e3) for p in results}
-    out["effective_hbm_fraction"] = {
-        "note": "updates/s x bytes a non-fused sweep would move (write + read h) / measured HBM copy bandwidth",
-        **{p: vals[p] * (8 if p == "fp32" else 16) / hbm for p in vals},
-    }
-
     if not args.skip_extras:
-        big = args.workload in ("batched", "permeability")
-        out["e2e"] = e2e(args, insts, stream, dvm, torch, sweeps=10 if big else 50, reps=1 if big else 3)
-        if args.workload == "permeability":
-            out["curves"] = curves(results, insts, torch)
-        else:
-            out["converge"] = converge(results, insts, torch, max_iter=10000 if big else 200000, dvm=dvm,
-                                       stream=stream.cuda_stream)
-    if rank == 0 and not args.skip_extras:
-        out["cpu_baseline"] = cpu_baseline(insts, args.workload)
-    for r in results.values():
-        r["batch"].close()
-        for s in r["solvers"]:
-            s.close()
+        out.update(extras(main))
+    close(main)
+    # the other configurations of the method, each with its own roofline, e2e and oracle baseline
+    # (same steps and warm-up; the default line's workload is the 64-instance batch)
+    if not args.single and not args.skip_extras and args.anderson == 0:
+        others = {"batched": [("rough", "fp32"), ("rough", "fp64"), ("porous", "fp32")],
+                  "rough": [("rough", "fp64" if args.precision == "fp32" else "fp32")]}.get(args.workload, [])
+        out["workloads"] = {}
+        cpu_done = {}
+        for wl, prec in others:
+            s2 = ClockSampler(local_rank)
+            s2.start()
+            m = measure(wl, prec, args.steps, args.warmup, s2)
+            rec = {"metric": METRICS[wl], "value": m["value"], "unit": UNIT, "ms_per_step": m["total_ms"] / args.steps,
+                   "dtype": "f32" if prec == "fp32" else "f64", "config": workload_config(prec, wl),
+                   "roofline": m["roofline"], "clocks": m["clocks"],
+                   "gpu_launches": args.steps * (m["kernels_per_step"] + 1)}
+            ex = extras(m, cpu=wl not in cpu_done, budget_s=8.0)
+            if "cpu_baseline" in ex:
+                cpu_done[wl] = ex["cpu_baseline"]
+            else:
+                ex["cpu_baseline"] = cpu_done.get(wl)
+            rec.update(ex)
+            out["workloads"][f"{wl}_{prec}"] = rec
+            close(m)
     return out
 
 
-def e2e(args, insts, stream, dvm, torch, sweeps=50, reps=3):
+def e2e(args, insts, precision, stream, dvm, torch, sweeps=50, reps=3):
     """Public API with host buffers: create from the host mask (H2D), `sweeps` sweeps, flow rate and
     fields back to the host (D2H), destroy -- for every instance; wall clock."""
     torch.cuda.synchronize()
@@ -401,7 +481,7 @@ def e2e(args, insts, stream, dvm, torch, sweeps=50, reps=3):
     h2d = d2h = 0
     for _ in range(reps):
         for inst in insts:
-            s = solver(dvm, inst, args.precision, stream.cuda_stream)
+            s = solver(dvm, inst, precision, stream.cuda_stream)
             s.iterate(sweeps)
             q, _ = s.flowrate()
             f = s.fields()
@@ -463,6 +543,25 @@ def converge(results, insts, torch, max_iter=200000, dvm=None, stream=None):
             ab.close()
             for s in aa:
                 s.close()
+        if len(insts) <= 6 and dvm is not None and prec == "fp32":
+            # the FP32 path's stated error: each converged Q against the same instance in FP64 storage
+            ref = [solver(dvm, s_inst, "fp64", stream) for s_inst in insts]
+            rb = dvm.Batch(ref)
+            st64 = rb.run(tol=1e-11, max_iter=max_iter)
+            q64 = [s.flowrate()[0] for s in ref]
+            u64 = [s.fields()["u1"] for s in ref]
+            rb.close()
+            for s in ref:
+                s.close()
+            f_err = []
+            for s, u in zip(r["solvers"], u64):
+                u32 = s.fields()["u1"]
+                gas = np.isfinite(u)
+                f_err.append(float(np.abs(u32[gas] - u[gas]).max() / np.abs(u[gas]).max()))
+            out[prec]["vs_fp64"] = {
+                "fp64_tol": 1e-11, "fp64_converged": int((np.asarray(st64) == 0).sum()), "Q_fp64": q64,
+                "rel_err_Q": [abs(a - b) / abs(b) for a, b in zip(bq, q64)],
+                "max_abs_err_u1_over_max_u1": f_err}
         if len(insts) <= 6:
             out[prec]["plain"] = per
             out[prec]["batched_Q"] = bq
@@ -711,7 +810,7 @@ def run_adjoint(args, rank, world, local_rank):
         pass
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak64 = 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
-    achieved = FLOPS_PER_UPDATE * value / 1e12
+    achieved = FLOPS_PER_UPDATE["fp64"] * value / 1e12
     out = {
         "metric": METRICS["adjoint"], "value": value, "unit": UNIT, "n_gpus": world, "steps": a_iters,
         "warmup": 1, "ms_per_step": adj_ms / a_iters, "higher_is_better": True, "scaling": "weak",
@@ -719,7 +818,7 @@ def run_adjoint(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                      "frac": achieved / peak64, "traffic": None,
                      "kernel": f"transposed sweep, {sched[0]} kernel (fp64), whole adjoint iteration incl. bookkeeping",
-                     "flops_per_update": FLOPS_PER_UPDATE},
+                     "flops_per_update": FLOPS_PER_UPDATE["fp64"]},
         "clocks": clocks,
         # per adjoint sweep: transposed sweep, seam sums, two finalize kernels; plus arm, reset, gradient
         "gpu_launches": 4 * a_iters + 3,
@@ -746,6 +845,9 @@ def run_reference(args):
     import oracle
 
     insts = instances(args.workload if args.workload != "adjoint" else "rough")
+    if len(insts) > 6:
+        # a bounded sample of the batch (every eighth instance): the rate is a per-update figure
+        insts = insts[::8]
     probs = [oracle_problem(oracle, i) for i in insts]
     states = [np.zeros((i.quad[1] ** 2, p.ny, p.nx)) for i, p in zip(insts, probs)]
     upd = updates_per_step(insts)
@@ -769,7 +871,8 @@ def run_reference(args):
                        anderson_depth=args.anderson),
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} steps, each one FP64 oracle sweep of every instance"},
+                         "sample": f"{args.steps} steps, each one FP64 oracle sweep of every instance"
+                                   + (f" of a sample of {len(insts)} (every eighth)" if args.workload == "batched" else "")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -123,6 +123,18 @@ typedef struct {
                                  about 1e-7 relative, pollutes the mixing history and its residual cannot
                                  certify the distance to the fixed point).  Extra memory (2 depth + 3)
                                  doubles per state element (8 per cell plus the seams). */
+  int fp32_refine;            /* FP32 storage only: the most passes of mixed-precision refinement that
+                                 dvm_solve / dvm_batch_run add after the FP32 iteration has converged
+                                 (0 = none; default 3).  A pass takes the residual of the FP32 fixed
+                                 point with one FP64 sweep (an FP64 twin of the context, created on first
+                                 use), solves the correction equation with the FP32 iteration itself (no
+                                 force, no plate drift, the residual as its source) and adds the
+                                 correction; passes stop once the correction changes the flow velocity by
+                                 less than tol (relative, L1 over gas cells).  This removes the FP32
+                                 rounding that the iteration amplifies by 1 / (1 - r) where it converges
+                                 slowly.  Fully diffuse walls only (accommodation = 1); with
+                                 accommodation < 1 or a grid too wide for FP64 the FP32 result is returned
+                                 unrefined. */
 } dvm_params;
 
 /* The transport sweep kernel (both compute the same update; see dvm_set_schedule; nx below is the
@@ -139,10 +151,13 @@ typedef enum { DVM_SWEEP_AUTO = 0, DVM_SWEEP_ROWS = 1, DVM_SWEEP_COLUMNS = 2 } d
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
  * accommodation 1, FP64, force 1, no stored distribution, automatic sweep shape, plates at rest,
- * automatic storage, square cells, equal rows. */
+ * automatic storage, square cells, equal rows, no mixing, up to 3 refinement passes for FP32. */
 dvm_status dvm_params_init(dvm_params *params);
 
-/* Build a solver for one geometry.
+/* Build a solver for one geometry: the Cartesian staircase approximation of the channel walls or the
+ * porous solids (Sec. II.A: rough surfaces are approximated by a staircase of grid cells; Sec. III:
+ * the porous media on the same kind of grid), with the collision rate delta = sqrt(pi) / (2 Kn) of
+ * Eq. (BGK) and the velocity grid of params->quad.
  *   mask      host, uint8 [ny][nx]; nonzero = solid cell.  At least one gas cell.
  *   params    host; copied.
  *   stream    a cudaStream_t on the current device, or NULL.
@@ -152,8 +167,10 @@ dvm_status dvm_params_init(dvm_params *params);
 dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *stream, dvm_ctx **out);
 
 /* Per-cell collision rate delta_c (host, double [ny][nx], >= 0; solid entries ignored), or NULL to
- * return to the uniform value of the parameters.  Resets the state to h = 0.  This is the field the
- * adjoint differentiates. */
+ * return to the uniform value of the parameters: the coefficient delta in front of the collision
+ * term of Eq. (BGK), sqrt(pi) / (2 Kn) for a uniform gas (Sec. II.A), here allowed to vary by cell as
+ * a wall-distance-dependent relaxation time would make it.  Resets the state to h = 0.  This is the
+ * field the adjoint differentiates. */
 dvm_status dvm_set_delta_field(dvm_ctx *ctx, const double *delta_c);
 
 /* Restart from h = 0 (the state a new context has). */
@@ -165,9 +182,11 @@ dvm_status dvm_reset(dvm_ctx *ctx);
  * and eps_n / (1 - r) < tol (an estimate of the relative distance to the fixed point; the paper
  * stops on eps_n < 1e-5, Sec. II.A).  With FP32 storage eps_n stalls at the rounding noise floor,
  * where r says nothing, so the test also passes when eps_n < tol and no sweep of the last 16 gave a
- * smaller eps; tol should then stay above about 1e-6.  iters (may be NULL) receives the sweeps run
- * by this call,
- * est (may be NULL) the last estimate.  Returns DVM_ENOCONV if max_iter is reached. */
+ * smaller eps; tol should then stay above about 1e-6.  With FP32 storage and fp32_refine > 0 the
+ * converged FP32 state is then refined (see dvm_params.fp32_refine).  iters (may be NULL) receives the
+ * FP32 or FP64 sweeps run by this call (refinement: the FP32 sweeps of every phase; the one FP64
+ * residual sweep per pass is not counted), est (may be NULL) the last estimate (refinement: the relative
+ * size of the last correction).  Returns DVM_ENOCONV if max_iter is reached. */
 dvm_status dvm_solve(dvm_ctx *ctx, double tol, int max_iter, int *iters, double *est);
 
 /* Run exactly n sweeps with no stopping test (timing and warm-up).  Synchronises the stream. */
@@ -270,7 +289,7 @@ dvm_status dvm_batch_solve(dvm_ctx *const *ctxs, int n, double tol, int max_iter
 
 /* Moments and flow rate of a distribution held by the caller (the plain, unfused form of the moment
  * reduction: Sec. II.A moments, Sec. III Eq. Q).
- *   q         host; the velocity grid of h (n nodes per axis, n <= 64).
+ *   q         host; the velocity grid of h (n nodes per axis, n even, 2 <= n <= 64).
  *   h         device, double [n*n][ncell]: velocity k = a*n + b (v = (x_a, x_b)) is row k.
  *   mask      device, uint8 [ncell], nonzero = solid (excluded from Q, moments 0), or NULL.
  *   ncell     number of cells (>= 1).
@@ -289,14 +308,16 @@ dvm_status dvm_moments(const dvm_quad *q, const double *h, const uint8_t *mask, 
  * use dvm_moments.  The paper has no counterpart: this is a deployment variant of the reduction above.
  * Arguments and results are those of dvm_moments.  Differences:
  *   - scratch is a fixed device array of about 8.3 KB inside the library, present on every device
- *     that loads it until the process exits; ncell may be at most 16,777,216 (DVM_EINVAL beyond,
- *     message in dvm_last_error(NULL));
+ *     that loads it until the process exits;
+ *   - ncell may be at most 16,777,216, a maximum this call sets for itself (the scratch would serve
+ *     any count): DVM_EINVAL beyond, message in dvm_last_error(NULL);
  *   - the call is asynchronous on `stream` (results are ready when the stream reaches them);
  *   - every call shares the array: calls that overlap on one device (for example on two streams)
  *     race and must be serialised by the caller;
- *   - the first call on a device looks up the array's address with that device current; make that
- *     first call before any stream capture.
- * Errors are reported through dvm_last_error(NULL). */
+ *   - the first call in a CUDA context looks up the array's address with that context current; make
+ *     that first call before any stream capture.  After cudaDeviceReset (or a released and re-created
+ *     primary context) the next call looks it up again.
+ * Errors are reported through dvm_last_error(NULL), including the reason an argument was rejected. */
 dvm_status dvm_moments_noalloc(const dvm_quad *q, const double *h, const uint8_t *mask, int ncell,
                                double dA_over_L, double *mom, double *Q, void *stream);
 
@@ -316,6 +337,15 @@ const char *dvm_status_string(dvm_status status);
  * flag was seen: impossible unless the primitive is broken), DVM_EINVAL or DVM_ECUDA; seconds (may be
  * NULL) receives the call's wall time.  The paper has no counterpart. */
 dvm_status dvm_selftest_wait(int primitive, int spin_limit, double *seconds);
+
+/* Measured arithmetic ceiling of the current GPU, for the roofline of the sweeps (the fused sweep keeps
+ * h on chip, so its bound is the SM's FMA rate): kind 0 = FP32 FMA, 1 = packed FP32x2 FMA, 2 = FP64
+ * FMA.  Every thread of a grid of 8 blocks of 256 threads per SM runs 8 independent FMA chains (no
+ * memory traffic) for about `seconds` (0 < seconds <= 10); tflops (required) receives 2 x FMAs / the
+ * kernel's CUDA-event time in TFLOP/s, l2_bytes and sms (may be NULL) the device's L2 size and SM
+ * count.  Runs on the current device's legacy default stream and synchronises it.  Returns DVM_OK,
+ * DVM_EINVAL or DVM_ECUDA.  The paper has no counterpart. */
+dvm_status dvm_probe_peaks(int kind, double seconds, double *tflops, int *l2_bytes, int *sms);
 
 /* Release the context and its device memory.  NULL is ignored. */
 void dvm_destroy(dvm_ctx *ctx);

@@ -76,6 +76,15 @@ struct dvm_ctx {
   InstanceDesc *a_desc = nullptr;
   cudaGraphExec_t a_graph = nullptr;
   int a_graph_iters = 0;
+  // mixed-precision refinement of FP32 storage (dvm_refine.cu): the caller's inputs (to build the FP64
+  // twin), the twin, and the state buffers, all created on first use
+  std::vector<uint8_t> mask_user;
+  std::vector<double> rows_user, delta_user;
+  dvm_ctx *twin = nullptr;
+  double *r_state = nullptr;       // snapshot [8 ncell + 1] | rho [8 ncell + 1] | scalars [4] | sums [2]
+  void *r_seam = nullptr;          // snapshot seams | rho seams, storage precision
+  size_t r_nseam = 0;
+  bool refine_unavailable = false;
 };
 
 // A set of contexts advanced together: one launch of each kernel per sweep, replayed as CUDA graphs.
@@ -94,6 +103,7 @@ struct dvm_batch {
   bool anderson = false;             // some member mixes its iterates (3 more kernels per sweep)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timed = false;
+  std::vector<InstanceDesc> hdescs;  // the members' descriptors as uploaded to d_descs
 };
 
 namespace {
@@ -320,6 +330,10 @@ void release_device(dvm_ctx *c) {
   free_dev(c->a_grad);
   free_dev(c->a_state);
   free_dev(c->a_desc);
+  if (c->twin) dvm_destroy(c->twin);
+  c->twin = nullptr;
+  free_dev(c->r_state);
+  free_dev(c->r_seam);
 }
 
 dvm_status reset_state(dvm_ctx *c) {
@@ -497,6 +511,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
       return fail(c0, DVM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
     }                                                                                            \
   } while (0)
+  b->hdescs = descs;
   BATCH_CUDA(cudaMalloc(&b->d_descs, sizeof(InstanceDesc) * n));
   BATCH_CUDA(cudaMalloc(&b->d_smap, sizeof(int) * smap.size()));
   BATCH_CUDA(cudaMalloc(&b->d_fmap, sizeof(int) * fmap.size()));
@@ -639,6 +654,170 @@ dvm_status ensure_self(dvm_ctx *c) {
   return batch_build(one, 1, &c->self);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Mixed-precision refinement of FP32 storage (kernels and the method in dvm_refine.cu).
+
+constexpr double kCorrectionTol = 1e-3;  // relative tolerance of each correction solve (on |d|)
+
+// Doubles per state region of the refinement buffers: 8 ncell + 1 rounded up to a multiple of four.
+size_t refine_state_stride(int ncell) { return ((size_t)8 * ncell + 1 + 3) & ~(size_t)3; }
+
+// The FP64 twin of an FP32 context (same grid, walls, drive, collision-rate field) and the state buffers.
+dvm_status ensure_refine(dvm_ctx *c) {
+  if (c->refine_unavailable) return DVM_EINVAL;
+  if (!c->twin) {
+    dvm_params P = c->P;
+    P.precision = DVM_FP64;
+    P.store_distribution = 0;
+    P.anderson_depth = 0;
+    P.fp32_refine = 0;
+    P.row_heights = c->rows_user.empty() ? nullptr : c->rows_user.data();
+    const std::string saved = g_create_error;
+    dvm_ctx *t = nullptr;
+    dvm_status st = dvm_create(c->mask_user.data(), &P, c->stream, &t);
+    if (st != DVM_OK) {
+      c->refine_unavailable = true;
+      c->err = "refinement unavailable: the FP64 twin could not be created (" + g_create_error + ")";
+      g_create_error = saved;
+      return st;
+    }
+    if (!c->uniform) {
+      st = dvm_set_delta_field(t, c->delta_user.data());
+      if (st != DVM_OK) {
+        dvm_destroy(t);
+        c->refine_unavailable = true;
+        return st;
+      }
+    }
+    c->twin = t;
+  }
+  if (!c->r_state) {
+    c->r_nseam = refine_seam_count(c->hdesc);
+    DVM_CUDA(c, cudaMalloc(&c->r_state, sizeof(double) * (2 * refine_state_stride(c->ncell) + 8)));
+    DVM_CUDA(c, cudaMalloc(&c->r_seam, (c->fp64 ? 8 : 4) * std::max<size_t>(2 * c->r_nseam, 1)));
+  }
+  return DVM_OK;
+}
+
+// After an FP32 batch has converged: up to fp32_refine passes of residual (FP64 twin sweep), correction
+// solve (FP32, no drive, residual injected after each projection) and update.  Members whose walls are
+// partially specular, or whose twin cannot be built, leave the batch unrefined (DVM_OK).
+dvm_status batch_refine(dvm_batch *b, double tol, int max_iter) {
+  if (b->fp64 || b->ctxs.empty()) return DVM_OK;
+  dvm_ctx *c0 = b->ctxs[0];
+  int passes = 0;
+  for (dvm_ctx *c : b->ctxs) {
+    if (c->alpha < 1.0 || c->P.fp32_refine <= 0) return DVM_OK;
+    passes = std::max(passes, c->P.fp32_refine);
+  }
+  for (dvm_ctx *c : b->ctxs)
+    if (ensure_refine(c) != DVM_OK) return DVM_OK;
+  const int n = (int)b->ctxs.size();
+  std::vector<dvm_ctx *> tw(n);
+  for (int i = 0; i < n; ++i) tw[i] = b->ctxs[i]->twin;
+  dvm_batch *tb = nullptr;
+  dvm_status st = batch_build(tw.data(), n, &tb);
+  if (st != DVM_OK) {
+    c0->err = "refinement: " + tw[0]->err;
+    return st;
+  }
+  cudaStream_t s = b->stream;
+  auto bufs = [&](dvm_ctx *c, double **snap, double **rho, double **sc, double **sums, void **sseam, void **rseam) {
+    // the kernels read the moment part of snapshot and rho as 32-byte vectors: every region starts on a
+    // multiple of four doubles (the allocation itself is 256-byte aligned)
+    const size_t nstate = refine_state_stride(c->ncell);
+    *snap = c->r_state;
+    *rho = c->r_state + nstate;
+    *sc = c->r_state + 2 * nstate;
+    *sums = c->r_state + 2 * nstate + 4;
+    *sseam = c->r_seam;
+    *rseam = static_cast<char *>(c->r_seam) + 4 * c->r_nseam;
+  };
+  std::vector<double> sums(2 * n);
+  dvm_status result = DVM_OK;
+  for (int pass = 0; pass < passes && result == DVM_OK; ++pass) {
+    for (int i = 0; i < n; ++i) {
+      dvm_ctx *c = b->ctxs[i];
+      double *snap, *rho, *sc, *sm;
+      void *sseam, *rseam;
+      bufs(c, &snap, &rho, &sc, &sm, &sseam, &rseam);
+      DVM_CUDA(c0, launch_refine_snapshot(b->d_descs + i, b->hdescs[i], false, snap, sseam, sc, s));
+      DVM_CUDA(c0, launch_refine_load_twin(b->d_descs + i, tb->d_descs + i, b->hdescs[i], false, s));
+      DVM_CUDA(c0, launch_records(tb->d_descs + i, c->ncell, true, s));
+    }
+    DVM_CUDA(c0, cudaStreamSynchronize(s));
+    st = batch_iterate(tb, 1);  // rho = G(x~) - x~ needs one FP64 sweep from x~
+    if (st != DVM_OK) {
+      c0->err = "refinement residual sweep: " + tw[0]->err;
+      result = st;
+      break;
+    }
+    for (int i = 0; i < n; ++i) {
+      dvm_ctx *c = b->ctxs[i];
+      double *snap, *rho, *sc, *sm;
+      void *sseam, *rseam;
+      bufs(c, &snap, &rho, &sc, &sm, &sseam, &rseam);
+      DVM_CUDA(c0, launch_refine_residual(b->d_descs + i, tb->d_descs + i, b->hdescs[i], false, snap, sseam, sc, rho,
+                                          rseam, s));
+      // the correction phase: the member's descriptor without drive and with rho, its state d = 0
+      InstanceDesc cd = b->hdescs[i];
+      cd.force = 0.0;
+      cd.top_u = 0.0;
+      cd.rho = rho;
+      cd.rho_seam_x = rseam;
+      cd.rho_seam_y = static_cast<char *>(rseam) + 4 * (cd.periodic_x ? (size_t)c->ngroups * c->ny * 2 * kLanes : 0);
+      DVM_CUDA(c0, cudaMemcpyAsync(b->d_descs + i, &cd, sizeof(InstanceDesc), cudaMemcpyHostToDevice, s));
+      const size_t ts = 4;
+      DVM_CUDA(c0, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * 4 * c->ncell, s));
+      DVM_CUDA(c0, cudaMemsetAsync(c->d_facc, 0, sizeof(double) * 8 * c->ncell, s));
+      DVM_CUDA(c0, cudaMemsetAsync(c->d_mom, 0, sizeof(double) * 4 * c->ncell, s));
+      DVM_CUDA(c0, cudaMemsetAsync(c->d_u1prev, 0, sizeof(double) * c->ncell, s));
+      DVM_CUDA(c0, cudaMemsetAsync(c->d_seamx, 0, ts * c->ngroups * c->ny * 2 * kLanes, s));
+      DVM_CUDA(c0, cudaMemsetAsync(c->d_seamy, 0, ts * c->ngroups * c->nx * 2 * kLanes, s));
+      DVM_CUDA(c0, launch_reset(b->d_descs + i, c->ncell, false, s));
+    }
+    DVM_CUDA(c0, cudaStreamSynchronize(s));
+    std::vector<dvm_status> per(n);
+    st = batch_run(b, kCorrectionTol, max_iter, per.data(), nullptr, nullptr);
+    // back to the members' own descriptors, then x = x~ + d and the records of x with the full drive
+    for (int i = 0; i < n; ++i)
+      DVM_CUDA(c0, cudaMemcpyAsync(b->d_descs + i, &b->hdescs[i], sizeof(InstanceDesc), cudaMemcpyHostToDevice, s));
+    if (st != DVM_OK && st != DVM_ENOCONV) {
+      result = st;
+      break;
+    }
+    for (int i = 0; i < n; ++i) {
+      dvm_ctx *c = b->ctxs[i];
+      double *snap, *rho, *sc, *sm;
+      void *sseam, *rseam;
+      bufs(c, &snap, &rho, &sc, &sm, &sseam, &rseam);
+      DVM_CUDA(c0, launch_refine_combine(b->d_descs + i, b->hdescs[i], false, snap, sseam, sc, rho, sm, s));
+      DVM_CUDA(c0, launch_records(b->d_descs + i, c->ncell, false, s));
+      DVM_CUDA(c0, cudaMemcpyAsync(&sums[2 * i], sm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    DVM_CUDA(c0, cudaStreamSynchronize(s));
+    double worst = 0.0;
+    for (int i = 0; i < n; ++i) worst = std::max(worst, sums[2 * i + 1] > 0.0 ? sums[2 * i] / sums[2 * i + 1] : 0.0);
+    if (worst < tol) break;
+  }
+  batch_free(tb);
+  if (result != DVM_OK) return result;
+  if (b->store_h) {
+    // the stored distribution: one more (plain) sweep from the refined state, whose own rounding is
+    // about 1e-7 relative; the refined estimate is kept
+    std::vector<double> est(n);
+    for (int i = 0; i < n; ++i)
+      DVM_CUDA(c0, cudaMemcpyAsync(&est[i], &b->ctxs[i]->d_state->est, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DVM_CUDA(c0, cudaStreamSynchronize(s));
+    st = batch_iterate(b, 1);
+    if (st != DVM_OK) return st;
+    for (int i = 0; i < n; ++i)
+      DVM_CUDA(c0, cudaMemcpyAsync(&b->ctxs[i]->d_state->est, &est[i], sizeof(double), cudaMemcpyHostToDevice, s));
+    DVM_CUDA(c0, cudaStreamSynchronize(s));
+  }
+  return DVM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -663,6 +842,7 @@ dvm_status dvm_params_init(dvm_params *p) {
   p->sweep_warps = 0;
   p->top_wall_u1 = 0.0;
   p->storage = DVM_STORAGE_AUTO;
+  p->fp32_refine = 3;
   return DVM_OK;
 }
 
@@ -712,6 +892,7 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   if (!(P.dx1 >= 0.0) || !std::isfinite(P.dx1)) return fail(nullptr, DVM_EINVAL, "dx1 must be finite and >= 0");
   if (P.anderson_depth < 0 || P.anderson_depth > kAAMaxDepth)
     return fail(nullptr, DVM_EINVAL, "anderson_depth must be 0.." + std::to_string(kAAMaxDepth));
+  if (P.fp32_refine < 0 || P.fp32_refine > 8) return fail(nullptr, DVM_EINVAL, "fp32_refine must be 0..8");
   if (P.anderson_depth > 0 && P.accommodation < 1.0)
     return fail(nullptr, DVM_EINVAL, "Anderson mixing needs fully diffuse walls (accommodation = 1)");
   if (P.anderson_depth > 0 && P.precision != DVM_FP64)
@@ -732,7 +913,9 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
   dvm_ctx *c = new (std::nothrow) dvm_ctx();
   if (!c) return fail(nullptr, DVM_ENOMEM, "host allocation failed");
   c->P = P;
-  c->P.row_heights = nullptr;  // the caller's array is read here only
+  c->P.row_heights = nullptr;  // the caller's array is read here only (a copy is kept for the FP64 twin)
+  c->mask_user.assign(mask, mask + (size_t)P.nx * P.ny);
+  if (P.row_heights) c->rows_user.assign(P.row_heights, P.row_heights + P.ny);
   // the sweeps run along the stored x2 (column sweep: one thread per stored column; row sweep: rows in
   // flight across the stored x1), so a grid wider than tall is stored transposed by default
   // (row heights: the caller's x2 becomes the stored x1, along which every sweep thread owns a column)
@@ -1015,8 +1198,15 @@ dvm_status dvm_set_delta_field(dvm_ctx *ctx, const double *delta_c) {
                                   ctx->stream));
     DVM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->uniform = false;
+    ctx->delta_user.assign(delta_c, delta_c + ctx->ncell);
   } else {
     ctx->uniform = true;
+    ctx->delta_user.clear();
+  }
+  if (ctx->twin) {
+    // the FP64 twin of the refinement is rebuilt with the new field when next needed
+    dvm_destroy(ctx->twin);
+    ctx->twin = nullptr;
   }
   if (ctx->self) {
     batch_free(ctx->self);
@@ -1036,7 +1226,18 @@ dvm_status dvm_solve(dvm_ctx *ctx, double tol, int max_iter, int *iters, double 
   if (!(tol > 0.0)) return fail(ctx, DVM_EINVAL, "tol must be > 0");
   dvm_status st = ensure_self(ctx);
   if (st != DVM_OK) return st;
-  return batch_run(ctx->self, tol, max_iter, nullptr, iters, est);
+  DVM_CUDA(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, ctx->stream));
+  DVM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int start = ctx->h_state->iter;
+  st = batch_run(ctx->self, tol, max_iter, nullptr, iters, est);
+  if (st != DVM_OK || ctx->fp64) return st;
+  st = batch_refine(ctx->self, tol, max_iter);
+  if (st != DVM_OK) return st;
+  DVM_CUDA(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, ctx->stream));
+  DVM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (iters) *iters = ctx->h_state->iter - start;
+  if (est) *est = ctx->h_state->est;
+  return DVM_OK;
 }
 
 dvm_status dvm_iterate(dvm_ctx *ctx, int n) {
@@ -1292,7 +1493,9 @@ dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
 dvm_status dvm_batch_run(dvm_batch *batch, double tol, int max_iter, dvm_status *per) {
   if (!batch) return DVM_EINVAL;
   if (!(tol > 0.0)) return fail(batch->ctxs[0], DVM_EINVAL, "tol must be > 0");
-  return batch_run(batch, tol, max_iter, per, nullptr, nullptr);
+  dvm_status st = batch_run(batch, tol, max_iter, per, nullptr, nullptr);
+  if (st != DVM_OK || batch->fp64) return st;
+  return batch_refine(batch, tol, max_iter);
 }
 
 dvm_status dvm_batch_iterate(dvm_batch *batch, int n) {
@@ -1467,6 +1670,7 @@ dvm_status dvm_batch_solve(dvm_ctx *const *ctxs, int n, double tol, int max_iter
   dvm_status st = batch_build(ctxs, n, &b);
   if (st != DVM_OK) return st;
   st = batch_run(b, tol, max_iter, per, nullptr, nullptr);
+  if (st == DVM_OK && !b->fp64) st = batch_refine(b, tol, max_iter);
   batch_free(b);
   return st;
 }

@@ -186,6 +186,11 @@ struct InstanceDesc {
   const DeviceState *state_fwd;
   double *grad;                // [ncell] dQ / d delta_c
   AndersonDesc *aa;            // Anderson mixing state (device), or nullptr: plain source iteration
+  // Correction phase of the mixed-precision refinement (dvm_refine.cu), or nullptr: the iteration
+  // d <- P S(d) + rho with no drive.  rho = [4 ncell] moments (rho, u1, u2, tau) | [4 ncell] projected
+  // wall-face fluxes (cell * 4 + side) | [1] mass shift; rho_seam_x / _y have the layout of seam_x / _y.
+  const double *rho;
+  const void *rho_seam_x, *rho_seam_y;
 };
 
 // Launch descriptor shared by the kernels of one (possibly batched) iteration.

@@ -107,6 +107,53 @@ __device__ __forceinline__ void store_rec<double>(SweepRec<double> *dst, double 
   *dst = r;
 }
 
+// The sweep records of gas cell `cell` for all four quadrants from its moments (rho, u1, u2, tau), the
+// accumulated mass shift c, the pending shift s of the stored fluxes and the raw incident fluxes fcur
+// (with the correction phase's rho added to the projected fluxes when rho_in is set); the diagonal-
+// major copy too when `diag`.
+template <typename T>
+__device__ __forceinline__ void write_records(const InstanceDesc *D, int cell, double rho, double u1, double u2,
+                                              double tau, double c, double s, const double *fcur,
+                                              const double *rho_in, bool diag) {
+  const int ncell = D->ncell;
+  const double d = D->uniform_delta ? D->delta : D->delta_field[cell];
+  // collision coefficients a = G^{-1} m, m = (rho, u1, u2, rho + tau) = sum W psi h
+  const double m[4] = {rho, u1, u2, rho + tau};
+  double a[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    a[i] = D->ginv[i * 4] * m[0] + D->ginv[i * 4 + 1] * m[1] + D->ginv[i * 4 + 2] * m[2] + D->ginv[i * 4 + 3] * m[3];
+  // R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v_flow in the basis 1, v1, v2, |v|^2 - 1
+  const double A = d * (a[0] + a[3] - c);
+  const double B = d * a[1] + (D->flow_axis ? 0.0 : D->force);
+  const double Cc = d * a[2] + (D->flow_axis ? D->force : 0.0);
+  const double Dd = d * a[3];
+  SweepRec<T> *rec = static_cast<SweepRec<T> *>(D->rec);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double hw[2];
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+      const int src = D->hw_src[(size_t)cell * 8 + q * 2 + ax];
+      if (src >= 0) {
+        const int side = src & 3;
+        // diffuse part alpha rho_w; the specular part (1 - alpha) h(mirror v) is added in the sweep
+        const double corr = rho_in ? rho_in[(size_t)4 * ncell + src] : 0.0;
+        hw[ax] = D->alpha * (fcur[src] - s * D->ain[side] + corr) / D->nrm[side];
+      } else {
+        hw[ax] = 0.0;
+      }
+    }
+    store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+    // the diagonal-major copy only feeds the column sweep (rebuilt by sync_diag when a launch
+    // switches to it)
+    if (diag && D->rec_diag)
+      store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
+                       diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
+                   A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
   __shared__ double sh[32];
@@ -117,7 +164,9 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
   const int ncell = D->ncell;
   const int cell = (map & 0xffff) * kFinBlock + threadIdx.x;
   const double s = st->s_new;
-  const double c_new = st->c + s;
+  // correction phase of the refinement: the fixed residual rho is added after the projection
+  const double *rho_in = D->rho;
+  const double c_new = st->c + s + (rho_in ? rho_in[(size_t)8 * ncell] : 0.0);
   const int parity = (st->iter + 1) & 1;
   const double *fcur = D->facc + (size_t)parity * ncell * 4;
   double *fnext = D->facc + (size_t)(parity ^ 1) * ncell * 4;
@@ -128,46 +177,19 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
       Dbl4 *acc4 = reinterpret_cast<Dbl4 *>(D->acc);
       const Dbl4 am = acc4[cell];
       acc4[cell] = Dbl4{0.0, 0.0, 0.0, 0.0};
-      const double rho = am.x - s * D->sumW[0];
-      const double u1 = am.y - s * D->sumW[1];
-      const double u2 = am.z - s * D->sumW[2];
-      const double tau = (am.w - s * D->sumW[3]) - rho;
-      reinterpret_cast<Dbl4 *>(D->mom)[cell] = Dbl4{rho, u1, u2, tau};
-      const double d = D->uniform_delta ? D->delta : D->delta_field[cell];
-      // collision coefficients a = G^{-1} m, m = (rho, u1, u2, rho + tau) = sum W psi h
-      const double m[4] = {rho, u1, u2, rho + tau};
-      double a[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        a[i] = D->ginv[i * 4] * m[0] + D->ginv[i * 4 + 1] * m[1] + D->ginv[i * 4 + 2] * m[2] + D->ginv[i * 4 + 3] * m[3];
-      // R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v_flow in the basis 1, v1, v2, |v|^2 - 1
-      const double A = d * (a[0] + a[3] - c_new);
-      const double B = d * a[1] + (D->flow_axis ? 0.0 : D->force);
-      const double Cc = d * a[2] + (D->flow_axis ? D->force : 0.0);
-      const double Dd = d * a[3];
-      SweepRec<T> *rec = static_cast<SweepRec<T> *>(D->rec);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        double hw[2];
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax) {
-          const int src = D->hw_src[(size_t)cell * 8 + q * 2 + ax];
-          if (src >= 0) {
-            const int side = src & 3;
-            // diffuse part alpha rho_w; the specular part (1 - alpha) h(mirror v) is added in the sweep
-            hw[ax] = D->alpha * (fcur[src] - s * D->ain[side]) / D->nrm[side];
-          } else {
-            hw[ax] = 0.0;
-          }
-        }
-        store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
-        // the diagonal-major copy only feeds the column sweep (rebuilt by sync_diag when a launch
-        // switches to it)
-        if (L.cols_v && D->rec_diag)
-          store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
-                           diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
-                       A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+      double rho = am.x - s * D->sumW[0];
+      double u1 = am.y - s * D->sumW[1];
+      double u2 = am.z - s * D->sumW[2];
+      double tau = (am.w - s * D->sumW[3]) - rho;
+      if (rho_in) {
+        const Dbl4 r = reinterpret_cast<const Dbl4 *>(rho_in)[cell];
+        rho += r.x;
+        u1 += r.y;
+        u2 += r.z;
+        tau += r.w;
       }
+      reinterpret_cast<Dbl4 *>(D->mom)[cell] = Dbl4{rho, u1, u2, tau};
+      write_records<T>(D, cell, rho, u1, u2, tau, c_new, s, fcur, rho_in, L.cols_v != 0);
       const double uf = D->flow_axis ? u2 : u1;  // velocity along the flow
       du = fabs(uf - D->u1prev[cell]);
       ua = fabs(uf);
@@ -176,6 +198,18 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
       if (!isfinite(rho) || !isfinite(u1) || !isfinite(u2) || !isfinite(tau)) bad = 1.0;
     }
     reinterpret_cast<Dbl4 *>(fnext)[cell] = Dbl4{0.0, 0.0, 0.0, 0.0};
+  }
+  if (rho_in) {
+    // the seam part of rho goes into the raw seam values the next sweep reads (this sweep has written
+    // them; the next one subtracts the pending shift from raw + rho)
+    const size_t nsx = D->periodic_x ? (size_t)D->ngroups * D->ny * 2 * kLanes : 0;
+    const size_t nsy = D->periodic_y ? (size_t)D->ngroups * D->nx * 2 * kLanes : 0;
+    const size_t stride = (size_t)D->fin_nblocks * kFinBlock;
+    for (size_t e = (size_t)(map & 0xffff) * kFinBlock + threadIdx.x; e < nsx + nsy; e += stride) {
+      T *dst = e < nsx ? static_cast<T *>(D->seam_x) + e : static_cast<T *>(D->seam_y) + (e - nsx);
+      const T add = e < nsx ? static_cast<const T *>(D->rho_seam_x)[e] : static_cast<const T *>(D->rho_seam_y)[e - nsx];
+      *dst += add;
+    }
   }
   du = block_sum(du, sh);
   ua = block_sum(ua, sh);
@@ -294,6 +328,31 @@ __global__ void reset_kernel(const InstanceDesc *D) {
   }
 }
 
+// Records (both layouts) of every cell from the stored state: moments, st->c, st->s and the fluxes of
+// the last sweep (parity st->iter & 1).  Solid cells get zero records.
+template <typename T>
+__global__ void records_kernel(const InstanceDesc *D) {
+  const DeviceState *st = D->state;
+  const int ncell = D->ncell;
+  const double *fcur = D->facc + (size_t)(st->iter & 1) * ncell * 4;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncell; cell += gridDim.x * blockDim.x) {
+    const uint32_t code0 = D->code4[(size_t)cell * 4];
+    if (code0 & kSolid) {
+      for (int q = 0; q < 4; ++q) {
+        store_rec<T>(static_cast<SweepRec<T> *>(D->rec) + (size_t)q * ncell + cell, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0,
+                     D->code4[(size_t)cell * 4 + q], 0.0);
+        if (D->rec_diag)
+          store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
+                           diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
+                       0.0, 0.0, 0.0, 0.0, 0.0, 0.0, D->code4[(size_t)cell * 4 + q], 0.0);
+      }
+      continue;
+    }
+    const Dbl4 m = reinterpret_cast<const Dbl4 *>(D->mom)[cell];
+    write_records<T>(D, cell, m.x, m.y, m.z, m.w, st->c, st->s, fcur, nullptr, true);
+  }
+}
+
 // Rebuild the diagonal-major records from the row-major ones (all four quadrants).
 template <typename T>
 __global__ void sync_diag_kernel(const InstanceDesc *D) {
@@ -371,6 +430,15 @@ cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cud
     reset_kernel<double><<<blocks, 256, 0, stream>>>(inst_dev);
   else
     reset_kernel<float><<<blocks, 256, 0, stream>>>(inst_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_records(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream) {
+  const int blocks = (ncell + 255) / 256 < 1024 ? (ncell + 255) / 256 : 1024;
+  if (fp64)
+    records_kernel<double><<<blocks, 256, 0, stream>>>(inst_dev);
+  else
+    records_kernel<float><<<blocks, 256, 0, stream>>>(inst_dev);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,21 @@ cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStr
 cudaError_t launch_anderson(const LaunchDesc &L, bool fp64, cudaStream_t stream);
 // Reset an instance to h = 0 (records, accumulators and state; arrays are cleared by the caller).
 cudaError_t launch_reset(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
+// Rebuild an instance's records (both layouts) from its stored state: moments, mass shift, pending shift
+// and the last sweep's wall fluxes (the mixed-precision refinement, dvm_refine.cu).
+cudaError_t launch_records(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
+// Mixed-precision refinement (dvm_refine.cu): seam values per instance, and the four steps of a pass.
+size_t refine_seam_count(const InstanceDesc &D);
+cudaError_t launch_refine_snapshot(const InstanceDesc *d, const InstanceDesc &h, bool fp64, double *snap, void *snap_seam,
+                                   double *snap_sc, cudaStream_t s);
+cudaError_t launch_refine_load_twin(const InstanceDesc *d, const InstanceDesc *twin, const InstanceDesc &h, bool fp64,
+                                    cudaStream_t s);
+cudaError_t launch_refine_residual(const InstanceDesc *d, const InstanceDesc *twin, const InstanceDesc &h, bool fp64,
+                                   const double *snap, const void *snap_seam, const double *snap_sc, double *rho,
+                                   void *rho_seam, cudaStream_t s);
+cudaError_t launch_refine_combine(const InstanceDesc *d, const InstanceDesc &h, bool fp64, const double *snap,
+                                  const void *snap_seam, const double *snap_sc, const double *rho, double *sums,
+                                  cudaStream_t s);
 // Rebuild an instance's diagonal-major records from its row-major ones (before column-sweep launches).
 cudaError_t launch_sync_diag(const InstanceDesc *inst_dev, int ncell, bool fp64, cudaStream_t stream);
 // Arm every instance of a launch for `count` more sweeps (device-relative; one launch).

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "dvm.h"
 #include "dvm_tables.h"
 
@@ -81,11 +83,17 @@ __global__ void __launch_bounds__(kMomBlock) moments_kernel(const double *__rest
 
 // Validate arguments and build the velocity table; returns DVM_OK or the failure.
 dvm_status prepare(const dvm_quad *q, const double *h, int ncell, double *mom, double *Q, VelTable &vt,
-                   int &blocks) {
-  if (!q || !h || !mom || !Q || ncell < 1) return DVM_EINVAL;
+                   int &blocks, std::string *why = nullptr) {
+  if (!q || !h || !mom || !Q || ncell < 1) {
+    if (why) *why = "null pointer argument or ncell < 1";
+    return DVM_EINVAL;
+  }
   std::vector<double> x, w;
   std::string err;
-  if (!quadrature_1d(q->kind, q->n, q->vmax, x, w, err)) return DVM_EINVAL;
+  if (!quadrature_1d(q->kind, q->n, q->vmax, x, w, err)) {  // n even, 2 <= n <= 64 (VelTable holds 64)
+    if (why) *why = err;
+    return DVM_EINVAL;
+  }
   vt.n = q->n;
   for (int a = 0; a < q->n; ++a) {
     vt.x[a] = x[a];
@@ -133,32 +141,60 @@ extern "C" dvm_status dvm_moments(const dvm_quad *q, const double *h, const uint
 // device that loads this library until the process exits.  Every call shares it and it keeps the
 // last call's contents; the ticket, which must start at zero, is cleared at the start of each call.
 // Calls on one device that overlap on the GPU (for example on two streams) race on the same array and
-// must be serialised by the caller.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress, with that device current); make that first call before any stream capture.
+// must be serialised by the caller.  The first call in a CUDA context looks up the array's device
+// address (cudaGetSymbolAddress, with that context current); make that first call before any stream
+// capture.  The address is cached per (device, context): after cudaDeviceReset, or when the primary
+// context is released and created again, the module is loaded anew and the next call looks the
+// address up again instead of using the stale one.
 namespace dvm {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = sizeof(double) * kMomMaxBlocks + 256;
-constexpr long long kNoAllocMaxCells = (long long)kMomMaxBlocks * kMomBlock * 64;  // 16,777,216 cells
+// The grid-stride kernel needs only kMomMaxBlocks partial sums for any cell count, so the scratch does
+// not bound ncell; the call accepts at most this many cells (as many as the largest dvm_create grid,
+// rounded up to a power of two) so that its cost stays bounded.
+constexpr long long kNoAllocMaxCells = 16777216LL;
 
 __device__ __align__(256) unsigned char g_moments_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
+// The current driver context, read through the runtime's driver entry point (no link against libcuda).
+cudaError_t current_context(CUcontext *out) {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  static GetCurrent fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<GetCurrent>(p);
+  }
+  return fn(out) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of the scratch array in the current context, looked up once per (device, context).
 cudaError_t scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  e = cudaFree(nullptr);  // makes the device's primary context current (no allocation, no free)
+  if (e != cudaSuccess) return e;
+  CUcontext ctx = nullptr;
+  e = current_context(&ctx);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_moments_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
@@ -171,15 +207,16 @@ extern "C" dvm_status dvm_moments_noalloc(const dvm_quad *q, const double *h, co
                                           double dA_over_L, double *mom, double *Q, void *stream) {
   using namespace dvm;
   if ((long long)ncell > kNoAllocMaxCells) {
-    set_moments_error("dvm_moments_noalloc: ncell = " + std::to_string(ncell) + " exceeds the maximum of " +
-                      std::to_string(kNoAllocMaxCells) + " cells of the fixed scratch; use dvm_moments");
+    set_moments_error("dvm_moments_noalloc: ncell = " + std::to_string(ncell) + " exceeds this call's maximum of " +
+                      std::to_string(kNoAllocMaxCells) + " cells; use dvm_moments");
     return DVM_EINVAL;
   }
   VelTable vt;
   int blocks = 0;
-  dvm_status st = prepare(q, h, ncell, mom, Q, vt, blocks);
+  std::string why;
+  dvm_status st = prepare(q, h, ncell, mom, Q, vt, blocks, &why);
   if (st != DVM_OK) {
-    set_moments_error("dvm_moments_noalloc: invalid argument");
+    set_moments_error("dvm_moments_noalloc: " + why);
     return st;
   }
   void *scratch = nullptr;

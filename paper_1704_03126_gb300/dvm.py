@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("force", ctypes.c_double), ("store_distribution", ctypes.c_int), ("sweep_warps", ctypes.c_int),
         ("top_wall_u1", ctypes.c_double), ("storage", ctypes.c_int),
         ("dx1", ctypes.c_double), ("row_heights", ctypes.c_void_p), ("anderson_depth", ctypes.c_int),
+        ("fp32_refine", ctypes.c_int),
     ]
 
 
@@ -100,13 +101,14 @@ def lib():
         L.dvm_batch_get_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         L.dvm_batch_autotune.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
         L.dvm_selftest_wait.argtypes = [I, I, ctypes.POINTER(D)]
+        L.dvm_probe_peaks.argtypes = [I, D, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I)]
         for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
                      "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
                      "dvm_moments_noalloc", "dvm_adjoint", "dvm_set_schedule", "dvm_get_schedule",
                      "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune",
-                     "dvm_batch_enqueue", "dvm_batch_check", "dvm_selftest_wait"):
+                     "dvm_batch_enqueue", "dvm_batch_check", "dvm_selftest_wait", "dvm_probe_peaks"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -129,13 +131,15 @@ class Solver:
     "transposed"; arguments and results keep the [ny][nx] layout either way.  dx1: x1 spacing (0 = square
     cells ly / ny); row_heights: [ny] heights of the rows along x2 (ly becomes their sum; needs dx1 > 0,
     runs on the column sweep, stored transposed; no adjoint).  anderson: depth of the Anderson mixing of
-    the source iteration (0 = plain; 1..8; FP64 storage and accommodation 1 only).
+    the source iteration (0 = plain; 1..8; FP64 storage and accommodation 1 only).  refine: FP32 storage,
+    the most passes of mixed-precision refinement after the FP32 iteration (None = the library's default,
+    3; 0 = off; see dvm_params.fp32_refine).
     """
 
     def __init__(self, mask, periodic_x=True, periodic_y=False, kn=None, delta=None, quad=("gh", 12, 5.0),
                  precision="fp64", ly=1.0, force=1.0, store_distribution=False, sweep_warps=0, stream=None,
                  schedule=None, accommodation=1.0, top_wall_u1=0.0, storage="auto", dx1=0.0, row_heights=None,
-                 anderson=0):
+                 anderson=0, refine=None):
         L = lib()
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         self.mask = mask
@@ -161,6 +165,8 @@ class Solver:
         p.storage = STORAGE[storage]
         p.dx1 = float(dx1)
         p.anderson_depth = int(anderson)
+        if refine is not None:
+            p.fp32_refine = int(refine)
         rows = None
         if row_heights is not None:
             rows = np.ascontiguousarray(row_heights, dtype=np.float64)
@@ -172,6 +178,9 @@ class Solver:
         p.sweep_warps = int(sweep_warps)
         self.params = p
         self.nv = p.quad.n
+        # bumped by every call that changes the state (delta field, reset, sweeps): autograd checks it
+        self.state_id = 0
+        self.last_adjoint_status = None
         self._ctx = ctypes.c_void_p()
         st = L.dvm_create(_ptr(mask), ctypes.byref(p), ctypes.c_void_p(stream or 0), ctypes.byref(self._ctx))
         if st != DVM_OK:
@@ -189,6 +198,7 @@ class Solver:
         return self.mask.shape
 
     def set_delta_field(self, delta_c):
+        self.state_id += 1
         if delta_c is None:
             return self._check(lib().dvm_set_delta_field(self._ctx, None))
         d = np.ascontiguousarray(delta_c, dtype=np.float64)
@@ -196,6 +206,7 @@ class Solver:
         return self._check(lib().dvm_set_delta_field(self._ctx, _ptr(d)))
 
     def reset(self):
+        self.state_id += 1
         return self._check(lib().dvm_reset(self._ctx))
 
     def set_schedule(self, kind="auto", shape=0):
@@ -212,11 +223,13 @@ class Solver:
         """Returns (status, sweeps run, error estimate)."""
         it = ctypes.c_int(0)
         est = ctypes.c_double(0.0)
+        self.state_id += 1
         st = lib().dvm_solve(self._ctx, float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(est))
         self._check(st, (DVM_OK,) if raise_on_noconv else (DVM_OK, DVM_ENOCONV))
         return st, it.value, est.value
 
     def iterate(self, n):
+        self.state_id += 1
         return self._check(lib().dvm_iterate(self._ctx, int(n)))
 
     def flowrate(self):
@@ -237,12 +250,16 @@ class Solver:
                     status=inf.status, transposed=bool(inf.transposed))
 
     def adjoint(self, tol=1e-10, max_iter=100000):
-        """dQ/d delta_c at the current forward state: (grad [ny][nx], F sum z v1, adjoint sweeps)."""
+        """dQ/d delta_c at the current forward state: (grad [ny][nx], F sum z v1, adjoint sweeps).
+
+        An adjoint iteration that ran out of sweeps (DVM_ENOCONV) still returns its last gradient; the
+        status is kept in last_adjoint_status (DVM_OK or DVM_ENOCONV)."""
         g = np.empty(self.shape)
         qid = ctypes.c_double()
         it = ctypes.c_int()
         st = lib().dvm_adjoint(self._ctx, float(tol), int(max_iter), _ptr(g), ctypes.byref(qid), ctypes.byref(it))
         self._check(st, (DVM_OK, DVM_ENOCONV))
+        self.last_adjoint_status = st
         return g, qid.value, it.value
 
     def distribution(self, ks):
@@ -287,20 +304,27 @@ class Batch:
     def _err(self, st):
         raise DvmError(st, lib().dvm_last_error(self.solvers[0]._ctx).decode())
 
+    def _touch(self):
+        for s in self.solvers:
+            s.state_id += 1
+
     def run(self, tol=1e-10, max_iter=100000):
         per = np.zeros(len(self.solvers), dtype=np.int32)
+        self._touch()
         st = lib().dvm_batch_run(self._b, float(tol), int(max_iter), _ptr(per))
         if st not in (DVM_OK, DVM_ENOCONV):
             self._err(st)
         return per
 
     def iterate(self, n=1):
+        self._touch()
         st = lib().dvm_batch_iterate(self._b, int(n))
         if st != DVM_OK:
             self._err(st)
 
     def enqueue(self, n=1):
         """n sweeps of every member, enqueued without waiting (see check)."""
+        self._touch()
         st = lib().dvm_batch_enqueue(self._b, int(n))
         if st != DVM_OK:
             self._err(st)
@@ -339,6 +363,7 @@ class Batch:
         """Time every fitting sweep kernel (the trial sweeps advance the state); keeps the fastest.
         Returns (kind, shape, median sweep ms); shape is the chunk width for "rows"."""
         k, v, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        self._touch()
         st = lib().dvm_batch_autotune(self._b, int(sweeps), ctypes.byref(k), ctypes.byref(v), ctypes.byref(ms))
         if st != DVM_OK:
             self._err(st)
@@ -361,6 +386,8 @@ def batch_solve(solvers, tol=1e-10, max_iter=100000):
     n = len(solvers)
     arr = (ctypes.c_void_p * n)(*[s._ctx.value for s in solvers])
     per = np.zeros(n, dtype=np.int32)
+    for s in solvers:
+        s.state_id += 1
     st = lib().dvm_batch_solve(arr, n, float(tol), int(max_iter), _ptr(per))
     if st not in (DVM_OK, DVM_ENOCONV):
         raise DvmError(st, lib().dvm_last_error(solvers[0]._ctx).decode())
@@ -373,6 +400,21 @@ def selftest_wait(primitive: int, spin_limit: int = 0):
     sec = ctypes.c_double(0.0)
     st = lib().dvm_selftest_wait(int(primitive), int(spin_limit), ctypes.byref(sec))
     return st, sec.value
+
+
+PROBE_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def probe_peaks(kind: str, seconds: float = 0.2):
+    """Measured FMA rate of the current GPU (dvm_probe_peaks): (TFLOP/s, L2 bytes, SMs).
+    kind: "fp32", "fp32x2" (packed pairs) or "fp64"."""
+    tf = ctypes.c_double(0.0)
+    l2 = ctypes.c_int(0)
+    sms = ctypes.c_int(0)
+    st = lib().dvm_probe_peaks(PROBE_KINDS[kind], float(seconds), ctypes.byref(tf), ctypes.byref(l2), ctypes.byref(sms))
+    if st != DVM_OK:
+        raise DvmError(st, "dvm_probe_peaks failed")
+    return tf.value, l2.value, sms.value
 
 
 def velocity_grid(kind: str, n: int, vmax: float = 5.0):

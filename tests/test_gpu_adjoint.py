@@ -129,6 +129,47 @@ def test_autograd_flow_rate_backward():
     assert abs((qp - qm) / (2 * eps) - float((g_auto * dirn).sum())) < 1e-6 * np.abs(g_auto).sum()
 
 
+def test_autograd_backward_after_the_solver_moved_on():
+    """One solver, two graph nodes: forward(d1), forward(d2), then backward of the first.  The first
+    node's gradient must be the one at d1 (backward re-solves at d1), equal to that of a fresh
+    forward(d1) + backward; and an adjoint cut short by max_iter raises unless allowed."""
+    import torch
+
+    from paper_1704_03126_gb300.autograd import flow_rate
+
+    mask = inputs.porous_disks_mask(24, 0.7, 2, 4, seed=5)[0]
+    quad = ("cubic", 8, 4.0)
+    sol = dvm.Solver(mask, True, True, delta=1.0, quad=quad, precision="fp64", store_distribution=True)
+    d1 = _delta_field(mask, 1.2, 21)
+    d2 = _delta_field(mask, 0.4, 22)
+    t1 = torch.tensor(d1, dtype=torch.float64, device="cuda", requires_grad=True)
+    t2 = torch.tensor(d2, dtype=torch.float64, device="cuda", requires_grad=True)
+    q1 = flow_rate(t1, sol, tol=1e-13)
+    q2 = flow_rate(t2, sol, tol=1e-13)
+    q1.backward()
+    g1 = t1.grad.cpu().numpy()
+    p = oracle.Problem.make(mask, True, True, d1, quad)
+    ref = oracle.solve(p, tol=1e-13, max_iter=200000)
+    g_ref, _, _, _ = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=200000)
+    assert np.abs(g1 - g_ref).max() < 1e-8 * np.abs(g_ref).max()
+    q2.backward()
+    g2 = t2.grad.cpu().numpy()
+    p2 = oracle.Problem.make(mask, True, True, d2, quad)
+    ref2 = oracle.solve(p2, tol=1e-13, max_iter=200000)
+    g_ref2, _, _, _ = oracle.adjoint(p2, ref2["h"], ref2["c"], tol=1e-13, max_iter=200000)
+    assert np.abs(g2 - g_ref2).max() < 1e-8 * np.abs(g_ref2).max()
+    # an adjoint iteration stopped by max_iter: error by default, a warning when allowed
+    t3 = torch.tensor(d1, dtype=torch.float64, device="cuda", requires_grad=True)
+    q3 = flow_rate(t3, sol, tol=1e-13, adjoint_max_iter=3)
+    with pytest.raises(dvm.DvmError) as ei:
+        q3.backward()
+    assert ei.value.status == dvm.DVM_ENOCONV
+    t4 = torch.tensor(d1, dtype=torch.float64, device="cuda", requires_grad=True)
+    q4 = flow_rate(t4, sol, tol=1e-13, adjoint_max_iter=3, allow_noconv=True)
+    with pytest.warns(RuntimeWarning):
+        q4.backward()
+
+
 @pytest.mark.parametrize("storage", ["as_given", "transposed"])
 @pytest.mark.parametrize("schedule", SCHEDULES[:2], ids=["rows", "cols1"])
 @pytest.mark.parametrize("name", ["rough24_nc8", "block_periodic_cubic10"])

@@ -52,4 +52,4 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(dvm.DvmError) as ei:
         dvm.moments(1, 16_777_217, ("gh", 4, 0.0), 1, 1, 1.0, noalloc=True)
     assert ei.value.status == dvm.DVM_EINVAL
-    assert "exceeds the maximum" in str(ei.value)
+    assert "exceeds this call's maximum" in str(ei.value)
