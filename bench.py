@@ -403,11 +403,28 @@ def run_ours(args, rank, world, local_rank):
         total_ms, sweep_ms, fin_ms, wsteps = timed_steps(batch, steps, warmup)
         clocks = sampler.stop() if sampler is not None else None
         total_ms = max_over_ranks(total_ms, world, device="cuda")
+        persistent_ok = args.anderson == 0 and not any(
+            i.extra.get("top_u", 0.0) or i.extra.get("row_heights") is not None for i in insts)
         return dict(workload=workload, precision=precision, insts=insts, upd=upd, solvers=solvers, batch=batch,
                     sched=sched, total_ms=total_ms, sweep_ms=sweep_ms, fin_ms=fin_ms, warmup_steps=wsteps,
                     kernels_per_step=batch.kernels_per_sweep(), steps=steps, clocks=clocks,
-                    value=job_value(world, steps, upd, total_ms),
+                    value=job_value(world, steps, upd, total_ms), persistent_ok=persistent_ok,
                     roofline=roofline(upd, sweep_ms, fin_ms, precision, sched, hbm_gbs, alu, workload))
+
+    def measure_persistent(m, steps, warmup):
+        """The same batch and steps in the persistent launch (one launch per step: every member's sweep
+        and finalize, scheduled on the device)."""
+        b = m["batch"]
+        b.set_schedule("rows", m["sched"]["shape"] if m["sched"]["kernel"] == "rows" else 0)
+        b.set_persistent(True)
+        total_ms, sweep_ms, _, _ = timed_steps(b, steps, warmup)
+        total_ms = max_over_ranks(total_ms, world, device="cuda")
+        on, blocks = b.persistent()
+        return {"value": job_value(world, steps, m["upd"], total_ms), "ms_per_step": total_ms / steps,
+                "launch_ms": sweep_ms, "blocks": blocks, "kernels_per_step": b.kernels_per_sweep() + 1,
+                "effective_hbm_frac": m["upd"] * (8 if m["precision"] == "fp32" else 16) / (sweep_ms / 1e3) / 1e9 / hbm_gbs,
+                "note": "one launch per step (arming + scheduler kernels): every member's sweep tiles and "
+                        "finalize chunks; launch_ms = CUDA-event time of that launch"}
 
     def close(m):
         m["batch"].close()
@@ -418,8 +435,7 @@ def run_ours(args, rank, world, local_rank):
         """e2e, time to converge, the CPU oracle beside it."""
         big = len(m["insts"]) > 6
         r = {}
-        r["e2e"] = e2e(args, m["insts"], m["precision"], stream, dvm, torch, sweeps=10 if big else 50,
-                       reps=1 if big else 3)
+        r["e2e"] = e2e(args, m["insts"], m["precision"], stream, dvm, torch, max_iter=10000 if big else 200000)
         if m["workload"] == "permeability":
             r["curves"] = curves({m["precision"]: m}, m["insts"], torch)
         else:
@@ -446,11 +462,13 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.skip_extras:
         out.update(extras(main))
+    if main["persistent_ok"] and not args.skip_extras and args.workload in ("batched", "rough", "porous"):
+        out["persistent"] = measure_persistent(main, args.steps, args.warmup)
     close(main)
     # the other configurations of the method, each with its own roofline, e2e and oracle baseline
     # (same steps and warm-up; the default line's workload is the 64-instance batch)
     if not args.single and not args.skip_extras and args.anderson == 0:
-        others = {"batched": [("rough", "fp32"), ("rough", "fp64"), ("porous", "fp32")],
+        others = {"batched": [("batched", "fp64"), ("rough", "fp32"), ("rough", "fp64"), ("porous", "fp32")],
                   "rough": [("rough", "fp64" if args.precision == "fp32" else "fp32")]}.get(args.workload, [])
         out["workloads"] = {}
         cpu_done = {}
@@ -462,39 +480,59 @@ def run_ours(args, rank, world, local_rank):
                    "dtype": "f32" if prec == "fp32" else "f64", "config": workload_config(prec, wl),
                    "roofline": m["roofline"], "clocks": m["clocks"],
                    "gpu_launches": args.steps * (m["kernels_per_step"] + 1)}
-            ex = extras(m, cpu=wl not in cpu_done, budget_s=8.0)
-            if "cpu_baseline" in ex:
-                cpu_done[wl] = ex["cpu_baseline"]
+            if wl == args.workload:
+                # the same batch in FP64 storage: timed steps only (its solve to 1e-10 would take minutes);
+                # the oracle baseline is the main line's
+                ex = {"cpu_baseline": out.get("cpu_baseline"),
+                      "note": "timed steps of the default batch in FP64 storage (no converge or e2e run)"}
+                if m["persistent_ok"]:
+                    ex["persistent"] = measure_persistent(m, args.steps, args.warmup)
             else:
-                ex["cpu_baseline"] = cpu_done.get(wl)
+                ex = extras(m, cpu=wl not in cpu_done, budget_s=8.0)
+                if "cpu_baseline" in ex:
+                    cpu_done[wl] = ex["cpu_baseline"]
+                else:
+                    ex["cpu_baseline"] = cpu_done.get(wl)
             rec.update(ex)
             out["workloads"][f"{wl}_{prec}"] = rec
             close(m)
     return out
 
 
-def e2e(args, insts, precision, stream, dvm, torch, sweeps=50, reps=3):
-    """Public API with host buffers: create from the host mask (H2D), `sweeps` sweeps, flow rate and
-    fields back to the host (D2H), destroy -- for every instance; wall clock."""
+def e2e(args, insts, precision, stream, dvm, torch, max_iter=200000):
+    """Time to solution through the public API with host buffers, in the line's metric: create every
+    instance from its host mask (H2D: mask, tables, the launch graphs), one batched solve to the
+    converge tolerance (dvm_batch_run; FP32 storage includes its refinement), flow rates and fields
+    back to the host (D2H), destroy.  updates = the sweeps each instance ran x its cell-velocity
+    updates per sweep; value = updates / wall time of all of it.  The breakdown gives each part."""
+    tol = 1e-10 if precision == "fp64" else 1e-6
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2d = d2h = 0
-    for _ in range(reps):
-        for inst in insts:
-            s = solver(dvm, inst, precision, stream.cuda_stream)
-            s.iterate(sweeps)
-            q, _ = s.flowrate()
-            f = s.fields()
-            s.close()
-            h2d += inst.mask.nbytes
-            d2h += 8 + sum(a.nbytes for a in f.values())
+    sols = [solver(dvm, inst, precision, stream.cuda_stream) for inst in insts]
+    t1 = time.perf_counter()
+    batch = dvm.Batch(sols)
+    t2 = time.perf_counter()
+    status = batch.run(tol=tol, max_iter=max_iter)
+    t3 = time.perf_counter()
+    out = [(s.flowrate()[0], s.fields()) for s in sols]
+    sweeps = [s.info()["iterations"] for s in sols]
+    t4 = time.perf_counter()
+    batch.close()
+    for s in sols:
+        s.close()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    upd = updates_per_step(insts) * sweeps * reps
-    return {"value": upd / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // (reps * sweeps),
-            "d2h_bytes_per_step": d2h // (reps * sweeps),
-            "note": f"per instance: dvm_create from host mask, {sweeps} sweeps, dvm_flowrate + dvm_fields to host, "
-                    f"dvm_destroy; {reps} repetitions"}
+    t5 = time.perf_counter()
+    upd = sum(int((inst.mask == 0).sum()) * inst.quad[1] ** 2 * n for inst, n in zip(insts, sweeps))
+    steps = max(1, max(sweeps))
+    h2d = sum(inst.mask.nbytes for inst in insts)
+    d2h = sum(8 + sum(a.nbytes for a in f.values()) for _, f in out)
+    return {"value": upd / (t5 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "seconds": t5 - t0, "tol": tol, "converged": int((np.asarray(status) == 0).sum()),
+            "sweeps": {"max": max(sweeps), "total": sum(sweeps)},
+            "breakdown_s": {"create": t1 - t0, "batch_graphs": t2 - t1, "solve": t3 - t2, "readback": t4 - t3,
+                            "destroy": t5 - t4},
+            "note": "dvm_create from host masks, dvm_batch_create, dvm_batch_run to tol, dvm_flowrate + dvm_fields "
+                    "to host, destroy; per-step bytes = all bytes / the most sweeps of an instance"}
 
 
 def converge(results, insts, torch, max_iter=200000, dvm=None, stream=None):
@@ -526,6 +564,22 @@ def converge(results, insts, torch, max_iter=200000, dvm=None, stream=None):
                      "converged_plain": sum(v["status"] == 0 for v in per.values()),
                      "converged_batched": int((np.asarray(status) == 0).sum()), "instances": len(insts),
                      "max_rel_dQ_batched_vs_plain": max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(bq, pq))}
+        # the same batch in one persistent launch per 64 sweeps (device-side scheduler, row sweep)
+        if dvm is not None and r.get("persistent_ok"):
+            pb = dvm.Batch(r["solvers"])
+            pb.set_schedule("rows", r["sched"]["shape"] if r["sched"]["kernel"] == "rows" else 0)
+            pb.set_persistent(True)
+            for s in r["solvers"]:
+                s.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pst = pb.run(tol=t, max_iter=max_iter)
+            t_p = time.perf_counter() - t0
+            pqs = [s.flowrate()[0] for s in r["solvers"]]
+            out[prec]["persistent"] = {
+                "batched_total_s": t_p, "converged": int((np.asarray(pst) == 0).sum()), "blocks": pb.persistent()[1],
+                "max_rel_dQ_vs_per_kernel_batch": max(abs(a - b) / max(abs(b), 1e-300) for a, b in zip(pqs, bq))}
+            pb.close()
         # the batched run again with mixed iterates (an extension of the paper's plain iteration; FP64
         # storage only)
         if len(insts) <= 6 and dvm is not None and prec == "fp64":

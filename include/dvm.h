@@ -129,8 +129,10 @@ typedef struct {
                                  point with one FP64 sweep (an FP64 twin of the context, created on first
                                  use), solves the correction equation with the FP32 iteration itself (no
                                  force, no plate drift, the residual as its source) and adds the
-                                 correction; passes stop once the correction changes the flow velocity by
-                                 less than tol (relative, L1 over gas cells).  This removes the FP32
+                                 correction (solved to 1e-2 relative); passes stop once the error left,
+                                 estimated as |d| / |x| (1e-2 + |d_1| / |x|) with d_1 the first pass's
+                                 correction (flow velocity, L1 over gas cells), is below tol / 10 --
+                                 usually after one pass.  This removes the FP32
                                  rounding that the iteration amplifies by 1 / (1 - r) where it converges
                                  slowly.  Fully diffuse walls only (accommodation = 1); with
                                  accommodation < 1 or a grid too wide for FP64 the FP32 result is returned
@@ -185,8 +187,8 @@ dvm_status dvm_reset(dvm_ctx *ctx);
  * smaller eps; tol should then stay above about 1e-6.  With FP32 storage and fp32_refine > 0 the
  * converged FP32 state is then refined (see dvm_params.fp32_refine).  iters (may be NULL) receives the
  * FP32 or FP64 sweeps run by this call (refinement: the FP32 sweeps of every phase; the one FP64
- * residual sweep per pass is not counted), est (may be NULL) the last estimate (refinement: the relative
- * size of the last correction).  Returns DVM_ENOCONV if max_iter is reached. */
+ * residual sweep per pass is not counted), est (may be NULL) the last estimate (refinement: the
+ * estimated relative error left after the last pass).  Returns DVM_ENOCONV if max_iter is reached. */
 dvm_status dvm_solve(dvm_ctx *ctx, double tol, int max_iter, int *iters, double *est);
 
 /* Run exactly n sweeps with no stopping test (timing and warm-up).  Synchronises the stream. */
@@ -250,7 +252,9 @@ dvm_status dvm_velocity_grid(const dvm_quad *q, double *nodes, double *weights);
 /* Batched solves: several contexts (independent geometries, Kn and velocity grids, one precision and
  * one store_distribution setting, one device) advanced by one launch of each kernel per sweep, on the
  * stream of the first context.  A batch records the contexts' configuration when it is created:
- * re-create it after dvm_set_delta_field on a member.  The contexts must outlive the batch. */
+ * re-create it after dvm_set_delta_field on a member.  Destroying a member first releases the batch's
+ * device resources (its launches run on a member's stream); the batch then answers DVM_ESTATE to every
+ * call and only dvm_batch_destroy remains to be called. */
 typedef struct dvm_batch dvm_batch;
 dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out);
 /* Source iteration of every member until each passes the stopping test of dvm_solve or has run
@@ -280,8 +284,25 @@ dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *shape)
  * (any output may be NULL; sweep_ms is its median sweep time).  The trial sweeps are ordinary source
  * iterations: they advance every member's state. */
 dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *shape, float *sweep_ms);
-/* Kernel launches issued per sweep of the batch (sweep + finalize kernels). */
+/* Kernel launches issued per sweep of the batch (sweep + finalize kernels; with the persistent launch,
+ * the arming and scheduler kernels of one launch). */
 int dvm_batch_kernels_per_sweep(const dvm_batch *batch);
+/* The persistent batched launch (on = 1) or one launch of each kernel per sweep (on = 0, the default).
+ * Persistent: one kernel runs up to 64 source iterations of every member not yet done, its blocks
+ * (as many as the SMs hold) taking work items -- a member's sweep tiles (velocity groups of the row
+ * wavefront), then its finalize chunks (mass shift; moments, records, residual and stopping test) --
+ * from a device-side scheduler: members advance independently, a converged member drops out at once
+ * and one member's finalize overlaps the others' sweeps; the launch (with its arming kernel) is one
+ * CUDA graph.  Needs the row sweep (dvm_batch_set_schedule rows), fully diffuse fixed walls, equal rows
+ * and the plain iteration (DVM_EINVAL otherwise).  Same fixed point and stopping test; sums are
+ * accumulated in another order (results agree to rounding).  Every wait of the scheduler is bounded:
+ * an idle block that finds no work for about a second gives up and the batch reports DVM_ETIMEOUT.
+ * dvm_batch_timing then reports the whole launch as the sweep time and 0 for the finalize.  The
+ * autotuner returns a batch to per-kernel launches.  The paper has no counterpart (Sec. II.A iterates
+ * one geometry at a time). */
+dvm_status dvm_batch_set_persistent(dvm_batch *batch, int on);
+/* on: 1 when the batch uses the persistent launch; blocks: the blocks of that launch (or 0). */
+dvm_status dvm_batch_get_persistent(const dvm_batch *batch, int *on, int *blocks);
 void dvm_batch_destroy(dvm_batch *batch);
 
 /* One-shot batch: create, run, destroy. */
@@ -332,8 +353,10 @@ const char *dvm_status_string(dvm_status status);
  * up after a fixed spin count, records DVM_ETIMEOUT in the instance state (dvm_solve then returns it)
  * and returns, leaving the context usable.  This entry point runs one of those wait primitives in a
  * one-block kernel on a flag that nothing raises: primitive 0 = the row sweep's progress-word wait,
- * 1 = the column sweep's mbarrier wait.  spin_limit > 0 replaces the sweeps' limit (2^22 spins) to
- * keep the call short.  Returns DVM_ETIMEOUT (the wait gave up, the expected outcome), DVM_OK (the
+ * 1 = the column sweep's mbarrier wait, 2 = the persistent launch's scheduler poll on an active
+ * instance whose work never appears (its own limit, 2^22 polls, about a second; spin_limit is not
+ * used).  spin_limit > 0 replaces the sweeps' limit (2^22 spins) of primitives 0 and 1 to keep the
+ * call short.  Returns DVM_ETIMEOUT (the wait gave up, the expected outcome), DVM_OK (the
  * flag was seen: impossible unless the primitive is broken), DVM_EINVAL or DVM_ECUDA; seconds (may be
  * NULL) receives the call's wall time.  The paper has no counterpart. */
 dvm_status dvm_selftest_wait(int primitive, int spin_limit, double *seconds);

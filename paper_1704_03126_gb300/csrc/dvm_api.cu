@@ -67,6 +67,7 @@ struct dvm_ctx {
   int *d_wall_slot = nullptr;      // alpha < 1: [ncell][4] face slots (freed with the context)
   void *d_wbuf = nullptr;          // alpha < 1: incident values at the wall faces, two parities
   dvm_batch *self = nullptr;       // batch of this context alone (built on first use)
+  std::vector<dvm_batch *> batches; // every live batch that has this context as a member
   DeviceState *h_state = nullptr;  // pinned
   std::string err;
   // adjoint (allocated by the first dvm_adjoint)
@@ -92,6 +93,7 @@ struct dvm_batch {
   std::vector<dvm_ctx *> ctxs;
   bool fp64 = true, store_h = false, uniform = true;
   int warps = 0, cw = 0, nsweep = 0, nfin = 0;
+  int row_tiles = 1;                 // row sweep: most velocity groups a block sweeps side by side
   int kind = DVM_SWEEP_COLUMNS, cols_v = 1;  // resolved sweep schedule of the launch
   InstanceDesc *d_descs = nullptr;
   int *d_smap = nullptr, *d_fmap = nullptr;
@@ -104,6 +106,12 @@ struct dvm_batch {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timed = false;
   std::vector<InstanceDesc> hdescs;  // the members' descriptors as uploaded to d_descs
+  bool detached = false;             // a member was destroyed first: device resources released
+  // persistent launch: the device scheduler's arrays (one allocation) and its descriptor
+  bool persistent = false;
+  void *p_mem = nullptr;
+  PersistDesc pdesc{};
+  int p_blocks = 0;
 };
 
 namespace {
@@ -217,6 +225,7 @@ bool table_sums(const dvm_ctx *c, const std::vector<T> &vel, InstanceDesc &D) {
 struct Schedule {
   int kind = DVM_SWEEP_COLUMNS;
   int v = 1;
+  bool persistent = false;  // row sweep only: the persistent batched launch (dvm_persist.cu)
 };
 
 // The column sweep needs nx * v <= kColsMaxThreads (a thread per column and velocity subset); the
@@ -377,6 +386,7 @@ LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const in
   L.fin_map = fin_map;
   L.ninst = ninst;
   L.warps = warps;
+  L.row_tiles = 1;
   L.cw = cw;
   L.anderson = 0;
   L.aa_blocks = 0;
@@ -413,8 +423,8 @@ int iters_per_graph(double updates_per_iter) {
   return 32;
 }
 
-void batch_free(dvm_batch *b) {
-  if (!b) return;
+// The batch's device resources (graphs, events, launch arrays), not the host struct.
+void batch_release(dvm_batch *b) {
   if (b->g_many) cudaGraphExecDestroy(b->g_many);
   if (b->g_sweep) cudaGraphExecDestroy(b->g_sweep);
   if (b->g_fin) cudaGraphExecDestroy(b->g_fin);
@@ -423,7 +433,112 @@ void batch_free(dvm_batch *b) {
   if (b->d_descs) cudaFree(b->d_descs);
   if (b->d_smap) cudaFree(b->d_smap);
   if (b->d_fmap) cudaFree(b->d_fmap);
+  if (b->p_mem) cudaFree(b->p_mem);
+  b->g_many = b->g_sweep = b->g_fin = nullptr;
+  for (auto &e : b->ev) e = nullptr;
+  b->d_descs = nullptr;
+  b->d_smap = b->d_fmap = nullptr;
+  b->p_mem = nullptr;
+}
+
+// Unregister the batch from its members (each member keeps the list of batches it belongs to).
+void batch_unlink(dvm_batch *b) {
+  for (dvm_ctx *c : b->ctxs) {
+    auto &v = c->batches;
+    v.erase(std::remove(v.begin(), v.end(), b), v.end());
+  }
+}
+
+void batch_free(dvm_batch *b) {
+  if (!b) return;
+  batch_unlink(b);
+  batch_release(b);
   delete b;
+}
+
+// A member is being destroyed while the batch lives on: release the batch's device resources now,
+// while the member's stream still exists; the batch can then only be destroyed (DVM_ESTATE otherwise).
+void batch_detach(dvm_batch *b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_unlink(b);
+  batch_release(b);
+  b->ctxs.clear();
+  b->stream = nullptr;
+  b->detached = true;
+}
+
+constexpr int kPersistSweeps = 64;     // sweeps per instance per persistent launch (members retire early)
+constexpr int kPersistFinCells = 4096; // cells per finalize work item of the persistent launch
+
+// The persistent launch of a row-sweep batch: its scheduler arrays and one graph per sweep count.
+dvm_status persist_setup(dvm_batch *b, const std::vector<int> &smap, const std::vector<double> &work,
+                         const LaunchDesc &L) {
+  const int n = (int)b->ctxs.size();
+  dvm_ctx *c0 = b->ctxs[0];
+  std::vector<int> order(n), base(n), count(n, 0), fin(n), tiles;
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+  for (int i = 0; i < n; ++i) {
+    base[i] = (int)tiles.size();
+    for (int e : smap)
+      if ((e >> 16) == i) {
+        tiles.push_back(e);
+        ++count[i];
+      }
+    fin[i] = (b->ctxs[i]->ncell + kPersistFinCells - 1) / kPersistFinCells;
+  }
+  // one allocation: work words (8-byte aligned first), then the int arrays
+  const size_t nint = 5 * (size_t)n + tiles.size() + 2;
+  const size_t bytes = 8 * (size_t)n + 4 * (size_t)n + 4 * nint;
+  DVM_CUDA(c0, cudaMalloc(&b->p_mem, bytes));
+  char *m = static_cast<char *>(b->p_mem);
+  PersistDesc &P = b->pdesc;
+  P.ninst = n;
+  P.fin_cells = kPersistFinCells;
+  P.work = reinterpret_cast<unsigned long long *>(m);
+  P.finished = reinterpret_cast<unsigned int *>(m + 8 * (size_t)n);
+  int *ip = reinterpret_cast<int *>(m + 12 * (size_t)n);
+  P.left = ip;
+  P.active = ip + n;
+  P.error = ip + n + 1;
+  int *arrays = ip + n + 2;
+  std::vector<int> host;
+  host.insert(host.end(), order.begin(), order.end());
+  host.insert(host.end(), base.begin(), base.end());
+  host.insert(host.end(), count.begin(), count.end());
+  host.insert(host.end(), fin.begin(), fin.end());
+  host.insert(host.end(), tiles.begin(), tiles.end());
+  P.order = arrays;
+  P.tile_base = arrays + n;
+  P.tile_count = arrays + 2 * n;
+  P.fin_items = arrays + 3 * n;
+  P.tiles = arrays + 4 * n;
+  DVM_CUDA(c0, cudaMemsetAsync(b->p_mem, 0, bytes, b->stream));
+  DVM_CUDA(c0, cudaMemcpyAsync(arrays, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, b->stream));
+  DVM_CUDA(c0, cudaStreamSynchronize(b->stream));
+  int sms = 0;
+  DVM_CUDA(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+  const int per_sm = persistent_blocks_per_sm(b->fp64, b->uniform, L);
+  if (per_sm < 1) return fail(c0, DVM_EINVAL, "the persistent launch does not fit an SM");
+  b->p_blocks = sms * per_sm;
+  return DVM_OK;
+}
+
+// Capture the persistent launch (arming kernel + scheduler kernel) for `sweeps` sweeps per member.
+dvm_status capture_persistent(dvm_batch *b, const LaunchDesc &L, int sweeps, cudaGraphExec_t *out) {
+  dvm_ctx *c0 = b->ctxs[0];
+  cudaGraph_t graph = nullptr;
+  DVM_CUDA(c0, cudaStreamBeginCapture(c0->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_persistent(b->fp64, b->uniform, L, b->pdesc, b->p_blocks, sweeps, c0->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(c0->cap_stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(c0, DVM_ECUDA, std::string("persistent graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c0, DVM_ECUDA, std::string("persistent graph instantiate: ") + cudaGetErrorString(e));
+  return DVM_OK;
 }
 
 // Build a batch over ctxs (errors reported on ctxs[0]) with the given sweep schedule, or with the
@@ -486,19 +601,39 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
     descs[i] = ctxs[i]->hdesc;
     descs[i].uniform_delta = ctxs[i]->uniform ? 1 : 0;
     descs[i].delta_field = ctxs[i]->d_delta_field;
-    for (int g = 0; g < ctxs[i]->ngroups; ++g)
-      for (int part = 0; part < parts; ++part) smap.push_back((i << 16) | (part << 12) | g);
     for (int blk = 0; blk < ctxs[i]->hdesc.fin_nblocks; ++blk) fmap.push_back((i << 16) | blk);
     work[i] = (double)ctxs[i]->ncell;
     upd += (double)ctxs[i]->geo.n_gas * ctxs[i]->nv * ctxs[i]->nv;
+  }
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c0->device);
+  // Row sweep: a member whose rows in flight fill only part of the block sweeps several of its velocity
+  // groups side by side (at most 8, and as many as the shared memory of the launch allows).
+  int row_tiles = 1;
+  if (!cols) {
+    for (int i = 0; i < n; ++i) {
+      const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
+      row_tiles = std::max(row_tiles, std::min(std::min(b->warps / need, 8), ctxs[i]->ngroups));
+    }
+    while (row_tiles > 1 && sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles) > (size_t)smem_optin) --row_tiles;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (cols) {
+      for (int g = 0; g < ctxs[i]->ngroups; ++g)
+        for (int part = 0; part < parts; ++part) smap.push_back((i << 16) | (part << 12) | g);
+    } else {
+      const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
+      const int k = std::max(1, std::min(b->warps / need, row_tiles));
+      for (int g = 0; g < ctxs[i]->ngroups; g += k) smap.push_back((i << 16) | (k << 12) | g);
+    }
   }
   // longest sweeps first
   std::stable_sort(smap.begin(), smap.end(), [&](int a, int c) { return work[a >> 16] > work[c >> 16]; });
   b->nsweep = (int)smap.size();
   b->nfin = (int)fmap.size();
-  int smem_optin = 0;
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c0->device);
-  const size_t smem = cols ? cols_smem_bytes(b->fp64, b->cols_v, b->warps) : sweep_smem_bytes(b->fp64, b->warps, b->cw);
+  b->row_tiles = row_tiles;
+  const size_t smem = cols ? cols_smem_bytes(b->fp64, b->cols_v, b->warps)
+                           : sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles);
   if ((!cols && b->warps > kMaxSweepWarps) || (cols && b->warps * kLanes > kColsMaxThreads) || smem > (size_t)smem_optin) {
     batch_free(b);
     return fail(c0, DVM_EINVAL, "batched grids too wide for the sweep's shared memory");
@@ -525,6 +660,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   for (auto &e : b->ev) BATCH_CUDA(cudaEventCreate(&e));
 #undef BATCH_CUDA
   LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw, b->cols_v, spec);
+  L.row_tiles = b->row_tiles;
   {
     long long aa_max = 0;
     for (int i = 0; i < n; ++i) aa_max = std::max(aa_max, ctxs[i]->aa_n);
@@ -532,6 +668,27 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
     L.anderson = b->anderson ? 1 : 0;
     // about 8 elements per thread, at most 1024 blocks per instance
     L.aa_blocks = (int)std::min<long long>(1024, std::max<long long>(1, (aa_max + 2047) / 2048));
+  }
+  if (sched.persistent) {
+    if (cols || b->anderson || spec) {
+      batch_free(b);
+      return fail(c0, DVM_EINVAL, "the persistent launch runs the row sweep with fully diffuse fixed walls, equal rows "
+                                  "and the plain iteration (no mixing)");
+    }
+    b->persistent = true;
+    dvm_status st = persist_setup(b, smap, work, L);
+    if (st == DVM_OK) {
+      b->m = kPersistSweeps;
+      st = capture_persistent(b, L, b->m, &b->g_many);
+    }
+    if (st == DVM_OK) st = capture_persistent(b, L, 1, &b->g_sweep);
+    if (st != DVM_OK) {
+      batch_free(b);
+      return st;
+    }
+    for (dvm_ctx *c : b->ctxs) c->batches.push_back(b);
+    *out = b;
+    return DVM_OK;
   }
   b->m = iters_per_graph(upd);
   dvm_status st = capture_graph(c0, c0->cap_stream, L, b->nsweep, b->nfin, b->fp64, b->uniform, b->m, true, true,
@@ -544,6 +701,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
     batch_free(b);
     return st;
   }
+  for (dvm_ctx *c : b->ctxs) c->batches.push_back(b);
   *out = b;
   return DVM_OK;
 }
@@ -564,7 +722,10 @@ dvm_status batch_poll(dvm_batch *b, bool *all_done) {
   dvm_ctx *c0 = b->ctxs[0];
   for (dvm_ctx *c : b->ctxs)
     DVM_CUDA(c0, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, b->stream));
+  int perr = 0;
+  if (b->persistent) DVM_CUDA(c0, cudaMemcpyAsync(&perr, b->pdesc.error, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   DVM_CUDA(c0, cudaStreamSynchronize(b->stream));
+  if (perr) return fail(c0, DVM_ETIMEOUT, "persistent launch: an idle block gave up waiting for work");
   bool all = true;
   for (dvm_ctx *c : b->ctxs) all = all && c->h_state->done;
   *all_done = all;
@@ -634,7 +795,8 @@ dvm_status batch_iterate(dvm_batch *b, int n) {
     DVM_CUDA(c0, cudaEventRecord(b->ev[0], b->stream));
     DVM_CUDA(c0, cudaGraphLaunch(b->g_sweep, b->stream));
     DVM_CUDA(c0, cudaEventRecord(b->ev[1], b->stream));
-    DVM_CUDA(c0, cudaGraphLaunch(b->g_fin, b->stream));
+    // (the persistent launch finalizes inside g_sweep)
+    if (b->g_fin) DVM_CUDA(c0, cudaGraphLaunch(b->g_fin, b->stream));
     DVM_CUDA(c0, cudaEventRecord(b->ev[2], b->stream));
   }
   bool all = false;
@@ -657,7 +819,7 @@ dvm_status ensure_self(dvm_ctx *c) {
 // ------------------------------------------------------------------------------------------------
 // Mixed-precision refinement of FP32 storage (kernels and the method in dvm_refine.cu).
 
-constexpr double kCorrectionTol = 1e-3;  // relative tolerance of each correction solve (on |d|)
+constexpr double kCorrectionTol = 1e-2;  // relative tolerance of each correction solve (on |d|)
 
 // Doubles per state region of the refinement buffers: 8 ncell + 1 rounded up to a multiple of four.
 size_t refine_state_stride(int ncell) { return ((size_t)8 * ncell + 1 + 3) & ~(size_t)3; }
@@ -733,7 +895,7 @@ dvm_status batch_refine(dvm_batch *b, double tol, int max_iter) {
     *sseam = c->r_seam;
     *rseam = static_cast<char *>(c->r_seam) + 4 * c->r_nseam;
   };
-  std::vector<double> sums(2 * n);
+  std::vector<double> sums(2 * n), first(n, 0.0);
   dvm_status result = DVM_OK;
   for (int pass = 0; pass < passes && result == DVM_OK; ++pass) {
     for (int i = 0; i < n; ++i) {
@@ -796,8 +958,20 @@ dvm_status batch_refine(dvm_batch *b, double tol, int max_iter) {
       DVM_CUDA(c0, cudaMemcpyAsync(&sums[2 * i], sm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     DVM_CUDA(c0, cudaStreamSynchronize(s));
+    // Error left after this pass: the correction solve's own tolerance and the FP32 rounding it
+    // amplifies, both relative to |d|; the rounding part is at most |d_1| / |x| (the first correction
+    // carries the whole amplified rounding of the FP32 fixed point).  Stop when, with a factor 10 of
+    // margin, that is below tol for every member; the estimate is stored as the solve's est.
     double worst = 0.0;
-    for (int i = 0; i < n; ++i) worst = std::max(worst, sums[2 * i + 1] > 0.0 ? sums[2 * i] / sums[2 * i + 1] : 0.0);
+    std::vector<double> est(n);
+    for (int i = 0; i < n; ++i) {
+      const double rel = sums[2 * i + 1] > 0.0 ? sums[2 * i] / sums[2 * i + 1] : 0.0;
+      if (pass == 0) first[i] = rel;
+      est[i] = rel * (kCorrectionTol + first[i]);
+      worst = std::max(worst, 10.0 * est[i]);
+      DVM_CUDA(c0, cudaMemcpyAsync(&b->ctxs[i]->d_state->est, &est[i], sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    DVM_CUDA(c0, cudaStreamSynchronize(s));
     if (worst < tol) break;
   }
   batch_free(tb);
@@ -1492,6 +1666,7 @@ dvm_status dvm_batch_create(dvm_ctx *const *ctxs, int n, dvm_batch **out) {
 
 dvm_status dvm_batch_run(dvm_batch *batch, double tol, int max_iter, dvm_status *per) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   if (!(tol > 0.0)) return fail(batch->ctxs[0], DVM_EINVAL, "tol must be > 0");
   dvm_status st = batch_run(batch, tol, max_iter, per, nullptr, nullptr);
   if (st != DVM_OK || batch->fp64) return st;
@@ -1500,11 +1675,13 @@ dvm_status dvm_batch_run(dvm_batch *batch, double tol, int max_iter, dvm_status 
 
 dvm_status dvm_batch_iterate(dvm_batch *batch, int n) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   return batch_iterate(batch, n);
 }
 
 dvm_status dvm_batch_enqueue(dvm_batch *batch, int n) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   dvm_batch *b = batch;
   dvm_ctx *c0 = b->ctxs[0];
   if (n < 1 || n > 1000000) return fail(c0, DVM_EINVAL, "n must be in 1..1000000");
@@ -1520,7 +1697,8 @@ dvm_status dvm_batch_enqueue(dvm_batch *batch, int n) {
     DVM_CUDA(c0, cudaEventRecord(b->ev[0], b->stream));
     DVM_CUDA(c0, cudaGraphLaunch(b->g_sweep, b->stream));
     DVM_CUDA(c0, cudaEventRecord(b->ev[1], b->stream));
-    DVM_CUDA(c0, cudaGraphLaunch(b->g_fin, b->stream));
+    // (the persistent launch finalizes inside g_sweep)
+    if (b->g_fin) DVM_CUDA(c0, cudaGraphLaunch(b->g_fin, b->stream));
     DVM_CUDA(c0, cudaEventRecord(b->ev[2], b->stream));
   }
   b->timed = (n == 1) || (n % b->m != 0) || b->m == 1;
@@ -1529,6 +1707,7 @@ dvm_status dvm_batch_enqueue(dvm_batch *batch, int n) {
 
 dvm_status dvm_batch_check(dvm_batch *batch) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   bool all = false;
   dvm_status st = batch_poll(batch, &all);
   if (st != DVM_OK) return st;
@@ -1541,6 +1720,7 @@ dvm_status dvm_batch_check(dvm_batch *batch) {
 
 dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *finalize_ms) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   if (!batch->timed) return fail(batch->ctxs[0], DVM_ESTATE, "no timed single sweep has run on this batch");
   float a = 0.f, b = 0.f;
   DVM_CUDA(batch->ctxs[0], cudaEventElapsedTime(&a, batch->ev[0], batch->ev[1]));
@@ -1550,7 +1730,31 @@ dvm_status dvm_batch_timing(const dvm_batch *batch, float *sweep_ms, float *fina
   return DVM_OK;
 }
 
-int dvm_batch_kernels_per_sweep(const dvm_batch *batch) { return batch ? (batch->anderson ? 6 : 3) : 0; }
+int dvm_batch_kernels_per_sweep(const dvm_batch *batch) {
+  if (!batch || batch->detached) return 0;
+  if (batch->persistent) return 2;  // per launch: the arming kernel and the scheduler kernel
+  return batch->anderson ? 6 : 3;
+}
+
+dvm_status dvm_batch_set_persistent(dvm_batch *batch, int on) {
+  if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
+  Schedule sc;
+  sc.kind = batch->kind;
+  sc.v = batch->kind == DVM_SWEEP_ROWS ? batch->cw : batch->cols_v;
+  sc.persistent = on != 0;
+  if (sc.persistent && sc.kind != DVM_SWEEP_ROWS)
+    return fail(batch->ctxs[0], DVM_EINVAL, "the persistent launch runs the row sweep: set a row schedule first");
+  return batch_replan(batch, sc);
+}
+
+dvm_status dvm_batch_get_persistent(const dvm_batch *batch, int *on, int *blocks) {
+  if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
+  if (on) *on = batch->persistent ? 1 : 0;
+  if (blocks) *blocks = batch->persistent ? batch->p_blocks : 0;
+  return DVM_OK;
+}
 
 dvm_status dvm_set_schedule(dvm_ctx *ctx, int kind, int threads_per_column) {
   if (!ctx) return DVM_EINVAL;
@@ -1585,6 +1789,7 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
 
 dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_column) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   int nx_max = 0;
   bool spec = false;
   for (dvm_ctx *c : batch->ctxs) {
@@ -1600,6 +1805,7 @@ dvm_status dvm_batch_set_schedule(dvm_batch *batch, int kind, int threads_per_co
 
 dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *threads_per_column) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   if (kind) *kind = batch->kind;
   if (threads_per_column) *threads_per_column = batch->kind == DVM_SWEEP_ROWS ? batch->cw : batch->cols_v;
   return DVM_OK;
@@ -1607,6 +1813,7 @@ dvm_status dvm_batch_get_schedule(const dvm_batch *batch, int *kind, int *thread
 
 dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *threads_per_column, float *sweep_ms) {
   if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
   dvm_ctx *c0 = batch->ctxs[0];
   if (sweeps < 1 || sweeps > 1000) return fail(c0, DVM_EINVAL, "sweeps must be in 1..1000");
   int nx_max = 0;
@@ -1660,7 +1867,7 @@ dvm_status dvm_batch_autotune(dvm_batch *batch, int sweeps, int *kind, int *thre
 
 void dvm_batch_destroy(dvm_batch *batch) {
   if (!batch) return;
-  cudaStreamSynchronize(batch->stream);
+  if (!batch->detached) cudaStreamSynchronize(batch->stream);
   batch_free(batch);
 }
 
@@ -1678,6 +1885,16 @@ dvm_status dvm_batch_solve(dvm_ctx *const *ctxs, int n, double tol, int max_iter
 void dvm_destroy(dvm_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  // batches still holding this context lose their launches now (their streams may be this context's)
+  while (!ctx->batches.empty()) {
+    dvm_batch *b = ctx->batches.back();
+    if (b == ctx->self) {
+      batch_free(b);
+      ctx->self = nullptr;
+    } else {
+      batch_detach(b);
+    }
+  }
   release_device(ctx);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);

@@ -196,16 +196,38 @@ struct InstanceDesc {
 // Launch descriptor shared by the kernels of one (possibly batched) iteration.
 struct LaunchDesc {
   const InstanceDesc *inst;  // device array [ninst]
-  const int *sweep_map;      // [sweep blocks]: instance << 16 | part << 12 | group
+  const int *sweep_map;      // [sweep blocks]: instance << 16 | part << 12 | group; for the row sweep the
+                             // 4-bit field is the number of consecutive groups swept side by side (0 = 1)
   const int *fin_map;        // [finalize blocks]: instance << 16 | block within instance
   int ninst;
   int warps;                 // sweep warps per block: max over instances of ceil(nx / cw)
+  int row_tiles;             // row sweep: most velocity groups a block sweeps side by side (shared-memory
+                             // layout); a sweep-map entry carries its own count
   int cw;                    // chunk width (cells per warp and step) of the sweep: 1, 2, 4, 8 or 16
   int cols_v;                // 0: row-wavefront sweep; 1, 2, 4: column sweep with that many threads per
                              // column (the block's velocity set is split among them)
   int specular;              // 1: some instance has accommodation < 1 or a moving plate (column sweep only)
   int anderson;              // 1: some instance mixes its iterates (dvm_anderson.cu)
   int aa_blocks;             // blocks per instance of the mixing kernels
+};
+
+// Scheduler of the persistent batched launch (dvm_persist.cu).  Instance i's work items per sweep:
+// tile_count[i] sweep tiles (sweep-map entries tiles[tile_base[i] ...]), then fin_items[i] chunks of
+// fin_cells cells twice (mass shift; moments, records and stopping test).
+constexpr int kPersistSpinLimit = 1 << 22;  // polls of an idle block before it gives up (~1 s)
+struct PersistDesc {
+  int ninst;
+  int fin_cells;
+  const int *order;            // [ninst] instances in scan order (longest sweeps first)
+  const int *tile_base;        // [ninst]
+  const int *tile_count;       // [ninst]
+  const int *tiles;            // sweep-map entries grouped by instance
+  const int *fin_items;        // [ninst]
+  unsigned long long *work;    // [ninst] stage counter << 32 | items taken
+  unsigned int *finished;      // [ninst] items of the current stage finished
+  int *left;                   // [ninst] sweeps left in this launch
+  int *active;                 // instances not retired in this launch
+  int *error;                  // an idle block's poll limit ran out
 };
 
 #ifdef __CUDACC__

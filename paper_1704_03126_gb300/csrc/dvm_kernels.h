@@ -9,13 +9,14 @@ namespace dvm {
 
 // Shared-memory layout of the sweep kernel (bytes), identical on host and device: the 3-deep ring of
 // R warps x CW cells x ring_stride, the record stages, the staged seam rows (FP32), the 1/denominator
-// table, the moment weights and the warps' progress words.
+// table, the moment weights and the warps' progress words.  A block may sweep `ntile` velocity groups
+// side by side (narrow grids): the seam stages, the 1/denominator tables and the weights are per group.
 struct SweepSmemLayout {
   size_t ring, stage, seam, inv, wts, prog, total;
 };
 
 __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int tsize, int recsize, int nstage,
-                                                             int stage_seams, int ring_stride) {
+                                                             int stage_seams, int ring_stride, int ntile = 1) {
   SweepSmemLayout L;
   size_t off = 0;
   auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
@@ -24,18 +25,18 @@ __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int 
   L.stage = off;
   off = align16(off + (size_t)R * nstage * cw * recsize);
   L.seam = off;
-  if (stage_seams) off = align16(off + (size_t)2 * nstage * 2 * cw * kLanes * tsize);
+  if (stage_seams) off = align16(off + (size_t)ntile * 2 * nstage * 2 * cw * kLanes * tsize);
   L.inv = off;
-  off = align16(off + (size_t)kInvRows * kLanes * tsize);  // rows 0-8: stencil classes, row 9: solid (0)
+  off = align16(off + (size_t)ntile * kInvRows * kLanes * tsize);  // rows 0-8: stencil classes, row 9: solid (0)
   L.wts = off;
-  off = align16(off + (size_t)4 * ring_stride * tsize);
+  off = align16(off + (size_t)ntile * 4 * ring_stride * tsize);
   L.prog = off;
   off = align16(off + (size_t)R * sizeof(int));
   L.total = off;
   return L;
 }
 
-size_t sweep_smem_bytes(bool fp64, int warps, int cw);
+size_t sweep_smem_bytes(bool fp64, int warps, int cw, int ntile = 1);
 
 // Column sweep (dvm_sweep_cols.cuh): shared-memory layout -- per-pair velocity constants, the
 // 1/denominator table of the block's velocities and the 3-deep ring of column results.
@@ -80,8 +81,8 @@ size_t cols_smem_bytes(bool fp64, int v, int warps);
 cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 cudaError_t launch_sweep_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream);
-size_t sweep_smem_bytes_f32(int warps, int cw);
-size_t sweep_smem_bytes_f64(int warps, int cw);
+size_t sweep_smem_bytes_f32(int warps, int cw, int ntile);
+size_t sweep_smem_bytes_f64(int warps, int cw, int ntile);
 cudaError_t launch_sweep_cols_f32(bool uniform_delta, bool adjoint, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 cudaError_t launch_sweep_cols_f64(bool uniform_delta, bool adjoint, const LaunchDesc &L, int nblocks, cudaStream_t stream);
 // The transposed sweep of the adjoint iteration (launch over adjoint views of the instances).
@@ -94,6 +95,13 @@ cudaError_t launch_adjoint_finalize(const LaunchDesc &L, int fin_blocks, int sea
 cudaError_t launch_adjoint_reset(const InstanceDesc *adj_dev, int ncell, bool fp64, cudaStream_t stream);
 cudaError_t launch_adjoint_gradient(const InstanceDesc *adj_dev, int ncell, bool fp64, cudaStream_t stream);
 
+// The persistent batched launch (dvm_persist.cu): an arming kernel, then up to `sweeps` source
+// iterations of every member not done, scheduled on the device (row sweep, plain iteration).
+cudaError_t launch_persistent(bool fp64, bool uniform_delta, const LaunchDesc &L, const PersistDesc &P, int blocks,
+                              int sweeps, cudaStream_t stream);
+int persistent_blocks_per_sm(bool fp64, bool uniform_delta, const LaunchDesc &L);
+// One warp polls a scheduler with no work and one active instance: result_dev receives -1 when it gave up.
+cudaError_t launch_persist_selftest(const PersistDesc &P, int *result_dev, cudaStream_t stream);
 // Finalize: mean-density projection, (Anderson mixing,) moments, residual, flow rate, next sweep records.
 cudaError_t launch_finalize(const LaunchDesc &L, int nblocks, bool fp64, cudaStream_t stream);
 // Anderson mixing between the projection and the record writer (instances with a mixing state).

@@ -14,7 +14,8 @@
 //      iteration itself: its rounding is now relative to |d|, which is |rho| / (1 - r), not |x|;
 //   3. x = x~ + d.
 // The error left after a pass is about (1e-7 / (1 - r) + the correction's own tolerance) |d|; passes
-// repeat until |d| / |x| (flow velocity, L1 over gas cells) is below the caller's tolerance.
+// repeat until that estimate (flow velocity, L1 over gas cells, relative to |x|) is below the caller's
+// tolerance, usually after one pass.
 //
 // State buffers per instance (FP64 unless noted), laid out as the correction input rho of
 // InstanceDesc: [4 ncell] moments (rho, u1, u2, tau) | [4 ncell] wall values per (cell, side), the

@@ -9,6 +9,7 @@
 #include <chrono>
 
 #include "dvm.h"
+#include "dvm_kernels.h"
 #include "dvm_sweep.cuh"
 #include "dvm_sweep_cols.cuh"
 
@@ -45,7 +46,51 @@ __global__ void selftest_wait_kernel(int primitive, int spin_limit, int *result)
 }  // namespace
 }  // namespace dvm
 
+// Primitive 2: the persistent launch's scheduler poll (dvm_persist.cu) on one instance that is active
+// but whose only work item is already taken, so no work ever appears; the poll must give up (-1).
+static dvm_status selftest_persist(double *seconds) {
+  using namespace dvm;
+  // work word, finished, left, active, error, order, tile_base, tile_count, fin_items, tiles, result
+  int *mem = nullptr;
+  if (cudaMalloc(&mem, 64 * sizeof(int)) != cudaSuccess) return DVM_ECUDA;
+  int h[64] = {};
+  // work word of instance 0: stage 0, one item taken (ints 0-1); active = 1 (int 5)
+  h[0] = 1;
+  h[5] = 1;
+  h[7] = 0;   // order
+  h[8] = 0;   // tile_base
+  h[9] = 1;   // tile_count
+  h[10] = 1;  // fin_items
+  h[11] = 0;  // tiles
+  PersistDesc P{};
+  P.ninst = 1;
+  P.fin_cells = 1;
+  P.work = reinterpret_cast<unsigned long long *>(mem);
+  P.finished = reinterpret_cast<unsigned int *>(mem + 2);
+  P.left = mem + 4;
+  P.active = mem + 5;
+  P.error = mem + 6;
+  P.order = mem + 7;
+  P.tile_base = mem + 8;
+  P.tile_count = mem + 9;
+  P.fin_items = mem + 10;
+  P.tiles = mem + 11;
+  int *result = mem + 12;
+  h[12] = 7;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaMemcpy(mem, h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_persist_selftest(P, result, 0);
+  int r = 7;
+  if (e == cudaSuccess) e = cudaMemcpy(&r, result, sizeof(int), cudaMemcpyDeviceToHost);
+  const auto t1 = std::chrono::steady_clock::now();
+  cudaFree(mem);
+  if (seconds) *seconds = std::chrono::duration<double>(t1 - t0).count();
+  if (e != cudaSuccess) return DVM_ECUDA;
+  return r == -1 ? DVM_ETIMEOUT : DVM_OK;
+}
+
 extern "C" dvm_status dvm_selftest_wait(int primitive, int spin_limit, double *seconds) {
+  if (primitive == 2) return selftest_persist(seconds);
   if (primitive != 0 && primitive != 1) return DVM_EINVAL;
   int *d_result = nullptr;
   if (cudaMalloc(&d_result, sizeof(int)) != cudaSuccess) return DVM_ECUDA;

@@ -109,9 +109,9 @@ struct Traits<double> {
 };
 
 template <typename T>
-__host__ __device__ inline SweepSmemLayout layout(int warps, int cw) {
+__host__ __device__ inline SweepSmemLayout layout(int warps, int cw, int ntile = 1) {
   return sweep_smem_layout(warps, cw, (int)sizeof(T), (int)sizeof(SweepRec<T>), Traits<T>::kStages,
-                           Traits<T>::kStageSeams ? 1 : 0, Traits<T>::kRingStride);
+                           Traits<T>::kStageSeams ? 1 : 0, Traits<T>::kRingStride, ntile);
 }
 
 // ADJ = false: the forward sweep.  ADJ = true: the transposed sweep of the adjoint iteration --
@@ -119,65 +119,79 @@ __host__ __device__ inline SweepSmemLayout layout(int warps, int cw) {
 // from its forward-downstream cells with the transposed weights t1, t2, the right-hand side is
 // W (A + B v1 + C v2 + D (|v|^2 - 1)) + |v1| W TX + |v2| W TY, the moments are the unweighted sums
 // of (1, v1, v2, |v|^2) z, and cells next to a wall add 2 |v_a|/dx z to that wall's adjoint flux.
-template <typename T, bool UNIF, int CW, bool ADJ>
-__global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(LaunchDesc L) {
+//
+// sweep_tile is one block's share of a sweep: the velocity group(s) named by the sweep-map entry `map`.
+// PER = true: called from the persistent batched kernel (dvm_persist.cu), which hands out tiles of
+// active instances only and whose blocks run many tiles: data written earlier in the same launch by
+// other blocks (seams, the instance state) is read through L2, never from a possibly stale L1 line.
+template <typename T, bool UNIF, int CW, bool ADJ, bool PER>
+__device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigned char *smem, int Rb) {
   constexpr int NSTAGE = Traits<T>::kStages;
   constexpr bool STAGE_SEAM = Traits<T>::kStageSeams;
   constexpr int RS = Traits<T>::kRingStride;
-  const int map = L.sweep_map[blockIdx.x];
   const InstanceDesc *__restrict__ D = L.inst + (map >> 16);
-  const int g = map & 0xfff;
   DeviceState *st = D->state;
-  if (*reinterpret_cast<volatile int *>(&st->done)) return;
+  if (!PER && *reinterpret_cast<volatile int *>(&st->done)) return;
 
   const int nx = D->nx, ny = D->ny, ncell = D->ncell;
   const bool px = D->periodic_x != 0, py = D->periodic_y != 0;
-  const int quad = g / D->groups_per_quadrant;
-  const bool xneg = ((quad & 1) != 0) != ADJ, yneg = ((quad & 2) != 0) != ADJ;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int Rb = blockDim.x >> 5;           // warps of the block (layout)
   const int R = (nx + CW - 1) / CW;         // rows in flight of this instance (host ensures R <= Rb)
+  // A narrow grid leaves warps over: the block sweeps `ntile` consecutive groups side by side, group
+  // g0 + j on warps [j R, (j + 1) R) with its own seam stages, 1/denominator table and weights.
+  const int g0 = map & 0xfff;
+  const int ntile = min(max((map >> 12) & 15, 1), D->ngroups - g0);
+  const int wt = w / R, lw = w - wt * R, wb = wt * R;  // sub-tile, warp within it, its first warp
+  const int g = g0 + wt;
+  const int quad = min(g, D->ngroups - 1) / D->groups_per_quadrant;
+  const bool xneg = ((quad & 1) != 0) != ADJ, yneg = ((quad & 2) != 0) != ADJ;
 
-  extern __shared__ __align__(16) unsigned char smem[];
-  const SweepSmemLayout SL = layout<T>(Rb, CW);
+  const SweepSmemLayout SL = layout<T>(Rb, CW, L.row_tiles > 0 ? L.row_tiles : 1);
   T *ring = reinterpret_cast<T *>(smem + SL.ring);
   SweepRec<T> *stage = reinterpret_cast<SweepRec<T> *>(smem + SL.stage);
   T *seamst = reinterpret_cast<T *>(smem + SL.seam);
-  T *invt = reinterpret_cast<T *>(smem + SL.inv);
-  T *wts = reinterpret_cast<T *>(smem + SL.wts);
+  T *invt_all = reinterpret_cast<T *>(smem + SL.inv);
+  T *wts_all = reinterpret_cast<T *>(smem + SL.wts);
   int *prog = reinterpret_cast<int *>(smem + SL.prog);
 
   // zero the whole dynamic shared memory: ring slots and staged seam entries that are read before
   // (or without) being written are multiplied by zero coefficients and must not hold NaN patterns
-  for (size_t b = threadIdx.x; b < SL.total / 16; b += blockDim.x)
+  for (size_t b = threadIdx.x; b < SL.total / 16; b += (size_t)Rb * kLanes)
     reinterpret_cast<float4 *>(smem)[b] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
-  const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes;
-  if (UNIF) {
-    const T *iv = static_cast<const T *>(D->inv_den) + (size_t)g * kInvRows * kLanes;
-    for (int i = threadIdx.x; i < kInvRows * kLanes; i += blockDim.x) invt[i] = iv[i];
-  }
   constexpr int kMom0 = ADJ ? kZ0 : kW0;  // moment weights: (W, W v1, W v2, W |v|^2) or (1, v1, v2, |v|^2)
-  for (int i = threadIdx.x; i < 4 * kLanes; i += blockDim.x) wts[(i >> 5) * RS + (i & 31)] = vt[(kMom0 + (i >> 5)) * kLanes + (i & 31)];
-  // progress word of warp w = number of steps known finished; warp w starts at step w
-  for (int i = threadIdx.x; i < Rb; i += blockDim.x) prog[i] = i;
+  for (int j = 0; j < ntile; ++j) {
+    const T *vtj = static_cast<const T *>(D->vel) + (size_t)(g0 + j) * kNumVelFields * kLanes;
+    if (UNIF) {
+      const T *iv = static_cast<const T *>(D->inv_den) + (size_t)(g0 + j) * kInvRows * kLanes;
+      for (int i = threadIdx.x; i < kInvRows * kLanes; i += Rb * kLanes) invt_all[j * kInvRows * kLanes + i] = iv[i];
+    }
+    for (int i = threadIdx.x; i < 4 * kLanes; i += Rb * kLanes)
+      wts_all[(j * 4 + (i >> 5)) * RS + (i & 31)] = vtj[(kMom0 + (i >> 5)) * kLanes + (i & 31)];
+  }
+  // progress word of warp w = number of steps known finished; the warp of local row lw starts at step lw
+  for (int i = threadIdx.x; i < Rb; i += Rb * kLanes) prog[i] = i % R;
   __syncthreads();
-  if (w >= R) return;
+  if (wt >= ntile) return;
+  const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes;
+  const T *invt = invt_all + wt * kInvRows * kLanes;
+  const T *wts = wts_all + wt * 4 * RS;
 
   const T v1 = vt[kV1 * kLanes + lane], v2 = vt[kV2 * kLanes + lane], em1 = vt[kE2m1 * kLanes + lane];
   const T cx = vt[kCx * kLanes + lane], cy = vt[kCy * kLanes + lane];
   const T wnx = vt[kWnx * kLanes + lane], wny = vt[kWny * kLanes + lane];
   const T wl = vt[kW0 * kLanes + lane];
-  const T sshift = ADJ ? T(0) : static_cast<T>(st->s);
+  const T cx2 = T(2) * cx, cxh = T(-0.5) * cx, cy2 = T(2) * cy, cyh = T(-0.5) * cy;  // FP64 class weights
+  const T sshift = ADJ ? T(0) : static_cast<T>(__ldcg(&st->s));
   const SweepRec<T> *__restrict__ rec = static_cast<const SweepRec<T> *>(D->rec) + (size_t)quad * ncell;
   T *seamx = static_cast<T *>(D->seam_x) + (size_t)g * ny * 2 * kLanes;
   T *seamy = static_cast<T *>(D->seam_y) + (size_t)g * nx * 2 * kLanes;
   T *hout = D->h ? static_cast<T *>(D->h) + (size_t)g * ncell * kLanes : nullptr;
   double *acc = D->acc;
-  double *facc = D->facc + (size_t)((st->iter + 1) & 1) * ncell * 4;
+  double *facc = D->facc + (size_t)((__ldcg(&st->iter) + 1) & 1) * ncell * 4;
   const int sidex = xneg ? kW : kE;  // wall side hit by this quadrant's velocities along x
   const int sidey = yneg ? kS : kN;
-  const int wprev = (w + R - 1) % R, wnext2 = (w + 2) % R;
+  const int wprev = wb + (lw + R - 1) % R, wnext2 = wb + (lw + 2) % R;
 
   // stage the records of chunk (q, c) into buffer `buf` (and, for rows 0 and 1 of a periodic y
   // axis, the wrapped seam rows); x-seam values of a new row are loaded into registers
@@ -203,14 +217,22 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
     }
     if (STAGE_SEAM && py && q < 2) {
       // row 0 reads rows ny-1, ny-2 (seam slots 1, 0); row 1 reads row ny-1 (slot 1) as h(u2)
-      T *sd = seamst + ((size_t)(w & 1) * NSTAGE + buf) * 2 * CW * kLanes;
+      T *sd = seamst + (((size_t)wt * 2 + (lw & 1)) * NSTAGE + buf) * 2 * CW * kLanes;
 #pragma unroll
       for (int l = 0; l < CW; ++l) {
         if (l < cnt) {
           const int p = p0 + l;
           const int i = xneg ? nx - 1 - p : p;
           const T *s0 = seamy + i * 2 * kLanes + lane;
-          if (q == 0) {
+          if constexpr (PER) {
+            // plain L2 loads (cp.async of 4 bytes would go through L1)
+            if (q == 0) {
+              sd[l * kLanes + lane] = __ldcg(s0 + kLanes);
+              sd[(CW + l) * kLanes + lane] = __ldcg(s0);
+            } else {
+              sd[(CW + l) * kLanes + lane] = __ldcg(s0 + kLanes);
+            }
+          } else if (q == 0) {
             cp_async_small<sizeof(T)>(sd + l * kLanes + lane, s0 + kLanes);
             cp_async_small<sizeof(T)>(sd + (CW + l) * kLanes + lane, s0);
           } else {
@@ -221,8 +243,8 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
     }
     if (c == 0 && px) {
       const T *sx = seamx + j * 2 * kLanes + lane;
-      pf_hp1 = sx[kLanes];  // column nx-1 in sweep order (before its mass shift)
-      pf_hp2 = sx[0];       // column nx-2
+      pf_hp1 = __ldcg(sx + kLanes);  // column nx-1 in sweep order (before its mass shift)
+      pf_hp2 = __ldcg(sx);           // column nx-2
     }
     cp_async_commit();
   };
@@ -242,11 +264,16 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
     }
     const int p0 = c * CW;
     const int cnt = min(CW, nx - p0);
-    // The cell loop has no branches: stencil classes are coefficients in the records; solid cells
+    // The FP32 cell loop has no branches: stencil classes are coefficients in the records; solid cells
     // and the cells past a ragged row end have zero coefficients and sweep to h = 0.  Sub-chunks of
     // SUB cells run in two phases: first everything that does not depend on this row's x-recurrence
     // (records, the two upstream rows, the right-hand side, the y combination, 1/denominator) for all
     // SUB cells, so their shared-memory loads overlap; then the recurrence itself and the ring stores.
+    // FP64 forward sweep (bound by the FP64 pipe): the stencil weights a_k of a cell's classes are
+    // picked as per-lane products |v_a|/dx a_k (selects, no FP64 arithmetic), and the wall terms are
+    // added only at wall-class cells (a warp-uniform branch: every lane visits the same cell), so an
+    // interior update costs 3 FMA (right-hand side) + 4 FMA (upwind terms) + 1 MUL.
+    constexpr bool FAST64 = sizeof(T) == 8 && !ADJ;
     constexpr int SUB = (sizeof(T) == 4) ? (CW < 8 ? CW : 8) : (CW < 2 ? CW : 2);
 #pragma unroll
     for (int l0 = 0; l0 < CW; l0 += SUB) {
@@ -260,43 +287,51 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
           hq1 = pr1[l * ps1 + lane];
           hq2 = pr2[l * ps2 + lane];
         } else if (MODE == 1) {
-          hq1 = l < cnt ? pr1[l * ps1] - sshift : T(0);
-          hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
+          hq1 = l < cnt ? __ldcg(pr1 + l * ps1) - sshift : T(0);
+          hq2 = l < cnt ? __ldcg(pr2 + l * ps2) - sshift : T(0);
         } else {
           hq1 = pr1[l * ps1 + lane];
-          hq2 = l < cnt ? pr2[l * ps2] - sshift : T(0);
-        }
-        T ay1, ay2;
-        if constexpr (sizeof(T) == 4) {
-          cax1[u] = r.ax1;
-          cax2[u] = r.ax2;
-          ay1 = r.ay1;
-          ay2 = r.ay2;
-        } else if constexpr (!ADJ) {
-          const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
-          const bool solid = (r.code & kSolid) != 0;
-          cax1[u] = solid ? T(0) : T(class_a1(clx));
-          cax2[u] = solid ? T(0) : T(class_a2(clx));
-          ay1 = solid ? T(0) : T(class_a1(cly));
-          ay2 = solid ? T(0) : T(class_a2(cly));
-        } else {
-          cax1[u] = T((r.code >> kAdjT1XShift) & 3);
-          cax2[u] = (r.code & kAdjT2X) ? T(-0.5) : T(0);
-          ay1 = T((r.code >> kAdjT1YShift) & 3);
-          ay2 = (r.code & kAdjT2Y) ? T(-0.5) : T(0);
+          hq2 = l < cnt ? __ldcg(pr2 + l * ps2) - sshift : T(0);
         }
         T Rk = fma(r.D, em1, fma(r.C, v2, fma(r.B, v1, r.A)));
-        T by;
-        if constexpr (ADJ) {
-          // the incident-wall terms ride in the xw / yw slots of adjoint records
-          Rk = fma(wnx, r.xw, fma(wny, r.yw, wl * Rk));
+        if constexpr (FAST64) {
+          const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
+          const bool solid = (r.code & kSolid) != 0;
+          // class a1 = 2, 1, 0 and a2 = -1/2, 0, 0 (interior, second cell, next to a wall), times |v_a|/dx
+          const T y1 = solid ? T(0) : (cly == kFull ? cy2 : (cly == kNear ? cy : T(0)));
+          const T y2 = (!solid && cly == kFull) ? cyh : T(0);
+          cax1[u] = solid ? T(0) : (clx == kFull ? cx2 : (clx == kNear ? cx : T(0)));
+          cax2[u] = (!solid && clx == kFull) ? cxh : T(0);
+          T b = fma(y1, hq1, fma(y2, hq2, Rk));
+          if (!solid && cly == kWall) b = fma(cy, r.yw, b);
+          if (!solid && clx == kWall) b = fma(cx, r.xw, b);
+          base[u] = b;
           cxw[u] = T(0);
-          by = fma(ay1, hq1, ay2 * hq2);
         } else {
-          cxw[u] = r.xw;
-          by = fma(ay1, hq1, fma(ay2, hq2, r.yw));
+          T ay1, ay2;
+          if constexpr (sizeof(T) == 4) {
+            cax1[u] = r.ax1;
+            cax2[u] = r.ax2;
+            ay1 = r.ay1;
+            ay2 = r.ay2;
+          } else {
+            cax1[u] = T((r.code >> kAdjT1XShift) & 3);
+            cax2[u] = (r.code & kAdjT2X) ? T(-0.5) : T(0);
+            ay1 = T((r.code >> kAdjT1YShift) & 3);
+            ay2 = (r.code & kAdjT2Y) ? T(-0.5) : T(0);
+          }
+          T by;
+          if constexpr (ADJ) {
+            // the incident-wall terms ride in the xw / yw slots of adjoint records
+            Rk = fma(wnx, r.xw, fma(wny, r.yw, wl * Rk));
+            cxw[u] = T(0);
+            by = fma(ay1, hq1, ay2 * hq2);
+          } else {
+            cxw[u] = r.xw;
+            by = fma(ay1, hq1, fma(ay2, hq2, r.yw));
+          }
+          base[u] = fma(cy, by, Rk);
         }
-        base[u] = fma(cy, by, Rk);
         if (UNIF) {
           invv[u] = invt[((r.code >> kInvShift) & 15) * kLanes + lane];
         } else {
@@ -306,8 +341,13 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
       }
 #pragma unroll
       for (int u = 0; u < SUB; ++u) {
-        const T bx = fma(cax1[u], hp1, fma(cax2[u], hp2, cxw[u]));
-        const T h = fma(cx, bx, base[u]) * invv[u];
+        T h;
+        if constexpr (FAST64) {
+          h = fma(cax1[u], hp1, fma(cax2[u], hp2, base[u])) * invv[u];
+        } else {
+          const T bx = fma(cax1[u], hp1, fma(cax2[u], hp2, cxw[u]));
+          h = fma(cx, bx, base[u]) * invv[u];
+        }
         hp2 = hp1;
         hp1 = h;
         myr[(l0 + u) * RS + lane] = h;
@@ -394,8 +434,8 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
   };
 
   int item = 0;
-  if (NSTAGE == 2) issue(w, 0, 0);
-  for (int q = w; q < ny; q += R) {
+  if (NSTAGE == 2) issue(lw, 0, 0);
+  for (int q = lw; q < ny; q += R) {
     for (int c = 0; c < R; ++c, ++item) {
       const int t = q + c;
       const int buf = (NSTAGE == 2) ? (item & 1) : 0;
@@ -425,10 +465,10 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
       const SweepRec<T> *rs = stage + ((size_t)w * NSTAGE + buf) * CW;
       T *myr = ring + ((size_t)w * 3 + (t % 3)) * CW * RS;
       const T *pr1 = ring + ((size_t)wprev * 3 + ((t + 2) % 3)) * CW * RS;
-      const T *pr2 = ring + ((size_t)((w + 2 * R - 2) % R) * 3 + ((t + 1) % 3)) * CW * RS;
+      const T *pr2 = ring + ((size_t)(wb + (lw + 2 * R - 2) % R) * 3 + ((t + 1) % 3)) * CW * RS;
       if (py && q < 2) {
         if (STAGE_SEAM) {
-          T *sd = seamst + ((size_t)(w & 1) * NSTAGE + buf) * 2 * CW * kLanes;
+          T *sd = seamst + (((size_t)wt * 2 + (lw & 1)) * NSTAGE + buf) * 2 * CW * kLanes;
           const int cnt = min(CW, nx - c * CW);
           // the staged seam values are the previous iterate before its mass shift (own lane only)
           for (int l = 0; l < cnt; ++l) {
@@ -459,9 +499,15 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(Launc
 }
 
 template <typename T, bool UNIF, int CW, bool ADJ>
+__global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(LaunchDesc L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  sweep_tile<T, UNIF, CW, ADJ, false>(L, L.sweep_map[blockIdx.x], smem, (int)(blockDim.x >> 5));
+}
+
+template <typename T, bool UNIF, int CW, bool ADJ>
 cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   auto kern = sweep_kernel<T, UNIF, CW, ADJ>;
-  const size_t smem = layout<T>(L.warps, CW).total;
+  const size_t smem = layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<nblocks, L.warps * kLanes, smem, stream>>>(L);

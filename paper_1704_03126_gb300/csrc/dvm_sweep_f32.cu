@@ -3,7 +3,7 @@
 
 namespace dvm {
 
-size_t sweep_smem_bytes_f32(int warps, int cw) { return sweep::layout<float>(warps, cw).total; }
+size_t sweep_smem_bytes_f32(int warps, int cw, int ntile) { return sweep::layout<float>(warps, cw, ntile).total; }
 
 cudaError_t launch_sweep_f32(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   return uniform_delta ? sweep::launch_cw<float, true, false>(L, nblocks, stream)

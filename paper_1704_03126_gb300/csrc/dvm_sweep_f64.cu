@@ -3,7 +3,7 @@
 
 namespace dvm {
 
-size_t sweep_smem_bytes_f64(int warps, int cw) { return sweep::layout<double>(warps, cw).total; }
+size_t sweep_smem_bytes_f64(int warps, int cw, int ntile) { return sweep::layout<double>(warps, cw, ntile).total; }
 
 cudaError_t launch_sweep_f64(bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   return uniform_delta ? sweep::launch_cw<double, true, false>(L, nblocks, stream)
@@ -15,8 +15,8 @@ cudaError_t launch_sweep_adjoint_f64(bool uniform_delta, const LaunchDesc &L, in
                        : sweep::launch_cw<double, false, true>(L, nblocks, stream);
 }
 
-size_t sweep_smem_bytes(bool fp64, int warps, int cw) {
-  return fp64 ? sweep_smem_bytes_f64(warps, cw) : sweep_smem_bytes_f32(warps, cw);
+size_t sweep_smem_bytes(bool fp64, int warps, int cw, int ntile) {
+  return fp64 ? sweep_smem_bytes_f64(warps, cw, ntile) : sweep_smem_bytes_f32(warps, cw, ntile);
 }
 
 cudaError_t launch_sweep(bool fp64, bool uniform_delta, const LaunchDesc &L, int nblocks, cudaStream_t stream) {

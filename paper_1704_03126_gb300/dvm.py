@@ -8,6 +8,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import sys
 
 import numpy as np
 
@@ -102,13 +103,16 @@ def lib():
         L.dvm_batch_autotune.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
         L.dvm_selftest_wait.argtypes = [I, I, ctypes.POINTER(D)]
         L.dvm_probe_peaks.argtypes = [I, D, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.dvm_batch_set_persistent.argtypes = [P, I]
+        L.dvm_batch_get_persistent.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
                      "dvm_batch_run", "dvm_batch_iterate", "dvm_batch_timing", "dvm_moments",
                      "dvm_moments_noalloc", "dvm_adjoint", "dvm_set_schedule", "dvm_get_schedule",
                      "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune",
-                     "dvm_batch_enqueue", "dvm_batch_check", "dvm_selftest_wait", "dvm_probe_peaks"):
+                     "dvm_batch_enqueue", "dvm_batch_check", "dvm_selftest_wait", "dvm_probe_peaks",
+                     "dvm_batch_set_persistent", "dvm_batch_get_persistent"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -280,6 +284,9 @@ class Solver:
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):
+        # at interpreter shutdown the CUDA runtime may already be torn down; the process exit frees all
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -359,6 +366,22 @@ class Batch:
             self._err(st)
         return SWEEP_NAMES[k.value], v.value
 
+    def set_persistent(self, on=True):
+        """One persistent launch per up to 64 sweeps with a device-side scheduler (row sweep only); see
+        dvm_batch_set_persistent."""
+        self._touch()
+        st = lib().dvm_batch_set_persistent(self._b, int(bool(on)))
+        if st != DVM_OK:
+            self._err(st)
+
+    def persistent(self):
+        """(on, blocks of the persistent launch)."""
+        on, blocks = ctypes.c_int(), ctypes.c_int()
+        st = lib().dvm_batch_get_persistent(self._b, ctypes.byref(on), ctypes.byref(blocks))
+        if st != DVM_OK:
+            self._err(st)
+        return bool(on.value), blocks.value
+
     def autotune(self, sweeps=5):
         """Time every fitting sweep kernel (the trial sweeps advance the state); keeps the fastest.
         Returns (kind, shape, median sweep ms); shape is the chunk width for "rows"."""
@@ -375,6 +398,9 @@ class Batch:
             self._b = ctypes.c_void_p()
 
     def __del__(self):
+        # at interpreter shutdown the CUDA runtime may already be torn down; the process exit frees all
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
