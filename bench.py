@@ -75,7 +75,12 @@ FLOPS_PER_UPDATE = {"fp32": 25, "fp64": 25}
 # DRAM bytes (read + write) of one sweep-kernel launch from ncu, keyed by (workload, precision, kernel,
 # shape), each with the hash of the sweep kernels' sources it was measured on (kernel_source_hash);
 # a figure whose hash no longer matches is reported as null
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("batched", "fp32", "rows", 16): {"bytes": 706.2e6, "src": "63bd69a5f5e6b266"},
+    ("porous", "fp32", "rows", 16): {"bytes": 73.58e6, "src": "63bd69a5f5e6b266"},
+    ("rough", "fp32", "rows", 8): {"bytes": 14.36e6, "src": "63bd69a5f5e6b266"},
+    ("rough", "fp64", "rows", 8): {"bytes": 21.00e6, "src": "63bd69a5f5e6b266"},
+}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -97,6 +102,8 @@ def parse():
     ap.add_argument("--anderson", type=int, default=0,
                     help="mix the timed iterates with Anderson mixing of this depth (0 = the paper's plain "
                          "iteration; needs --precision fp64, times that precision only)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="time the main workload in the persistent launch (row sweep; profiling runs)")
     return ap.parse_args()
 
 
@@ -400,6 +407,10 @@ def run_ours(args, rank, world, local_rank):
         solvers = [solver(dvm, inst, precision, stream.cuda_stream, anderson=args.anderson) for inst in insts]
         batch = dvm.Batch(solvers)
         sched = apply_schedule(batch, args.schedule)
+        if args.persistent and workload == args.workload and precision == args.precision:
+            batch.set_schedule("rows", sched["shape"] if sched["kernel"] == "rows" else 0)
+            batch.set_persistent(True)
+            sched = dict(sched, persistent=True)
         total_ms, sweep_ms, fin_ms, wsteps = timed_steps(batch, steps, warmup)
         clocks = sampler.stop() if sampler is not None else None
         total_ms = max_over_ranks(total_ms, world, device="cuda")
