@@ -14,6 +14,8 @@ namespace dvm {
 struct SweepSmemLayout {
   size_t ring, stage, seam, inv, wts, prog, total;
 };
+// rows of the per-group weight table: the four moment weights, then the x and y wall-flux weights
+constexpr int kSweepWtsRows = 6;
 
 __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int tsize, int recsize, int nstage,
                                                              int stage_seams, int ring_stride, int ntile = 1) {
@@ -29,7 +31,7 @@ __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int 
   L.inv = off;
   off = align16(off + (size_t)ntile * kInvRows * kLanes * tsize);  // rows 0-8: stencil classes, row 9: solid (0)
   L.wts = off;
-  off = align16(off + (size_t)ntile * 4 * ring_stride * tsize);
+  off = align16(off + (size_t)ntile * kSweepWtsRows * ring_stride * tsize);
   L.prog = off;
   off = align16(off + (size_t)R * sizeof(int));
   L.total = off;

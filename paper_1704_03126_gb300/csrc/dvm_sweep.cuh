@@ -79,6 +79,28 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Dot product over the 32 velocities of a group: h values of one cell (a ring row) with one weight row,
+// both in shared memory.  FP32: float4 loads and packed FP32x2 FMAs in two interleaved partial sums.
+template <typename T, int RS>
+__device__ __forceinline__ T dot32(const T *hr, const T *wr) {
+  if constexpr (RS % 4 == 0 && sizeof(T) == 4) {
+    float2 s2a = make_float2(0.f, 0.f), s2b = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kLanes; k += 4) {
+      const float4 a = *reinterpret_cast<const float4 *>(hr + k);
+      const float4 b = *reinterpret_cast<const float4 *>(wr + k);
+      s2a = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), s2a);
+      s2b = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), s2b);
+    }
+    return (s2a.x + s2b.x) + (s2a.y + s2b.y);
+  } else {
+    T sum = T(0);
+#pragma unroll
+    for (int k = 0; k < kLanes; ++k) sum = fma(wr[k], hr[k], sum);
+    return sum;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T kappa_of(int cls) {
   return cls == kFull ? T(1.5) : (cls == kNear ? T(1.0) : T(2.0));
@@ -167,7 +189,13 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
       for (int i = threadIdx.x; i < kInvRows * kLanes; i += Rb * kLanes) invt_all[j * kInvRows * kLanes + i] = iv[i];
     }
     for (int i = threadIdx.x; i < 4 * kLanes; i += Rb * kLanes)
-      wts_all[(j * 4 + (i >> 5)) * RS + (i & 31)] = vtj[(kMom0 + (i >> 5)) * kLanes + (i & 31)];
+      wts_all[(j * kSweepWtsRows + (i >> 5)) * RS + (i & 31)] = vtj[(kMom0 + (i >> 5)) * kLanes + (i & 31)];
+    // wall-flux weights: forward |v_n| W (incident flux), adjoint 2 |v_a| / dx (transposed wall read)
+    for (int i = threadIdx.x; i < 2 * kLanes; i += Rb * kLanes) {
+      const int ax = i >> 5, ln = i & 31;
+      wts_all[(j * kSweepWtsRows + 4 + ax) * RS + ln] =
+          ADJ ? T(2) * vtj[(ax ? kCy : kCx) * kLanes + ln] : vtj[(ax ? kWny : kWnx) * kLanes + ln];
+    }
   }
   // progress word of warp w = number of steps known finished; the warp of local row lw starts at step lw
   for (int i = threadIdx.x; i < Rb; i += Rb * kLanes) prog[i] = i % R;
@@ -175,7 +203,7 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
   if (wt >= ntile) return;
   const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes;
   const T *invt = invt_all + wt * kInvRows * kLanes;
-  const T *wts = wts_all + wt * 4 * RS;
+  const T *wts = wts_all + wt * kSweepWtsRows * RS;
 
   const T v1 = vt[kV1 * kLanes + lane], v2 = vt[kV2 * kLanes + lane], em1 = vt[kE2m1 * kLanes + lane];
   const T cx = vt[kCx * kLanes + lane], cy = vt[kCy * kLanes + lane];
@@ -382,48 +410,38 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
       const uint32_t mycode = lane < cnt ? rs[lane].code : 0u;
       const bool fx = ADJ ? (((mycode >> kClsXShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncX) != 0;
       const bool fy = ADJ ? (((mycode >> kClsYShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncY) != 0;
-      unsigned incx = __ballot_sync(0xffffffffu, fx);
-      unsigned incy = __ballot_sync(0xffffffffu, fy);
-      const T weight_x = ADJ ? T(2) * cx : wnx, weight_y = ADJ ? T(2) * cy : wny;
-      while (incx | incy) {
-        const bool is_x = incx != 0;
-        const int l = __ffs(is_x ? incx : incy) - 1;
-        if (is_x) incx &= incx - 1;
-        else incy &= incy - 1;
-        const T f = warp_sum<T>((is_x ? weight_x : weight_y) * myr[l * RS + lane]);
-        if (lane == 0) {
-          const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
-          red_add(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
-        }
+      const unsigned incx = __ballot_sync(0xffffffffu, fx);
+      const unsigned incy = __ballot_sync(0xffffffffu, fy);
+      // one wall face per lane (at most 2 CW faces): the dot product over the velocities read back
+      // from the ring, like a moment
+      const int nfx = __popc(incx), nf = nfx + __popc(incy);
+      for (int e = lane; e < nf; e += kLanes) {
+        const bool is_x = e < nfx;
+        const int l = (int)__fns(is_x ? incx : incy, 0u, is_x ? e + 1 : e - nfx + 1);
+        const T f = dot32<T, RS>(myr + l * RS, wts + (is_x ? 4 : 5) * RS);
+        const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
+        red_add(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
       }
     }
-    // moments of the chunk: one (cell, moment) pair per lane and pass, dot product over the lanes
+    // moments of the chunk: one (cell, moment) pair per lane and pass, dot product over the lanes.
+    // All passes' dot products first (their shared-memory loads can overlap; rows past the chunk are
+    // clamped to its last cell and their sums dropped), then the global reductions.
+    constexpr int NPASS = (CW * 4 + kLanes - 1) / kLanes;
+    T msum[NPASS];
 #pragma unroll
-    for (int pass = 0; pass < (CW * 4 + kLanes - 1) / kLanes; ++pass) {
+    for (int pass = 0; pass < NPASS; ++pass) {
+      const int pr = pass * kLanes + lane;
+      const int l = min(pr >> 2, CW - 1), m = pr & 3;
+      msum[pass] = dot32<T, RS>(myr + l * RS, wts + m * RS);
+    }
+#pragma unroll
+    for (int pass = 0; pass < NPASS; ++pass) {
       const int pr = pass * kLanes + lane;
       const int l = pr >> 2, m = pr & 3;
       if (pr < CW * 4 && l < cnt && !(rs[l].code & kSolid)) {
-        const T *hr = myr + l * RS;
-        const T *wr = wts + m * RS;
-        T sum = T(0);
-        if constexpr (RS % 4 == 0 && sizeof(T) == 4) {
-          // packed FP32x2 FMAs: two interleaved partial sums
-          float2 s2a = make_float2(0.f, 0.f), s2b = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int k = 0; k < kLanes; k += 4) {
-            const float4 a = *reinterpret_cast<const float4 *>(hr + k);
-            const float4 b = *reinterpret_cast<const float4 *>(wr + k);
-            s2a = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), s2a);
-            s2b = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), s2b);
-          }
-          sum = (s2a.x + s2b.x) + (s2a.y + s2b.y);
-        } else {
-#pragma unroll
-          for (int k = 0; k < kLanes; ++k) sum = fma(wr[k], hr[k], sum);
-        }
         const int p = p0 + l;
         const int i = xneg ? nx - 1 - p : p;
-        red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(sum));
+        red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(msum[pass]));
       }
     }
   };

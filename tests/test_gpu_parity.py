@@ -314,6 +314,35 @@ def test_wide_grid_runs_on_the_column_sweep_only():
 
 # ------------------------------------------------------------------ full-size workloads
 
+@pytest.mark.parametrize("schedule", [("rows", 0), ("columns", 2)], ids=["rows", "cols2"])
+def test_rough_channel_full_size_converged_fp64(schedule):
+    """The benchmark's rough channel at full size (128 x 128 cells, 32 x 32 trapezoid velocities on
+    [-5, 5]), Kn = 1, FP64: the converged GPU fixed point against the oracle's converged solve, Q to
+    1e-10 and every field to 1e-9 (the FP64 bar)."""
+    inst = inputs.rough_instance(1.0)
+    sol, orc, iters = _solve_both(inst.mask, True, False, 1.0, inst.quad, "fp64", 1e-12, schedule=schedule)
+    _compare(sol, orc, inst.mask, "fp64")
+
+
+def test_porous_full_size_iterates_fp32():
+    """The benchmark's porous medium at full size (256 x 256 disk medium, porosity 0.6, cubic 48 x 48
+    velocities), Kn = 0.5, FP32 storage: its source iteration converges in about 1300 sweeps, too many
+    for the oracle here, so both run the same 20 sweeps from h = 0 (the same iteration with the same
+    lagging) and the iterates are compared: Q to 1e-5 of the flow scale and every field to 1e-4 of
+    max |u1| (the FP32 bar)."""
+    inst = inputs.porous_instance(0.5)
+    sol = dvm.Solver(inst.mask, True, True, kn=0.5, quad=inst.quad, precision="fp32")
+    sol.iterate(20)
+    orc = oracle.solve(_oracle_problem(inst.mask, True, True, dvm.kn_to_delta(0.5), inst.quad), tol=0.0, max_iter=20)
+    assert orc["iters"] == 20 and sol.info()["iterations"] == 20
+    gas = inst.mask == 0
+    scale = np.abs(orc["u1"][gas]).max()
+    assert abs(sol.flowrate()[0] - orc["Q"]) < 1e-5 * _flow_scale(orc, inst.mask)
+    f = sol.fields()
+    for name in ("rho", "u1", "u2", "tau"):
+        assert np.abs(f[name][gas] - orc[name][gas]).max() < 1e-4 * scale, name
+
+
 def test_rough_channel_full_size_fixed_point():
     """Rough channel 128 x 128, 32 x 32 trapezoid velocities on [-5, 5], Kn = 1, in the launch
     configuration the benchmark times (FP32 storage).  At this size the oracle checks, velocity by
