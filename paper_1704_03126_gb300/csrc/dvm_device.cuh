@@ -24,7 +24,8 @@ enum : uint32_t {
   kClsYShift = 3,
   kIncX = 1u << 5, // the cell owns a wall face on its downstream x side (incident for this quadrant)
   kIncY = 1u << 6,
-  kInvShift = 8,   // 4 bits: row of the 1/denominator table, clx * 3 + cly, or 9 (solid: 0)
+  kInvShift = 7,   // 4 bits: row of the 1/denominator table, clx * 3 + cly, or 9 (solid: 0); at bit 7
+                   // code & (15 << 7) is the row's byte offset in an FP32 table of 32-entry rows
   // Transposed stencil (adjoint sweep): the forward-downstream cells d1 = c + s and d2 = c + 2 s
   // read c with weights t1 in {0, 1, 2} (d1 solid / second cell from a wall / interior) and
   // t2 in {0, -1/2} (d1 or d2 solid / interior).

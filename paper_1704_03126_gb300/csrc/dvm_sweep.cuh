@@ -101,6 +101,70 @@ __device__ __forceinline__ T dot32(const T *hr, const T *wr) {
   }
 }
 
+// FP32 per-cell sums on the tensor cores.  The h values of a finished chunk sit in the ring as a
+// CW x 32 tile (cell x velocity); the four moments and the two wall fluxes of every cell are that tile
+// times a 32 x 6 weight matrix, a small dense contraction: one m16n8k8 TF32 mma per 8 velocities, with
+// each FP32 operand split into a TF32 head and a TF32 tail (hi*hi + hi*lo + lo*hi, error a few FP32
+// ulps of the products).  ldmatrix reads the tile once (16 cells x 32 velocities = 16 shared-memory
+// wavefronts); the weights stay in registers as B fragments.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// B fragments of the weight matrix B[k][n] = weight row n (0-5; 6, 7 zero) at velocity k of the group:
+// for k-step s, lane (n = lane / 4, t = lane % 4) holds B[8 s + t][n] and B[8 s + t + 4][n], each as
+// TF32 head and tail: bf[s] = {hi0, hi1, lo0, lo1}.
+template <int RS>
+__device__ __forceinline__ void weight_fragments(const float *wts, int lane, uint32_t (&bf)[4][4]) {
+  const int n = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float w = n < kSweepWtsRows ? wts[n * RS + 8 * s + t + 4 * e] : 0.f;
+      const uint32_t hi = tf32_rna(w);
+      bf[s][e] = hi;
+      bf[s][2 + e] = tf32_rna(w - __uint_as_float(hi));
+    }
+  }
+}
+// d = the tile times the weights.  `base`: this lane's ldmatrix row address for k-step 0 (lanes
+// 8 m .. 8 m + 7 address the rows of matrix m: cells 0-7 / 8-15 of the chunk (rows past the chunk
+// repeat its last cell) at velocities 0-3 / 4-3 + 4 of the k-step).  Lane (g = lane / 4, t = lane % 4)
+// gets columns 2t, 2t+1 of cells g (d0, d1) and g + 8 (d2, d3).
+__device__ __forceinline__ void cell_sums_mma(uint32_t base, const uint32_t (&bf)[4][4], float (&d)[4]) {
+  d[0] = d[1] = d[2] = d[3] = 0.f;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    uint32_t a[4], ah[4], al[4];
+    ldsm_x4(base + s * 32, a);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // head: x rounded to TF32 (round half away from zero on the bit pattern); tail: the exact
+      // remainder, which the mma truncates to TF32
+      ah[i] = (a[i] + 0x1000u) & 0xffffe000u;
+      al[i] = __float_as_uint(__uint_as_float(a[i]) - __uint_as_float(ah[i]));
+    }
+    mma_tf32(d, al, bf[s][0], bf[s][1]);
+    mma_tf32(d, ah, bf[s][2], bf[s][3]);
+    mma_tf32(d, ah, bf[s][0], bf[s][1]);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T kappa_of(int cls) {
   return cls == kFull ? T(1.5) : (cls == kNear ? T(1.0) : T(2.0));
@@ -202,7 +266,7 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
   __syncthreads();
   if (wt >= ntile) return;
   const T *vt = static_cast<const T *>(D->vel) + (size_t)g * kNumVelFields * kLanes;
-  const T *invt = invt_all + wt * kInvRows * kLanes;
+  const T *invt_lane = invt_all + wt * kInvRows * kLanes + lane;
   const T *wts = wts_all + wt * kSweepWtsRows * RS;
 
   const T v1 = vt[kV1 * kLanes + lane], v2 = vt[kV2 * kLanes + lane], em1 = vt[kE2m1 * kLanes + lane];
@@ -220,28 +284,73 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
   const int sidex = xneg ? kW : kE;  // wall side hit by this quadrant's velocities along x
   const int sidey = yneg ? kS : kN;
   const int wprev = wb + (lw + R - 1) % R, wnext2 = wb + (lw + 2) % R;
+  // FP32 per-cell sums (cell_sums_mma): the weight fragments, this lane's ldmatrix row in a ring slot,
+  // and where its two result columns go -- lanes t = 0, 1: moments 2t, 2t+1; t = 2: the x and y wall
+  // fluxes; t = 3: nothing -- each at the cells whose code satisfies (code & am) == cv
+  uint32_t bfr[4][4];
+  if constexpr (sizeof(T) == 4) weight_fragments<RS>(reinterpret_cast<const float *>(wts), lane, bfr);
+  const int t4 = lane & 3, g4 = lane >> 2;
+  const uint32_t ldsm_off =
+      (uint32_t)((min((lane & 7) + 8 * ((lane >> 3) & 1), CW - 1) * RS + 4 * (lane >> 4)) * (int)sizeof(T));
+  double *const red_base = t4 == 2 ? facc : acc;
+  double *const red_p0 = red_base + (t4 == 2 ? sidex : 2 * t4);
+  double *const red_p1 = red_base + (t4 == 2 ? sidey : 2 * t4 + 1);
+  // moments: gas cells; forward fluxes: the cell owns a downstream wall face; adjoint fluxes: the
+  // cell's class is "next to a wall" (upstream neighbour solid); lanes t = 3: never ((code & 0) == 1)
+  uint32_t red_am0 = kSolid, red_cv0 = 0u, red_am1 = kSolid, red_cv1 = 0u;
+  if (t4 == 2) {
+    if (ADJ) {
+      red_am0 = kSolid | (3u << kClsXShift);
+      red_cv0 = (uint32_t)kWall << kClsXShift;
+      red_am1 = kSolid | (3u << kClsYShift);
+      red_cv1 = (uint32_t)kWall << kClsYShift;
+    } else {
+      red_am0 = red_cv0 = kIncX;
+      red_am1 = red_cv1 = kIncY;
+    }
+  } else if (t4 == 3) {
+    red_am0 = red_am1 = 0u;
+    red_cv0 = red_cv1 = 1u;
+  }
 
   // stage the records of chunk (q, c) into buffer `buf` (and, for rows 0 and 1 of a periodic y
   // axis, the wrapped seam rows); x-seam values of a new row are loaded into registers
   T pf_hp1 = T(0), pf_hp2 = T(0);
+  // record staging of a full chunk: piece lane + 32 k (16 bytes) of the chunk's contiguous records goes
+  // to byte st_dst[k] of the stage buffer
+  constexpr int NPC = (int)sizeof(SweepRec<T>) / 16, NPIECE = NPC * CW, PPL = (NPIECE + kLanes - 1) / kLanes;
+  int st_dst[PPL];
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int pc = lane + k * kLanes, r = pc / NPC, l = xneg ? CW - 1 - r : r;
+    st_dst[k] = l * (int)sizeof(SweepRec<T>) + 16 * (pc - r * NPC);
+  }
   auto issue = [&](int q, int c, int buf) {
     const int j = yneg ? ny - 1 - q : q;
     SweepRec<T> *sdst = stage + ((size_t)w * NSTAGE + buf) * CW;
     const int p0 = c * CW;
     const int cnt = min(CW, nx - p0);
-    if (lane < cnt) {
-      const int p = p0 + lane;
-      const int i = xneg ? nx - 1 - p : p;
-      const char *src = reinterpret_cast<const char *>(rec + j * nx + i);
-      char *dst = reinterpret_cast<char *>(sdst + lane);
+    // the chunk's records are one contiguous run of cnt records in memory (cells i_lo .. i_lo + cnt - 1
+    // of row j): the lanes copy consecutive 16-byte pieces of it (coalesced), each into the slot of its
+    // record in sweep order
+    const char *src = reinterpret_cast<const char *>(rec + j * nx + (xneg ? nx - p0 - cnt : p0));
+    if (cnt == CW) {
 #pragma unroll
-      for (int b = 0; b < (int)sizeof(SweepRec<T>); b += 16) cp_async16(dst + b, src + b);
-    } else if (lane < CW) {
-      // past the ragged end of the row: a solid record (zero coefficients) sweeps to h = 0
-      float4 *dst = reinterpret_cast<float4 *>(sdst + lane);
+      for (int k = 0; k < PPL; ++k)
+        if (NPIECE % kLanes == 0 || lane + k * kLanes < NPIECE)
+          cp_async16(reinterpret_cast<char *>(sdst) + st_dst[k], src + 16 * (lane + k * kLanes));
+    } else {
+      for (int pc = lane; pc < NPC * cnt; pc += kLanes) {
+        const int r = pc / NPC, l = xneg ? cnt - 1 - r : r;
+        cp_async16(reinterpret_cast<char *>(sdst + l) + 16 * (pc - r * NPC), src + 16 * pc);
+      }
+      if (lane >= cnt && lane < CW) {
+        // past the ragged end of the row: a solid record (zero coefficients) sweeps to h = 0
+        float4 *dst = reinterpret_cast<float4 *>(sdst + lane);
 #pragma unroll
-      for (int b = 0; b < (int)(sizeof(SweepRec<T>) / 16); ++b) dst[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-      sdst[lane].code = kSolid | (9u << kInvShift);
+        for (int b = 0; b < NPC; ++b) dst[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sdst[lane].code = kSolid | (9u << kInvShift);
+      }
     }
     if (STAGE_SEAM && py && q < 2) {
       // row 0 reads rows ny-1, ny-2 (seam slots 1, 0); row 1 reads row ny-1 (slot 1) as h(u2)
@@ -361,7 +470,9 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
           base[u] = fma(cy, by, Rk);
         }
         if (UNIF) {
-          invv[u] = invt[((r.code >> kInvShift) & 15) * kLanes + lane];
+          // row (code >> kInvShift) & 15 of the table, as a byte offset: 128-byte rows (FP32), 256 (FP64)
+          const uint32_t boff = (r.code & (15u << kInvShift)) << (sizeof(T) == 8 ? 1 : 0);
+          invv[u] = *reinterpret_cast<const T *>(reinterpret_cast<const char *>(invt_lane) + boff);
         } else {
           const int clx = (r.code >> kClsXShift) & 3, cly = (r.code >> kClsYShift) & 3;
           invv[u] = recip<T>(r.delta + cx * kappa_of<T>(clx) + cy * kappa_of<T>(cly));
@@ -404,44 +515,65 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
         seamy[(i * 2 + (q - (ny - 2))) * kLanes + lane] = myr[l * RS + lane];
       }
     }
-    {
-      // forward: incident flux sum |v_n| W h at cells owning a downstream wall face; adjoint: the
-      // transposed wall reads, sum 2 |v_a|/dx z at cells whose upstream neighbour is solid
-      const uint32_t mycode = lane < cnt ? rs[lane].code : 0u;
-      const bool fx = ADJ ? (((mycode >> kClsXShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncX) != 0;
-      const bool fy = ADJ ? (((mycode >> kClsYShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncY) != 0;
-      const unsigned incx = __ballot_sync(0xffffffffu, fx);
-      const unsigned incy = __ballot_sync(0xffffffffu, fy);
-      // one wall face per lane (at most 2 CW faces): the dot product over the velocities read back
-      // from the ring, like a moment
-      const int nfx = __popc(incx), nf = nfx + __popc(incy);
-      for (int e = lane; e < nf; e += kLanes) {
-        const bool is_x = e < nfx;
-        const int l = (int)__fns(is_x ? incx : incy, 0u, is_x ? e + 1 : e - nfx + 1);
-        const T f = dot32<T, RS>(myr + l * RS, wts + (is_x ? 4 : 5) * RS);
-        const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
-        red_add(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
+    if constexpr (sizeof(T) == 4) {
+      // The six sums of every cell of the chunk on the tensor cores (four moments; forward: the
+      // incident flux sum |v_n| W h at cells owning a downstream wall face; adjoint: the transposed
+      // wall reads, sum 2 |v_a|/dx z at cells whose upstream neighbour is solid), added to the FP64
+      // accumulators by the lanes holding them.
+      float d[4];
+      cell_sums_mma(smem_u32(myr) + ldsm_off, bfr, d);
+      // element offset (cell * 4) of this lane's first cell, g, and the step to its second, g + 8
+      const int e0 = (j * nx + (xneg ? nx - 1 - p0 - g4 : p0 + g4)) * 4;
+      const int de = xneg ? -32 : 32;
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        if ((hf == 0 || CW > 8) && g4 + 8 * hf < cnt) {
+          const uint32_t code = rs[g4 + 8 * hf].code;
+          const int e = e0 + hf * de;
+          if ((code & red_am0) == red_cv0) red_add(red_p0 + e, static_cast<double>(d[2 * hf]));
+          if ((code & red_am1) == red_cv1) red_add(red_p1 + e, static_cast<double>(d[2 * hf + 1]));
+        }
       }
-    }
-    // moments of the chunk: one (cell, moment) pair per lane and pass, dot product over the lanes.
-    // All passes' dot products first (their shared-memory loads can overlap; rows past the chunk are
-    // clamped to its last cell and their sums dropped), then the global reductions.
-    constexpr int NPASS = (CW * 4 + kLanes - 1) / kLanes;
-    T msum[NPASS];
-#pragma unroll
-    for (int pass = 0; pass < NPASS; ++pass) {
-      const int pr = pass * kLanes + lane;
-      const int l = min(pr >> 2, CW - 1), m = pr & 3;
-      msum[pass] = dot32<T, RS>(myr + l * RS, wts + m * RS);
-    }
-#pragma unroll
-    for (int pass = 0; pass < NPASS; ++pass) {
-      const int pr = pass * kLanes + lane;
-      const int l = pr >> 2, m = pr & 3;
-      if (pr < CW * 4 && l < cnt && !(rs[l].code & kSolid)) {
-        const int p = p0 + l;
-        const int i = xneg ? nx - 1 - p : p;
-        red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(msum[pass]));
+    } else {
+      {
+        // forward: incident flux sum |v_n| W h at cells owning a downstream wall face; adjoint: the
+        // transposed wall reads, sum 2 |v_a|/dx z at cells whose upstream neighbour is solid
+        const uint32_t mycode = lane < cnt ? rs[lane].code : 0u;
+        const bool fx = ADJ ? (((mycode >> kClsXShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncX) != 0;
+        const bool fy = ADJ ? (((mycode >> kClsYShift) & 3u) == (uint32_t)kWall && !(mycode & kSolid)) : (mycode & kIncY) != 0;
+        const unsigned incx = __ballot_sync(0xffffffffu, fx);
+        const unsigned incy = __ballot_sync(0xffffffffu, fy);
+        // one wall face per lane (at most 2 CW faces): the dot product over the velocities read back
+        // from the ring, like a moment
+        const int nfx = __popc(incx), nf = nfx + __popc(incy);
+        for (int e = lane; e < nf; e += kLanes) {
+          const bool is_x = e < nfx;
+          const int l = (int)__fns(is_x ? incx : incy, 0u, is_x ? e + 1 : e - nfx + 1);
+          const T f = dot32<T, RS>(myr + l * RS, wts + (is_x ? 4 : 5) * RS);
+          const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
+          red_add(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
+        }
+      }
+      // moments of the chunk: one (cell, moment) pair per lane and pass, dot product over the lanes.
+      // All passes' dot products first (their shared-memory loads can overlap; rows past the chunk are
+      // clamped to its last cell and their sums dropped), then the global reductions.
+      constexpr int NPASS = (CW * 4 + kLanes - 1) / kLanes;
+      T msum[NPASS];
+  #pragma unroll
+      for (int pass = 0; pass < NPASS; ++pass) {
+        const int pr = pass * kLanes + lane;
+        const int l = min(pr >> 2, CW - 1), m = pr & 3;
+        msum[pass] = dot32<T, RS>(myr + l * RS, wts + m * RS);
+      }
+  #pragma unroll
+      for (int pass = 0; pass < NPASS; ++pass) {
+        const int pr = pass * kLanes + lane;
+        const int l = pr >> 2, m = pr & 3;
+        if (pr < CW * 4 && l < cnt && !(rs[l].code & kSolid)) {
+          const int p = p0 + l;
+          const int i = xneg ? nx - 1 - p : p;
+          red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(msum[pass]));
+        }
       }
     }
   };
@@ -452,6 +584,10 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
   };
 
   int item = 0;
+  int s0 = lw % 3;  // ring slot of the current step t: the warp's steps are lw, lw + 1, ...
+  T *ring_w = ring + (size_t)w * 3 * CW * RS;
+  const T *ring_p1 = ring + (size_t)wprev * 3 * CW * RS;
+  const T *ring_p2 = ring + (size_t)(wb + (lw + 2 * R - 2) % R) * 3 * CW * RS;
   if (NSTAGE == 2) issue(lw, 0, 0);
   for (int q = lw; q < ny; q += R) {
     for (int c = 0; c < R; ++c, ++item) {
@@ -481,9 +617,12 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
       if (R > 1 && !wait_at_least(&prog[wprev], t)) return give_up();
       if (R > 2 && !wait_at_least(&prog[wnext2], t)) return give_up();
       const SweepRec<T> *rs = stage + ((size_t)w * NSTAGE + buf) * CW;
-      T *myr = ring + ((size_t)w * 3 + (t % 3)) * CW * RS;
-      const T *pr1 = ring + ((size_t)wprev * 3 + ((t + 2) % 3)) * CW * RS;
-      const T *pr2 = ring + ((size_t)(wb + (lw + 2 * R - 2) % R) * 3 + ((t + 1) % 3)) * CW * RS;
+      // ring slots t % 3 (this row), (t - 1) % 3 (row q-1) and (t - 2) % 3 (row q-2)
+      const int s1 = s0 == 0 ? 2 : s0 - 1, s2 = s0 == 2 ? 0 : s0 + 1;
+      T *myr = ring_w + s0 * (CW * RS);
+      const T *pr1 = ring_p1 + s1 * (CW * RS);
+      const T *pr2 = ring_p2 + s2 * (CW * RS);
+      s0 = s2;
       if (py && q < 2) {
         if (STAGE_SEAM) {
           T *sd = seamst + (((size_t)wt * 2 + (lw & 1)) * NSTAGE + buf) * 2 * CW * kLanes;
