@@ -165,6 +165,8 @@ struct InstanceDesc {
   double ginv[16];      // inverse Gram matrix of psi = (1, v1, v2, |v|^2) under the weights W
   double ain[4];        // per side: sum_{v.n<0} |v.n| W  (incident weight of a constant)
   double nrm[4];        // per side: sum_{v.n>0} (v.n) W  (outgoing normaliser)
+  double wnrm[4];       // per side: alpha / nrm, the diffuse wall value per unit incident flux
+  int ginv_sparse;      // 1: ginv couples only (1, |v|^2) (entries off that pattern are exactly 0)
   const void *vel;      // [ngroups][kNumVelFields][32] T
   const void *inv_den;  // [ngroups][kInvRows][32] T: 1 / (delta + cx kx + cy ky), uniform delta only; row 9 = 0
   void *rec;            // [4][ncell] SweepRec<T>

@@ -21,34 +21,39 @@ namespace {
 
 constexpr int kFinBlock = 256;
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
+// Block sums of N doubles per thread, valid in thread 0.  The values go to shared memory and one warp
+// adds them: this part's FP64 pipe is narrow (2 lanes per SM and cycle), so the block does about one
+// FP64 add per value instead of the five of a shuffle tree run by every warp.
+template <int N>
+__device__ __forceinline__ void block_sums(double (&v)[N], double (*sh)[kFinBlock]) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < N; ++k) sh[k][threadIdx.x] = v[k];
   __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (wid == 0) {
-    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+  if (threadIdx.x < 32) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    for (int k = 0; k < N; ++k) {
+      double r = sh[k][threadIdx.x];
+#pragma unroll
+      for (int i = 32; i < kFinBlock; i += 32) r += sh[k][threadIdx.x + i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      v[k] = r;
+    }
   }
-  return r;  // valid in thread 0
 }
 
 __global__ void __launch_bounds__(kFinBlock) fin1_kernel(LaunchDesc L) {
-  __shared__ double sh[32];
+  __shared__ double sh[1][kFinBlock];
   const int map = L.fin_map[blockIdx.x];
   const InstanceDesc *D = L.inst + (map >> 16);
   DeviceState *st = D->state;
   if (*reinterpret_cast<volatile int *>(&st->done)) return;
   const int cell = (map & 0xffff) * kFinBlock + threadIdx.x;
-  double v = 0.0;
-  if (cell < D->ncell && !(D->code4[(size_t)cell * 4] & kSolid)) v = D->acc[(size_t)cell * 4];
-  v = block_sum(v, sh);
+  double v[1] = {0.0};
+  if (cell < D->ncell && !(D->code4[(size_t)cell * 4] & kSolid)) v[0] = D->acc[(size_t)cell * 4];
+  block_sums<1>(v, sh);
   if (threadIdx.x == 0) {
-    atomicAdd(&st->mass_acc, v);
+    atomicAdd(&st->mass_acc, v[0]);
     __threadfence();
     const unsigned t = atomicAdd(&st->ticket1, 1u);
     if (t == (unsigned)D->fin_nblocks - 1u) {
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(kFinBlock) fin1_kernel(LaunchDesc L) {
 
 template <typename T>
 __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
-  __shared__ double sh[32];
+  __shared__ double sh[3][kFinBlock];
   const int map = L.fin_map[blockIdx.x];
   const InstanceDesc *D = L.inst + (map >> 16);
   DeviceState *st = D->state;
@@ -80,15 +85,14 @@ __global__ void __launch_bounds__(kFinBlock) fin2_kernel(LaunchDesc L) {
   double du = 0.0, ua = 0.0, uq = 0.0, bad = 0.0;
   if (cell < ncell) fin2_cell<T>(D, cell, s, c_new, fcur, fnext, rho_in, L.cols_v != 0, du, ua, uq, bad);
   if (rho_in) seam_inject<T>(D, (size_t)(map & 0xffff) * kFinBlock + threadIdx.x, (size_t)D->fin_nblocks * kFinBlock);
-  du = block_sum(du, sh);
-  ua = block_sum(ua, sh);
-  uq = block_sum(uq, sh);
-  bad = block_sum(bad, sh);
+  double sums[3] = {du, ua, uq};
+  const bool any_bad = __syncthreads_or(bad > 0.0) != 0;
+  block_sums<3>(sums, sh);
   if (threadIdx.x == 0) {
-    atomicAdd(&st->du_acc, du);
-    atomicAdd(&st->u_acc, ua);
-    atomicAdd(&st->q_acc, uq);
-    if (bad > 0.0) atomicExch(&st->nan_flag, 1);
+    atomicAdd(&st->du_acc, sums[0]);
+    atomicAdd(&st->u_acc, sums[1]);
+    atomicAdd(&st->q_acc, sums[2]);
+    if (any_bad) atomicExch(&st->nan_flag, 1);
     __threadfence();
     const unsigned t = atomicAdd(&st->ticket2, 1u);
     if (t == (unsigned)D->fin_nblocks - 1u) {

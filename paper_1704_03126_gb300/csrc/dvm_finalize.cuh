@@ -14,21 +14,22 @@ struct alignas(32) Dbl4 {
   double x, y, z, w;
 };
 
-// Write the sweep record of one cell and quadrant: right-hand-side coefficients, the upwind
-// coefficients of the cell's stencil classes and the wall terms 2 h_w of wall-class axes.
+// Write the sweep record of one cell and quadrant: right-hand-side coefficients (already in the record's
+// precision), the upwind coefficients of the cell's stencil classes and the wall terms 2 h_w of
+// wall-class axes.
 template <typename T>
-__device__ __forceinline__ void store_rec(SweepRec<T> *dst, double A, double B, double C, double Dd, double hwx,
-                                          double hwy, uint32_t code, double delta);
+__device__ __forceinline__ void store_rec(SweepRec<T> *dst, T A, T B, T C, T Dd, double hwx, double hwy,
+                                          uint32_t code, T delta);
 template <>
-__device__ __forceinline__ void store_rec<float>(SweepRec<float> *dst, double A, double B, double C, double Dd,
-                                                 double hwx, double hwy, uint32_t code, double delta) {
+__device__ __forceinline__ void store_rec<float>(SweepRec<float> *dst, float A, float B, float C, float Dd,
+                                                 double hwx, double hwy, uint32_t code, float delta) {
   const int clx = (code >> kClsXShift) & 3, cly = (code >> kClsYShift) & 3;
   const bool solid = (code & kSolid) != 0;
   SweepRec<float> r;
-  r.A = solid ? 0.f : (float)A;
-  r.B = solid ? 0.f : (float)B;
-  r.C = solid ? 0.f : (float)C;
-  r.D = solid ? 0.f : (float)Dd;
+  r.A = solid ? 0.f : A;
+  r.B = solid ? 0.f : B;
+  r.C = solid ? 0.f : C;
+  r.D = solid ? 0.f : Dd;
   r.ax1 = solid ? 0.f : class_a1(clx);
   r.ax2 = solid ? 0.f : class_a2(clx);
   r.xw = (!solid && clx == kWall) ? (float)(2.0 * hwx) : 0.f;
@@ -36,7 +37,7 @@ __device__ __forceinline__ void store_rec<float>(SweepRec<float> *dst, double A,
   r.ay2 = solid ? 0.f : class_a2(cly);
   r.yw = (!solid && cly == kWall) ? (float)(2.0 * hwy) : 0.f;
   r.code = code;
-  r.delta = (float)delta;
+  r.delta = delta;
   *dst = r;
 }
 template <>
@@ -69,15 +70,25 @@ __device__ __forceinline__ void write_records(const InstanceDesc *D, int cell, d
   const double d = D->uniform_delta ? D->delta : D->delta_field[cell];
   // collision coefficients a = G^{-1} m, m = (rho, u1, u2, rho + tau) = sum W psi h
   const double m[4] = {rho, u1, u2, rho + tau};
+  const double *gi = D->ginv;
   double a[4];
+  if (D->ginv_sparse) {
+    a[0] = gi[0] * m[0] + gi[3] * m[3];
+    a[1] = gi[5] * m[1];
+    a[2] = gi[10] * m[2];
+    a[3] = gi[12] * m[0] + gi[15] * m[3];
+  } else {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    a[i] = D->ginv[i * 4] * m[0] + D->ginv[i * 4 + 1] * m[1] + D->ginv[i * 4 + 2] * m[2] + D->ginv[i * 4 + 3] * m[3];
-  // R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v_flow in the basis 1, v1, v2, |v|^2 - 1
-  const double A = d * (a[0] + a[3] - c);
-  const double B = d * a[1] + (D->flow_axis ? 0.0 : D->force);
-  const double Cc = d * a[2] + (D->flow_axis ? D->force : 0.0);
-  const double Dd = d * a[3];
+    for (int i = 0; i < 4; ++i)
+      a[i] = gi[i * 4] * m[0] + gi[i * 4 + 1] * m[1] + gi[i * 4 + 2] * m[2] + gi[i * 4 + 3] * m[3];
+  }
+  // R = delta (a0 + a1 v1 + a2 v2 + a3 |v|^2 - c) + F v_flow in the basis 1, v1, v2, |v|^2 - 1; the
+  // coefficients are shared by the four quadrants and rounded to the record's precision once
+  const T A = static_cast<T>(d * (a[0] + a[3] - c));
+  const T B = static_cast<T>(d * a[1] + (D->flow_axis ? 0.0 : D->force));
+  const T Cc = static_cast<T>(d * a[2] + (D->flow_axis ? D->force : 0.0));
+  const T Dd = static_cast<T>(d * a[3]);
+  const T dt = static_cast<T>(d);
   SweepRec<T> *rec = static_cast<SweepRec<T> *>(D->rec);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -89,18 +100,18 @@ __device__ __forceinline__ void write_records(const InstanceDesc *D, int cell, d
         const int side = src & 3;
         // diffuse part alpha rho_w; the specular part (1 - alpha) h(mirror v) is added in the sweep
         const double corr = rho_in ? rho_in[(size_t)4 * ncell + src] : 0.0;
-        hw[ax] = D->alpha * (__ldcg(fcur + src) - s * D->ain[side] + corr) / D->nrm[side];
+        hw[ax] = (__ldcg(fcur + src) - s * D->ain[side] + corr) * D->wnrm[side];
       } else {
         hw[ax] = 0.0;
       }
     }
-    store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+    store_rec<T>(rec + (size_t)q * ncell + cell, A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], dt);
     // the diagonal-major copy only feeds the column sweep (rebuilt by sync_diag when a launch
     // switches to it)
     if (diag && D->rec_diag)
       store_rec<T>(static_cast<SweepRec<T> *>(D->rec_diag) + q * diag_quadrant_size(D->nx, D->ny) +
                        diag_slot(D->nx, D->ny, cell % D->nx, cell / D->nx, (q & 1) != 0, (q & 2) != 0),
-                   A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], d);
+                   A, B, Cc, Dd, hw[0], hw[1], D->code4[(size_t)cell * 4 + q], dt);
   }
 }
 
