@@ -179,16 +179,20 @@ void build_velocity_tables(const dvm_ctx *c, std::vector<T> &vel, std::vector<T>
 template <typename T>
 bool table_sums(const dvm_ctx *c, const std::vector<T> &vel, InstanceDesc &D) {
   double g[4][8] = {};
+  // The moment sums are accumulated per quadrant and the quadrants added last: the four quadrants
+  // list mirrored velocities in the same lane order, so sums odd in v1 or v2 cancel exactly.
+  double gq[4][4][4] = {}, sq[4][4] = {};
   for (int k = 0; k < 4; ++k) D.sumW[k] = D.ain[k] = D.nrm[k] = 0.0;
   for (int grp = 0; grp < c->ngroups; ++grp) {
+    const int quad = grp / c->gq;
     for (int lane = 0; lane < kLanes; ++lane) {
       auto f = [&](int field) { return (double)vel[((size_t)grp * kNumVelFields + field) * kLanes + lane]; };
       const double w[4] = {f(kW0), f(kW1), f(kW2), f(kW3)};
       if (w[0] == 0.0) continue;  // padded lane
       const double psi[4] = {1.0, f(kV1), f(kV2), f(kE2m1) + 1.0};
       for (int i = 0; i < 4; ++i) {
-        D.sumW[i] += w[i];
-        for (int j = 0; j < 4; ++j) g[i][j] += w[i] * psi[j];
+        sq[quad][i] += w[i];
+        for (int j = 0; j < 4; ++j) gq[quad][i][j] += w[i] * psi[j];
       }
       const double v1 = f(kV1), v2 = f(kV2), wnx = f(kWnx), wny = f(kWny);
       // side W: inward normal +x, outgoing v1 > 0; E: -x; S: +y; N: -y
@@ -198,7 +202,11 @@ bool table_sums(const dvm_ctx *c, const std::vector<T> &vel, InstanceDesc &D) {
       (v2 < 0 ? D.nrm[kN] : D.ain[kN]) += wny;
     }
   }
-  // Gauss-Jordan inverse with partial pivoting
+  for (int i = 0; i < 4; ++i) {
+    D.sumW[i] = (sq[0][i] + sq[1][i]) + (sq[2][i] + sq[3][i]);
+    for (int j = 0; j < 4; ++j) g[i][j] = (gq[0][i][j] + gq[1][i][j]) + (gq[2][i][j] + gq[3][i][j]);
+  }
+  // Gauss-Jordan inverse with partial pivoting (exact zeros of G stay exact zeros of the inverse)
   for (int i = 0; i < 4; ++i) g[i][4 + i] = 1.0;
   for (int col = 0; col < 4; ++col) {
     int piv = col;
