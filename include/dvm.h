@@ -90,7 +90,8 @@ typedef struct {
   double accommodation;       /* alpha in [0, 1] of Eq. (diffuse2): the wall value of a reflected velocity
                                  is alpha rho_w + (1 - alpha) h(mirror v) at the face's gas cell (from the
                                  previous iterate).  1 = fully diffuse (the paper's case).  alpha < 1 runs
-                                 on the column sweep only and has no adjoint (DVM_EINVAL there). */
+                                 on the column sweep only; its adjoint reflects the transposed wall reads
+                                 specularly with weight 1 - alpha. */
   int precision;              /* dvm_precision */
   double force;               /* body-force source coefficient F along x1 (1 for the paper's Poiseuille flow) */
   int store_distribution;     /* 1 = also keep h in device memory (needed by dvm_distribution) */
@@ -113,7 +114,8 @@ typedef struct {
                                  the derivative at the cell centre of the polynomial through the same
                                  points (exact on linear fields, like the equal-row forms).  Needs the
                                  transposed storage (DVM_STORAGE_AS_GIVEN gives DVM_EINVAL) and runs on
-                                 the column sweep only; no adjoint.  The adjoint needs square cells. */
+                                 the column sweep only.  Its adjoint (the transposed stretched stencil)
+                                 needs a non-periodic x2 axis (DVM_EINVAL otherwise). */
   int anderson_depth;         /* 0 = plain source iteration (Eq. iteration, the paper's).  1..8: Anderson
                                  mixing of that depth (Walker & Ni 2011, type II) of the projected state
                                  the sweeps start from -- moments, wall-face fluxes, periodic seam values,
@@ -223,8 +225,10 @@ dvm_status dvm_get_info(const dvm_ctx *ctx, dvm_info *info);
  *   dQ_ddelta   host double [ny][nx] (output; 0 in solid cells).
  *   q_identity  host, may be NULL: F sum z v1, equal to Q at convergence (a consistency check).
  *   iters       host, may be NULL: adjoint sweeps run.
- * Needs store_distribution = 1 and at least one forward sweep (DVM_ESTATE otherwise).  Allocates the
- * adjoint state (about as much as the forward state plus one more distribution) on first use. */
+ * Needs store_distribution = 1 and at least one forward sweep (DVM_ESTATE otherwise).  Every wall
+ * accommodation, moving plate, cell shape and row-height set is covered, except unequal rows with a
+ * periodic x2 axis (DVM_EINVAL).  Allocates the adjoint state (about as much as the forward state plus
+ * one more distribution) on first use. */
 dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta, double *q_identity, int *iters);
 
 /* Choose the sweep kernel of the context's own solves and adjoint (dvm_sweep_kind) and its shape

@@ -116,19 +116,23 @@ __global__ void __launch_bounds__(kBlock) afin1_kernel(const InstanceDesc *D) {
       for (int j = 0; j < 4; ++j) y += D->ginv[j * 4 + i] * Z[j];
       al[i] = d * y;
     }
-    (D->flow_axis ? al[2] : al[1]) += D->dA_over_Lx;  // g = W v_flow dA / L
+    // g = W v_flow dA / L (dA: the column's width for columns of unequal width)
+    (D->flow_axis ? al[2] : al[1]) += D->dA_over_Lx * (D->xwidth ? D->xwidth[cell % D->nx] : 1.0);
     const double zf = D->flow_axis ? Z[2] : Z[1];
     reinterpret_cast<Dbl4 *>(D->mom)[cell] = Dbl4{al[0], al[1], al[2], al[3]};
     dz = d * Z[0];
 #pragma unroll
     for (int i = 0; i < 4; ++i) lam += al[i] * D->sumW[i];
-    // transposed diffuse walls: lambda(j, owner) += t_f |v_j . n| W_j / N over incident j
+    // transposed walls: lambda(j, owner) += alpha t_f |v_j . n| W_j / N over incident j (diffuse part)
+    // and (1 - alpha) 2 |v_a|/dx z of the mirrored velocity (specular part, added in the next
+    // transposed sweep): their sum over j is t_f (alpha ain / N + 1 - alpha)
     const uint32_t c0 = D->code4[(size_t)cell * 4 + 0], c1 = D->code4[(size_t)cell * 4 + 1],
                    c2 = D->code4[(size_t)cell * 4 + 2];
-    if (c0 & kIncX) lam += fcur[(size_t)cell * 4 + kE] * D->ain[kE] / D->nrm[kE];
-    if (c1 & kIncX) lam += fcur[(size_t)cell * 4 + kW] * D->ain[kW] / D->nrm[kW];
-    if (c0 & kIncY) lam += fcur[(size_t)cell * 4 + kN] * D->ain[kN] / D->nrm[kN];
-    if (c2 & kIncY) lam += fcur[(size_t)cell * 4 + kS] * D->ain[kS] / D->nrm[kS];
+    const double spec = 1.0 - D->alpha;
+    if (c0 & kIncX) lam += fcur[(size_t)cell * 4 + kE] * (D->ain[kE] * D->wnrm[kE] + spec);
+    if (c1 & kIncX) lam += fcur[(size_t)cell * 4 + kW] * (D->ain[kW] * D->wnrm[kW] + spec);
+    if (c0 & kIncY) lam += fcur[(size_t)cell * 4 + kN] * (D->ain[kN] * D->wnrm[kN] + spec);
+    if (c2 & kIncY) lam += fcur[(size_t)cell * 4 + kS] * (D->ain[kS] * D->wnrm[kS] + spec);
     du = fabs(zf - D->u1prev[cell]);
     ua = fabs(zf);
     D->u1prev[cell] = zf;
@@ -232,7 +236,7 @@ __device__ __forceinline__ void store_adj_rec<double>(SweepRec<double> *dst, con
 }
 
 // Right-hand sides of the next transposed sweep: W (alpha . psi + kappa) plus the incident-wall terms
-// TX = t_f / N at cells owning a face that the quadrant's velocities hit.
+// TX = alpha t_f / N at cells owning a face that the quadrant's velocities hit (alpha: accommodation).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) afin2_kernel(const InstanceDesc *D) {
   DeviceState *st = D->state;
@@ -254,8 +258,8 @@ __global__ void __launch_bounds__(kBlock) afin2_kernel(const InstanceDesc *D) {
   for (int q = 0; q < 4; ++q) {
     const uint32_t code = D->code4[(size_t)cell * 4 + q];
     const int sx = (q & 1) ? kW : kE, sy = (q & 2) ? kS : kN;  // wall sides these velocities hit
-    const double tx = (code & kIncX) ? fcur[(size_t)cell * 4 + sx] / D->nrm[sx] : 0.0;
-    const double ty = (code & kIncY) ? fcur[(size_t)cell * 4 + sy] / D->nrm[sy] : 0.0;
+    const double tx = (code & kIncX) ? fcur[(size_t)cell * 4 + sx] * D->wnrm[sx] : 0.0;
+    const double ty = (code & kIncY) ? fcur[(size_t)cell * 4 + sy] * D->wnrm[sy] : 0.0;
     store_adj_rec<T>(rec + (size_t)q * ncell + cell, al, kappa, tx, ty, code, d);
     // the transposed sweep visits cells in the opposite order of the quadrant
     if (D->rec_diag)

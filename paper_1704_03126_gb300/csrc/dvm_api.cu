@@ -30,7 +30,6 @@ struct dvm_ctx {
   bool tr = false;
   int unx = 0, uny = 0;
   double dxs = 0.0, dys = 0.0;     // stored x reference spacing and stored y spacing
-  bool square = true;              // square cells (the adjoint's case)
   bool nux = false;                // stored x spacing varies by column (the caller's unequal rows)
   double *d_xwidth = nullptr;      // nux: stored column widths / dxs
   // Anderson mixing (dvm_params.anderson_depth > 0): the device descriptor and its buffers
@@ -73,6 +72,7 @@ struct dvm_ctx {
   // adjoint (allocated by the first dvm_adjoint)
   void *a_rec = nullptr, *a_rec_diag = nullptr, *a_seamx = nullptr, *a_seamy = nullptr, *a_z = nullptr;
   double *a_acc = nullptr, *a_flux = nullptr, *a_alpha = nullptr, *a_z1prev = nullptr, *a_grad = nullptr;
+  void *a_wbuf = nullptr;          // accommodation < 1: z at the wall faces, two parities (adjoint)
   DeviceState *a_state = nullptr;
   InstanceDesc *a_desc = nullptr;
   cudaGraphExec_t a_graph = nullptr;
@@ -344,6 +344,7 @@ void release_device(dvm_ctx *c) {
   free_dev(c->a_flux);
   free_dev(c->a_alpha);
   free_dev(c->a_z1prev);
+  free_dev(c->a_wbuf);
   free_dev(c->a_grad);
   free_dev(c->a_state);
   free_dev(c->a_desc);
@@ -1113,7 +1114,6 @@ dvm_status dvm_create(const uint8_t *mask, const dvm_params *params, void *strea
     c->dxs = c->tr ? udy : udx;
     c->dys = c->tr ? udx : udy;
     c->nux = P.row_heights != nullptr;
-    c->square = !c->nux && udx == udy;
   }
   c->fp64 = P.precision == DVM_FP64;
   c->store_h = P.store_distribution != 0;
@@ -1569,8 +1569,11 @@ dvm_status adjoint_setup(dvm_ctx *c) {
     DVM_CUDA(c, cudaMalloc(&c->a_state, sizeof(DeviceState)));
     DVM_CUDA(c, cudaMalloc(&c->a_desc, sizeof(InstanceDesc)));
   }
+  const size_t wbytes = ts * 2 * (size_t)std::max(c->nwall, 1) * 2 * c->gq * kLanes;
+  if (c->alpha < 1.0 && !c->a_wbuf) DVM_CUDA(c, cudaMalloc(&c->a_wbuf, wbytes));
   // the adjoint view: the forward instance with the adjoint buffers in place of the forward ones
   InstanceDesc A = c->hdesc;
+  A.wbuf = c->a_wbuf;
   A.uniform_delta = c->uniform ? 1 : 0;
   A.delta_field = c->d_delta_field;
   A.rec = c->a_rec;
@@ -1596,6 +1599,7 @@ dvm_status adjoint_setup(dvm_ctx *c) {
   DVM_CUDA(c, cudaMemsetAsync(c->a_seamx, 0, ts * c->ngroups * c->ny * 2 * kLanes, c->stream));
   DVM_CUDA(c, cudaMemsetAsync(c->a_seamy, 0, ts * c->ngroups * c->nx * 2 * kLanes, c->stream));
   DVM_CUDA(c, cudaMemsetAsync(c->a_z, 0, ts * c->ngroups * ncell * kLanes, c->stream));
+  if (c->a_wbuf) DVM_CUDA(c, cudaMemsetAsync(c->a_wbuf, 0, wbytes, c->stream));
   DVM_CUDA(c, launch_adjoint_reset(c->a_desc, c->ncell, c->fp64, c->stream));
   if (!c->a_graph) {
     Schedule sc;
@@ -1612,7 +1616,8 @@ dvm_status adjoint_setup(dvm_ctx *c) {
     DVM_CUDA(c, cudaStreamSynchronize(c->stream));
     const int cw = (!cols && sc.v > 0) ? sc.v : c->cw;
     const int warps = cols ? (c->nx + kLanes / sc.v - 1) / (kLanes / sc.v) : (c->nx + cw - 1) / cw;
-    LaunchDesc L = make_launch(c->a_desc, c->d_adj_map, c->d_fin_map, 1, warps, cw, cols ? sc.v : 0);
+    LaunchDesc L = make_launch(c->a_desc, c->d_adj_map, c->d_fin_map, 1, warps, cw, cols ? sc.v : 0,
+                               cols && needs_special(c));
     const int sweep_blocks = (int)amap.size();
     const int fin_blocks = c->hdesc.fin_nblocks;
     const int lines = (c->hdesc.periodic_x ? c->ngroups * c->ny : 0) + (c->hdesc.periodic_y ? c->ngroups * c->nx : 0);
@@ -1623,7 +1628,8 @@ dvm_status adjoint_setup(dvm_ctx *c) {
     DVM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < c->a_graph_iters && e == cudaSuccess; ++it) {
-      e = launch_sweep_adjoint(c->fp64, c->uniform, L, sweep_blocks, c->cap_stream);
+      // columns of unequal width take the per-cell denominators (the uniform table assumes equal columns)
+      e = launch_sweep_adjoint(c->fp64, c->uniform && !c->nux, L, sweep_blocks, c->cap_stream);
       if (e == cudaSuccess) e = launch_adjoint_finalize(L, fin_blocks, seam_blocks, c->fp64, c->cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
@@ -1646,8 +1652,8 @@ dvm_status dvm_adjoint(dvm_ctx *ctx, double tol, int max_iter, double *dQ_ddelta
   if (!(tol > 0.0) || max_iter < 1) return fail(c, DVM_EINVAL, "tol must be > 0 and max_iter >= 1");
   if (!c->d_h) return fail(c, DVM_ESTATE, "dvm_adjoint needs the forward distribution (store_distribution = 1)");
   // a moving plate only adds a constant source: the transposed operator is the one of a plate at rest
-  if (c->alpha < 1.0) return fail(c, DVM_EINVAL, "dvm_adjoint supports fully diffuse walls only (accommodation = 1)");
-  if (!c->square) return fail(c, DVM_EINVAL, "dvm_adjoint supports square cells only (no dx1, no row heights)");
+  if (c->nux && c->hdesc.periodic_x)
+    return fail(c, DVM_EINVAL, "dvm_adjoint: rows of unequal height need a non-periodic x2 axis");
   DVM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(DeviceState), cudaMemcpyDeviceToHost, c->stream));
   DVM_CUDA(c, cudaStreamSynchronize(c->stream));
   if (c->h_state->iter < 1) return fail(c, DVM_ESTATE, "dvm_adjoint needs a forward solve first");

@@ -22,8 +22,9 @@
 //   - the warp of row q+2 to have read the ring slot this step overwrites.
 // Per-cell records (right-hand-side coefficients, wall values, stencil classes) are staged into
 // shared memory with cp.async one chunk ahead (FP32) or at the start of the chunk (FP64).  The
-// moments of each finished chunk are dot products over the 32 lanes read back from the ring (FP32
-// or FP64 sums) and are accumulated across groups with FP64 atomics; incident wall fluxes likewise.
+// moments and incident wall fluxes of each finished chunk are sums over the 32 lanes read back from
+// the ring -- an m16n8k8 TF32 tensor-core contraction in FP32, per-lane dot products in FP64 -- and
+// are accumulated across groups with FP64 atomics.
 // h itself goes to HBM only at the periodic seams (and when the distribution is kept).
 #pragma once
 #include <climits>
@@ -79,26 +80,14 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Dot product over the 32 velocities of a group: h values of one cell (a ring row) with one weight row,
-// both in shared memory.  FP32: float4 loads and packed FP32x2 FMAs in two interleaved partial sums.
+// Dot product over the 32 velocities of a group (FP64 sweep): h values of one cell (a ring row) with one
+// weight row, both in shared memory.
 template <typename T, int RS>
 __device__ __forceinline__ T dot32(const T *hr, const T *wr) {
-  if constexpr (RS % 4 == 0 && sizeof(T) == 4) {
-    float2 s2a = make_float2(0.f, 0.f), s2b = make_float2(0.f, 0.f);
+  T sum = T(0);
 #pragma unroll
-    for (int k = 0; k < kLanes; k += 4) {
-      const float4 a = *reinterpret_cast<const float4 *>(hr + k);
-      const float4 b = *reinterpret_cast<const float4 *>(wr + k);
-      s2a = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), s2a);
-      s2b = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), s2b);
-    }
-    return (s2a.x + s2b.x) + (s2a.y + s2b.y);
-  } else {
-    T sum = T(0);
-#pragma unroll
-    for (int k = 0; k < kLanes; ++k) sum = fma(wr[k], hr[k], sum);
-    return sum;
-  }
+  for (int k = 0; k < kLanes; ++k) sum = fma(wr[k], hr[k], sum);
+  return sum;
 }
 
 // FP32 per-cell sums on the tensor cores.  The h values of a finished chunk sit in the ring as a
@@ -144,7 +133,7 @@ __device__ __forceinline__ void weight_fragments(const float *wts, int lane, uin
 }
 // d = the tile times the weights.  `base`: this lane's ldmatrix row address for k-step 0 (lanes
 // 8 m .. 8 m + 7 address the rows of matrix m: cells 0-7 / 8-15 of the chunk (rows past the chunk
-// repeat its last cell) at velocities 0-3 / 4-3 + 4 of the k-step).  Lane (g = lane / 4, t = lane % 4)
+// repeat its last cell) at velocities 0-3 / 4-7 of the k-step).  Lane (g = lane / 4, t = lane % 4)
 // gets columns 2t, 2t+1 of cells g (d0, d1) and g + 8 (d2, d3).
 __device__ __forceinline__ void cell_sums_mma(uint32_t base, const uint32_t (&bf)[4][4], float (&d)[4]) {
   d[0] = d[1] = d[2] = d[3] = 0.f;
@@ -554,25 +543,18 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
           red_add(&facc[(j * nx + i) * 4 + (is_x ? sidex : sidey)], static_cast<double>(f));
         }
       }
-      // moments of the chunk: one (cell, moment) pair per lane and pass, dot product over the lanes.
-      // All passes' dot products first (their shared-memory loads can overlap; rows past the chunk are
-      // clamped to its last cell and their sums dropped), then the global reductions.
-      constexpr int NPASS = (CW * 4 + kLanes - 1) / kLanes;
-      T msum[NPASS];
+      // moments of the chunk (FP64, bound by the FP64 pipe): one (cell, moment) pair per lane and pass,
+      // dot product over the lanes, skipped for solid cells and rows past the chunk (a pass whose pairs
+      // are all skipped costs the warp nothing)
   #pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        const int pr = pass * kLanes + lane;
-        const int l = min(pr >> 2, CW - 1), m = pr & 3;
-        msum[pass] = dot32<T, RS>(myr + l * RS, wts + m * RS);
-      }
-  #pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
+      for (int pass = 0; pass < (CW * 4 + kLanes - 1) / kLanes; ++pass) {
         const int pr = pass * kLanes + lane;
         const int l = pr >> 2, m = pr & 3;
         if (pr < CW * 4 && l < cnt && !(rs[l].code & kSolid)) {
+          const T sum = dot32<T, RS>(myr + l * RS, wts + m * RS);
           const int p = p0 + l;
           const int i = xneg ? nx - 1 - p : p;
-          red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(msum[pass]));
+          red_add(&acc[(j * nx + i) * 4 + m], static_cast<double>(sum));
         }
       }
     }

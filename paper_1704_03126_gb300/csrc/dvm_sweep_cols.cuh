@@ -197,34 +197,52 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
   double *facc = D->facc + (size_t)((st->iter + 1) & 1) * ncell * 4;
   const int sidex = xneg ? kW : kE;
   const int sidey = yneg ? kS : kN;
-  // accommodation < 1 (forward only): the wall value of a wall-class cell gains (1 - alpha) times the
-  // previous sweep's value of the mirrored velocity at the same face, written by the mirrored
-  // quadrant's block at its incident cells; double-buffered by sweep parity
-  const bool spec = SPEC && !ADJ && D->alpha < 1.0;
+  // accommodation < 1: the wall value of a wall-class cell gains (1 - alpha) times the previous
+  // sweep's value of the mirrored velocity at the same face, written by the mirrored quadrant's block
+  // at its incident cells; double-buffered by sweep parity.  The transposed sweep swaps the roles:
+  // wall-class cells write z, and a cell owning the (forward) downstream face adds (1 - alpha) 2 |v_a|/dx
+  // times the mirrored velocity's z of the last transposed sweep to its right-hand side.
+  const bool spec = SPEC && D->alpha < 1.0;
   // a moving plate beyond the last row (Couette flow, Eq. diffuse1): its wall value alpha (rho_w +
   // 2 U v1) adds 4 alpha U v1 to the y combination of the cells under it (forward only)
   const T top_term = static_cast<T>(4.0 * D->alpha * D->top_u);
   const T one_m_alpha2 = static_cast<T>(2.0 * (1.0 - D->alpha));
-  // Columns of unequal width (the caller's rows of Sec. II.A stored transposed; forward only).  The x
-  // stencil of this thread's column i is the derivative at its centre of the polynomial through the
-  // points the class uses, widths w relative to dx: upstream centre distances d1 = (w_i + w_u1)/2 and
-  // d2 = d1 + (w_u1 + w_u2)/2; interior kappa = 1/d1 + 1/d2 with weights d2/(d1 (d2 - d1)) on h(u1)
-  // and -d1/(d2 (d2 - d1)) on h(u2); first order kappa = weight = 1/d1; next to a wall (face at w_i/2)
-  // kappa = 2/w_i, the wall terms (2 alpha rho_w, the specular part, the plate's drift) times 1/w_i.
-  const bool nux = SPEC && !ADJ && D->xwidth != nullptr;
+  // Columns of unequal width (the caller's rows of Sec. II.A stored transposed).  The x stencil of a
+  // column k is the derivative at its centre of the polynomial through the points the class uses,
+  // widths w relative to dx: upstream centre distances d1 = (w_k + w_u1)/2 and d2 = d1 + (w_u1 + w_u2)/2;
+  // interior kappa = 1/d1 + 1/d2 with weights d2/(d1 (d2 - d1)) on h(u1) and -d1/(d2 (d2 - d1)) on
+  // h(u2); first order kappa = weight = 1/d1; next to a wall (face at w_k/2) kappa = 2/w_k, the wall
+  // terms (2 alpha rho_w, the specular part, the plate's drift) times 1/w_k.  The transposed sweep has
+  // the same diagonal; its cell c pulls z of the forward-downstream columns d1, d2 with the forward
+  // weights of d1 (on its u1 = c) and of d2 (on its u2 = c).
+  const bool nux = SPEC && D->xwidth != nullptr;
   T nk_full = T(1.5), na1_full = T(2), na2_full = T(-0.5), nk_near = T(1), nwsc = T(1);
+  T ta1_full = T(2), ta1_near = T(1), ta2_full = T(-0.5);
   if (nux && p < nx) {
-    const int i = xneg ? nx - 1 - p : p, sgn = xneg ? -1 : 1;
-    // an upstream column beyond a closed x end belongs to a wall-class cell, whose stencil does not
-    // use it: read column i instead
-    auto col = [&](int c) { return (c >= 0 && c < nx) ? c : (px ? ((c % nx) + nx) % nx : i); };
-    const double w0 = D->xwidth[i], w1 = D->xwidth[col(i - sgn)], w2 = D->xwidth[col(i - 2 * sgn)];
-    const double d1 = 0.5 * (w0 + w1), d2 = d1 + 0.5 * (w1 + w2);
-    nk_full = static_cast<T>(1.0 / d1 + 1.0 / d2);
-    na1_full = static_cast<T>(d2 / (d1 * (d2 - d1)));
-    na2_full = static_cast<T>(-d1 / (d2 * (d2 - d1)));
-    nk_near = static_cast<T>(1.0 / d1);
-    nwsc = static_cast<T>(1.0 / w0);
+    const int i = xneg ? nx - 1 - p : p;
+    const int sf = (xneg != ADJ) ? -1 : 1;  // forward direction: the forward upstream of column k is k - sf
+    // a column beyond a closed x end belongs to a cell whose stencil does not use it: read `k` instead
+    auto col = [&](int c, int k) { return (c >= 0 && c < nx) ? c : (px ? ((c % nx) + nx) % nx : k); };
+    struct Stencil {
+      double k_full, a1, a2, k_near, wsc;
+    };
+    auto stencil = [&](int k) {
+      const double w0 = D->xwidth[k], w1 = D->xwidth[col(k - sf, k)], w2 = D->xwidth[col(k - 2 * sf, k)];
+      const double d1 = 0.5 * (w0 + w1), d2 = d1 + 0.5 * (w1 + w2);
+      return Stencil{1.0 / d1 + 1.0 / d2, d2 / (d1 * (d2 - d1)), -d1 / (d2 * (d2 - d1)), 1.0 / d1, 1.0 / w0};
+    };
+    const Stencil s0 = stencil(i);
+    nk_full = static_cast<T>(s0.k_full);
+    na1_full = static_cast<T>(s0.a1);
+    na2_full = static_cast<T>(s0.a2);
+    nk_near = static_cast<T>(s0.k_near);
+    nwsc = static_cast<T>(s0.wsc);
+    if (ADJ) {
+      const Stencil s1 = stencil(col(i + sf, i)), s2 = stencil(col(i + 2 * sf, i));
+      ta1_full = static_cast<T>(s1.a1);
+      ta1_near = static_cast<T>(s1.k_near);
+      ta2_full = static_cast<T>(s2.a2);
+    }
   }
   const int gi = g % D->groups_per_quadrant, gq = D->groups_per_quadrant;
   T *wbuf_wr = nullptr;
@@ -366,7 +384,12 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           yw = r.yw;
         }
         T xsc = T(1);  // scale of the x wall terms (unequal columns)
-        if (nux && !(code & kSolid)) {
+        if (ADJ && nux && !(code & kSolid)) {
+          const uint32_t t1c = (code >> kAdjT1XShift) & 3u;
+          ax1 = t1c == 2u ? ta1_full : (t1c == 1u ? ta1_near : T(0));
+          ax2 = (code & kAdjT2X) ? ta2_full : T(0);
+          xsc = nwsc;
+        } else if (nux && !(code & kSolid)) {
           const int clx = (code >> kClsXShift) & 3;
           if (clx == kFull) {
             ax1 = na1_full;
@@ -428,14 +451,18 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           }
         }
         if (spec && !(code & kSolid)) {
-          if (((code >> kClsXShift) & 3u) == (uint32_t)kWall) {
+          // forward: wall-class cells read the mirrored velocity's incident value; transposed: cells
+          // owning the forward downstream face read the mirrored velocity's z at that face
+          const bool rdx = ADJ ? (code & kIncX) != 0 : ((code >> kClsXShift) & 3u) == (uint32_t)kWall;
+          const bool rdy = ADJ ? (code & kIncY) != 0 : ((code >> kClsYShift) & 3u) == (uint32_t)kWall;
+          if (rdx) {
             const int slot = D->wall_slot[(size_t)cell * 4 + (xneg ? kE : kW)];
             if (slot >= 0) {  // always: every wall-class face has a slot
               load_vec(wbuf_rd + wface(slot, (quad >> 1) & 1), u1, sshift);
               ax1 = one_m_alpha2 * xsc;  // x combination 2 alpha rho_w + 2 (1 - alpha) h(mirror v)
             }
           }
-          if (((code >> kClsYShift) & 3u) == (uint32_t)kWall) {
+          if (rdy) {
             const int slot = D->wall_slot[(size_t)cell * 4 + (yneg ? kN : kS)];
             if (slot >= 0) {
               // h(p, q-1) lies in a solid cell here, so its register is free; the next cell reads it
@@ -457,7 +484,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
         const T2 sA = Q::splat(r.A), sB = Q::splat(r.B), sC = Q::splat(r.C), sD = Q::splat(r.D);
         const T2 sax1 = Q::splat(ax1), sax2 = Q::splat(ax2), say1 = Q::splat(ay1), say2 = Q::splat(ay2);
         const T2 sxw = Q::splat(xw), syw = Q::splat(yw);
-        const T2 stx = Q::splat(ADJ ? T(r.xw) * dx : T(0)), sty = Q::splat(ADJ ? T(r.yw) * dx : T(0));
+        const T2 stx = Q::splat(ADJ ? T(r.xw) * dx : T(0)), sty = Q::splat(ADJ ? T(r.yw) * dy : T(0));
         const int irow = (code >> kInvShift) & 15;
         T2 skx = zero2, sky = zero2, sdl = zero2;
         if (!UNIF) {
@@ -550,7 +577,7 @@ __global__ void __launch_bounds__(kColsMaxThreads, 1) cols_kernel(LaunchDesc L) 
           fy += __shfl_xor_sync(0xffffffffu, fy, off);
         }
         // (|v_a|/d_a) W h summed, times d_a: the incident flux sum |v_a| W h
-        const T scx = ADJ ? T(2) : dx, scy = ADJ ? T(2) : dy;
+        const T scx = ADJ ? T(2) * nwsc : dx, scy = ADJ ? T(2) : dy;
         if (v == 0 && fxf) red_add(&facc[(size_t)cell * 4 + sidex], static_cast<double>(fx * scx));
         if (v == 0 && fyf) red_add(&facc[(size_t)cell * 4 + sidey], static_cast<double>(fy * scy));
         if (spec && fxf) {
@@ -610,12 +637,11 @@ cudaError_t launch_vs(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   }
 }
 
-// SPEC: some instance of the launch has partially specular walls or a moving plate (forward sweeps only)
+// SPEC: some instance of the launch has partially specular walls, a moving plate or columns of unequal
+// width
 template <typename T, bool ADJ, bool UNIF>
 cudaError_t launch_v(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
-  if constexpr (!ADJ) {
-    if (L.specular) return launch_vs<T, ADJ, UNIF, true>(L, nblocks, stream);
-  }
+  if (L.specular) return launch_vs<T, ADJ, UNIF, true>(L, nblocks, stream);
   return launch_vs<T, ADJ, UNIF, false>(L, nblocks, stream);
 }
 

@@ -229,3 +229,145 @@ def test_couette_adjoint_matches_oracle(storage):
     scale = np.abs(g_ref).max()
     assert np.abs(grad - g_ref).max() < 1e-8 * scale
     assert abs(q_id) < 1e-14
+
+
+# ------------------------------------------------------------------ partially specular walls, unequal rows
+
+def _stretched_rows(ny, seed):
+    rng = inputs.SplitMix64(seed)
+    h = np.array([0.4 + 1.2 * rng.uniform() for _ in range(ny)])
+    return h / h.sum()
+
+
+def _notch(nx, ny):
+    m = np.zeros((ny, nx), np.uint8)
+    m[0:2, nx // 3] = 1
+    m[ny - 1, nx // 2: nx // 2 + 2] = 1
+    return m
+
+
+SPEC_ADJ_CASES = [
+    # name, mask, periodic_x, periodic_y, delta, quad, alpha
+    ("plates_gh8_a0.6", inputs.plates_mask(4, 16), True, False, 0.7, ("gh", 8, 0.0), 0.6),
+    ("rough24_nc8_a0.5", inputs.rough_channel_mask(24), True, False, 1.5, ("nc", 8, 4.0), 0.5),
+    ("block_periodic_cubic10_a0.8", _block(20, 16), True, True, 1.0, ("cubic", 10, 4.0), 0.8),
+    ("closed_box_nc8_a0.3", _block(12, 12), False, False, 1.0, ("nc", 8, 4.0), 0.3),
+]
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_spec_gradient(name):
+    _, mask, px, py, delta, quad, alpha = next(c for c in SPEC_ADJ_CASES if c[0] == name)
+    p = oracle.Problem.make(mask, px, py, _delta_field(mask, delta, 4), quad, alpha=alpha)
+    ref = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_ref, _, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=400000)
+    return g_ref, ok
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_unequal_gradient(name):
+    _, mask, px, delta, quad, alpha, top_u = next(c for c in UNEQUAL_ADJ_CASES if c[0] == name)
+    p = oracle.Problem.make(mask, px, False, _delta_field(mask, delta, 6), quad, alpha=alpha,
+                            force=0.0 if top_u else 1.0, top_u=top_u, dy=_stretched_rows(mask.shape[0], 23), dx1=0.07)
+    ref = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_ref, _, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=400000)
+    return g_ref, ok
+
+
+@pytest.mark.parametrize("schedule", [("columns", 1), ("columns", 2), ("columns", 4)], ids=["cols1", "cols2", "cols4"])
+@pytest.mark.parametrize("case", SPEC_ADJ_CASES, ids=[c[0] for c in SPEC_ADJ_CASES])
+def test_partially_specular_adjoint_matches_oracle(case, schedule):
+    """Accommodation alpha < 1 (Eq. diffuse2 with a specular part): the transposed sweep reflects
+    (1 - alpha) 2 |v_a|/dx z of the mirrored velocity at each wall face into the next one; the GPU
+    gradient against the oracle's adjoint of the same iteration."""
+    name, mask, px, py, delta, quad, alpha = case
+    d = _delta_field(mask, delta, 4)
+    sol = dvm.Solver(mask, px, py, delta=delta, quad=quad, precision="fp64", store_distribution=True,
+                     schedule=schedule, accommodation=alpha)
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=400000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=400000)
+    g_ref, ok = _oracle_spec_gradient(name)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale, np.abs(grad - g_ref).max() / scale
+    q, _ = sol.flowrate()
+    assert abs(q_id - q) < 1e-9 * abs(q)
+    assert np.all(grad[mask == 1] == 0.0)
+
+
+UNEQUAL_ADJ_CASES = [
+    # name, mask, periodic_x, delta, quad, alpha, top_u
+    ("plates_gh8", np.zeros((18, 5), np.uint8), True, 0.6, ("gh", 8, 0.0), 1.0, 0.0),
+    ("plates8x4_gh4", np.zeros((8, 4), np.uint8), True, 0.9, ("gh", 4, 0.0), 1.0, 0.0),
+    ("notched_nc8", _notch(9, 14), True, 1.2, ("nc", 8, 4.0), 1.0, 0.0),
+    ("notched_nc8_a0.6", _notch(9, 14), True, 1.2, ("nc", 8, 4.0), 0.6, 0.0),
+    ("couette_notched_cubic8_a0.7", _notch(9, 14), True, 1.0, ("cubic", 8, 4.0), 0.7, 1.0),
+]
+
+
+@pytest.mark.parametrize("schedule", [("columns", 1), ("columns", 2), ("columns", 4)], ids=["cols1", "cols2", "cols4"])
+@pytest.mark.parametrize("case", UNEQUAL_ADJ_CASES, ids=[c[0] for c in UNEQUAL_ADJ_CASES])
+def test_unequal_rows_adjoint_matches_oracle(case, schedule):
+    """Rows of seeded unequal heights (stored transposed: columns of unequal width): the transposed
+    sweep pulls z of its two forward-downstream columns with their stretched weights; the source
+    g = W v1 dA / Lx carries each row's height."""
+    name, mask, px, delta, quad, alpha, top_u = case
+    dy = _stretched_rows(mask.shape[0], 23)
+    force = 0.0 if top_u else 1.0
+    d = _delta_field(mask, delta, 6)
+    sol = dvm.Solver(mask, px, False, delta=delta, quad=quad, precision="fp64", store_distribution=True,
+                     schedule=schedule, accommodation=alpha, top_wall_u1=top_u, force=force, dx1=0.07,
+                     row_heights=dy)
+    assert sol.info()["transposed"]
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=400000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=400000)
+    g_ref, ok = _oracle_unequal_gradient(name)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale, np.abs(grad - g_ref).max() / scale
+    if force:
+        assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)
+    else:
+        assert abs(q_id) < 1e-14
+
+
+@pytest.mark.parametrize("schedule", [("rows", 0), ("columns", 1), ("columns", 2)], ids=["rows", "cols1", "cols2"])
+@pytest.mark.parametrize("storage", ["as_given", "transposed"])
+def test_rectangular_cells_adjoint_matches_oracle(storage, schedule):
+    """Equal rows of height ly / ny with a different x1 spacing (cells not square)."""
+    mask = _notch(12, 10)
+    ny = mask.shape[0]
+    d = _delta_field(mask, 1.1, 8)
+    sol = dvm.Solver(mask, True, False, delta=1.1, quad=("nc", 8, 4.0), precision="fp64", store_distribution=True,
+                     schedule=schedule, dx1=0.043, storage=storage)
+    sol.set_delta_field(d)
+    sol.solve(tol=1e-13, max_iter=400000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=400000)
+    p = oracle.Problem.make(mask, True, False, d, ("nc", 8, 4.0), dy=np.full(ny, 1.0 / ny), dx1=0.043)
+    ref = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_ref, _, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=400000)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale, np.abs(grad - g_ref).max() / scale
+    assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)
+
+
+@pytest.mark.parametrize("schedule", [("columns", 1), ("columns", 4)], ids=["cols1", "cols4"])
+def test_unequal_rows_adjoint_with_a_uniform_collision_rate(schedule):
+    """Unequal rows with one collision rate for every cell (no delta field): the transposed sweep still
+    takes per-cell denominators, since the stretched columns change the stencil's diagonal."""
+    mask = _notch(9, 14)
+    dy = _stretched_rows(mask.shape[0], 29)
+    sol = dvm.Solver(mask, True, False, delta=0.9, quad=("nc", 8, 4.0), precision="fp64", store_distribution=True,
+                     schedule=schedule, dx1=0.07, row_heights=dy)
+    sol.solve(tol=1e-13, max_iter=400000)
+    grad, q_id, iters = sol.adjoint(tol=1e-13, max_iter=400000)
+    p = oracle.Problem.make(mask, True, False, 0.9, ("nc", 8, 4.0), dy=dy, dx1=0.07)
+    ref = oracle.solve(p, tol=1e-14, max_iter=400000)
+    g_ref, _, _, ok = oracle.adjoint(p, ref["h"], ref["c"], tol=1e-13, max_iter=400000)
+    assert ok
+    scale = np.abs(g_ref).max()
+    assert np.abs(grad - g_ref).max() < 1e-8 * scale, np.abs(grad - g_ref).max() / scale
+    assert abs(q_id - sol.flowrate()[0]) < 1e-9 * abs(q_id)
