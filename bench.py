@@ -79,6 +79,8 @@ NCU_TRAFFIC = {
     ("batched", "fp32", "rows", 16): {"bytes": 704.28e6, "src": "cac1214a4399438b"},
     ("porous", "fp32", "rows", 16): {"bytes": 73.33e6, "src": "cac1214a4399438b"},
     ("rough", "fp32", "rows", 8): {"bytes": 14.36e6, "src": "cac1214a4399438b"},
+    ("rough", "fp32", "rows", 16): {"bytes": 14.37e6, "src": "cac1214a4399438b"},
+    ("batched", "fp64", "rows", 16): {"bytes": 1124.2e6, "src": "cac1214a4399438b"},
     ("rough", "fp64", "rows", 8): {"bytes": 21.05e6, "src": "cac1214a4399438b"},
 }
 L2_FLUSH_BYTES = 256 << 20
