@@ -307,6 +307,21 @@ int dvm_batch_kernels_per_sweep(const dvm_batch *batch);
 dvm_status dvm_batch_set_persistent(dvm_batch *batch, int on);
 /* on: 1 when the batch uses the persistent launch; blocks: the blocks of that launch (or 0). */
 dvm_status dvm_batch_get_persistent(const dvm_batch *batch, int *on, int *blocks);
+
+/* Paired velocity groups in the FP32 row sweep (an implementation choice, same update as Eq.
+ * (iteration)): a warp sweeps two groups of 32 velocities of one quadrant, each lane holding one velocity
+ * of each, so the cell records, the waits and the loop control serve 64 velocities and the update runs
+ * as packed FP32x2 arithmetic.  Needs FP32 storage, a uniform collision rate, fully diffuse fixed walls,
+ * equal rows, per-kernel launches and grids narrow enough for the doubled shared-memory ring (192 cells
+ * at 16 cells per chunk); members outside these keep one group per warp.  Pairing halves the blocks of a
+ * launch, so DVM_PAIRING_AUTO (the default) pairs only when the launch has at least three waves of
+ * single-group blocks; DVM_PAIRING_ON pairs wherever eligible, DVM_PAIRING_OFF never.  The batch is
+ * re-planned (its graphs rebuilt; the members' state is untouched).  DVM_EINVAL for another mode. */
+enum dvm_pairing { DVM_PAIRING_AUTO = 0, DVM_PAIRING_ON = 1, DVM_PAIRING_OFF = 2 };
+dvm_status dvm_batch_set_pairing(dvm_batch *batch, int mode);
+/* mode: the batch's dvm_pairing policy; paired_blocks: sweep blocks of the planned launch that sweep
+ * paired groups (0 when none). */
+dvm_status dvm_batch_get_pairing(const dvm_batch *batch, int *mode, int *paired_blocks);
 void dvm_batch_destroy(dvm_batch *batch);
 
 /* One-shot batch: create, run, destroy. */

@@ -95,6 +95,7 @@ struct dvm_batch {
   int warps = 0, cw = 0, nsweep = 0, nfin = 0;
   int row_tiles = 1;                 // row sweep: most velocity groups a block sweeps side by side
   int kind = DVM_SWEEP_COLUMNS, cols_v = 1;  // resolved sweep schedule of the launch
+  int pairing = DVM_PAIRING_AUTO, pair_blocks = 0;  // paired-group policy and the paired blocks planned
   InstanceDesc *d_descs = nullptr;
   int *d_smap = nullptr, *d_fmap = nullptr;
   cudaStream_t stream = nullptr;
@@ -234,6 +235,7 @@ struct Schedule {
   int kind = DVM_SWEEP_COLUMNS;
   int v = 1;
   bool persistent = false;  // row sweep only: the persistent batched launch (dvm_persist.cu)
+  int pairing = DVM_PAIRING_AUTO;  // FP32 row sweep: paired velocity groups (dvm_batch_set_pairing)
 };
 
 // The column sweep needs nx * v <= kColsMaxThreads (a thread per column and velocity subset); the
@@ -397,6 +399,8 @@ LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const in
   L.warps = warps;
   L.row_tiles = 1;
   L.cw = cw;
+  L.pair_tiles = 0;
+  L.pair_warps = 0;
   L.anderson = 0;
   L.aa_blocks = 0;
   return L;
@@ -626,23 +630,73 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
     }
     while (row_tiles > 1 && sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles) > (size_t)smem_optin) --row_tiles;
   }
+  // Paired groups (FP32 row sweep with a uniform collision rate, per-kernel launches): a member sweeps two
+  // velocity groups of a quadrant per warp, k pairs side by side, when the paired layout of the launch
+  // fits the shared memory; the widest members that would not fit keep one group per warp.
+  // Pairing halves the blocks, so it is used only when the launch has at least three waves of single-
+  // group blocks (otherwise the SMs it leaves idle cost more than it saves).
+  int pair_tiles = 0, pair_warps = 0;
+  std::vector<int> pair_k(n, 0);
+  long long single_blocks = 0;
+  if (!cols)
+    for (int i = 0; i < n; ++i) {
+      const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
+      const int k = std::max(1, std::min(b->warps / need, row_tiles));
+      single_blocks += (ctxs[i]->ngroups + k - 1) / k;
+    }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
+  b->pairing = sched.pairing;
+  if (!cols && !b->fp64 && b->uniform && !spec && !sched.persistent && n < (1 << 14) &&
+      (sched.pairing == DVM_PAIRING_ON ||
+       (sched.pairing == DVM_PAIRING_AUTO && single_blocks >= 3LL * std::max(nsm, 1)))) {
+    for (int cap = b->warps; cap >= 1 && pair_tiles == 0; --cap) {
+      int tiles = 0, warps = 0;
+      for (int i = 0; i < n; ++i) {
+        const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
+        pair_k[i] = (need <= cap && ctxs[i]->gq >= 2) ? std::min(std::min(cap / need, ctxs[i]->gq / 2), 7) : 0;
+        tiles = std::max(tiles, pair_k[i]);
+        warps = std::max(warps, pair_k[i] * need);
+      }
+      if (tiles == 0) break;
+      if (sweep_pair_smem_layout(warps, b->cw, tiles).total <= (size_t)smem_optin) {
+        pair_tiles = tiles;
+        pair_warps = warps;
+      }
+    }
+    if (pair_tiles == 0) std::fill(pair_k.begin(), pair_k.end(), 0);
+  }
   for (int i = 0; i < n; ++i) {
     if (cols) {
       for (int g = 0; g < ctxs[i]->ngroups; ++g)
         for (int part = 0; part < parts; ++part) smap.push_back((i << 16) | (part << 12) | g);
+    } else if (pair_k[i] > 0) {
+      // pairs (g, g + 1) within each quadrant, pair_k of them per block; an odd group left over at the
+      // end of a quadrant is swept alone
+      const int gq = ctxs[i]->gq, np = gq / 2;
+      for (int q = 0; q < 4; ++q) {
+        for (int m = 0; m < np; m += pair_k[i]) {
+          const int k = std::min(pair_k[i], np - m);
+          smap.push_back(kPairFlag | (i << 16) | (k << 12) | (q * gq + 2 * m));
+        }
+        if (gq & 1) smap.push_back((i << 16) | (1 << 12) | (q * gq + gq - 1));
+      }
     } else {
       const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
       const int k = std::max(1, std::min(b->warps / need, row_tiles));
       for (int g = 0; g < ctxs[i]->ngroups; g += k) smap.push_back((i << 16) | (k << 12) | g);
     }
   }
+  b->pair_blocks = (int)std::count_if(smap.begin(), smap.end(), [](int e) { return (e & kPairFlag) != 0; });
   // longest sweeps first
-  std::stable_sort(smap.begin(), smap.end(), [&](int a, int c) { return work[a >> 16] > work[c >> 16]; });
+  std::stable_sort(smap.begin(), smap.end(),
+                   [&](int a, int c) { return work[(a >> 16) & 0x3fff] > work[(c >> 16) & 0x3fff]; });
   b->nsweep = (int)smap.size();
   b->nfin = (int)fmap.size();
   b->row_tiles = row_tiles;
-  const size_t smem = cols ? cols_smem_bytes(b->fp64, b->cols_v, b->warps)
-                           : sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles);
+  size_t smem = cols ? cols_smem_bytes(b->fp64, b->cols_v, b->warps)
+                     : sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles);
+  if (pair_tiles > 0) smem = std::max(smem, sweep_pair_smem_layout(pair_warps, b->cw, pair_tiles).total);
   if ((!cols && b->warps > kMaxSweepWarps) || (cols && b->warps * kLanes > kColsMaxThreads) || smem > (size_t)smem_optin) {
     batch_free(b);
     return fail(c0, DVM_EINVAL, "batched grids too wide for the sweep's shared memory");
@@ -670,6 +724,8 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
 #undef BATCH_CUDA
   LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw, b->cols_v, spec);
   L.row_tiles = b->row_tiles;
+  L.pair_tiles = pair_tiles;
+  L.pair_warps = pair_warps;
   {
     long long aa_max = 0;
     for (int i = 0; i < n; ++i) aa_max = std::max(aa_max, ctxs[i]->aa_n);
@@ -720,7 +776,9 @@ dvm_status batch_replan(dvm_batch *b, const Schedule &sched) {
   dvm_batch *nb = nullptr;
   dvm_ctx *c0 = b->ctxs[0];
   DVM_CUDA(c0, cudaStreamSynchronize(b->stream));
-  dvm_status st = batch_build(b->ctxs.data(), (int)b->ctxs.size(), &nb, &sched);
+  Schedule s2 = sched;
+  s2.pairing = b->pairing;  // the batch's pairing policy outlives schedule changes
+  dvm_status st = batch_build(b->ctxs.data(), (int)b->ctxs.size(), &nb, &s2);
   if (st != DVM_OK) return st;
   std::swap(*b, *nb);
   batch_free(nb);
@@ -1773,6 +1831,30 @@ dvm_status dvm_batch_set_persistent(dvm_batch *batch, int on) {
   if (sc.persistent && sc.kind != DVM_SWEEP_ROWS)
     return fail(batch->ctxs[0], DVM_EINVAL, "the persistent launch runs the row sweep: set a row schedule first");
   return batch_replan(batch, sc);
+}
+
+dvm_status dvm_batch_set_pairing(dvm_batch *batch, int mode) {
+  if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;  // a member context was destroyed
+  if (mode != DVM_PAIRING_AUTO && mode != DVM_PAIRING_ON && mode != DVM_PAIRING_OFF)
+    return fail(batch->ctxs[0], DVM_EINVAL, "pairing mode must be DVM_PAIRING_AUTO, _ON or _OFF");
+  Schedule sc;
+  sc.kind = batch->kind;
+  sc.v = batch->kind == DVM_SWEEP_ROWS ? batch->cw : batch->cols_v;
+  sc.persistent = batch->persistent;
+  const int old = batch->pairing;
+  batch->pairing = mode;
+  const dvm_status st = batch_replan(batch, sc);
+  if (st != DVM_OK) batch->pairing = old;
+  return st;
+}
+
+dvm_status dvm_batch_get_pairing(const dvm_batch *batch, int *mode, int *paired_blocks) {
+  if (!batch) return DVM_EINVAL;
+  if (batch->detached) return DVM_ESTATE;
+  if (mode) *mode = batch->pairing;
+  if (paired_blocks) *paired_blocks = batch->pair_blocks;
+  return DVM_OK;
 }
 
 dvm_status dvm_batch_get_persistent(const dvm_batch *batch, int *on, int *blocks) {

@@ -40,6 +40,37 @@ __host__ __device__ inline SweepSmemLayout sweep_smem_layout(int R, int cw, int 
 
 size_t sweep_smem_bytes(bool fp64, int warps, int cw, int ntile = 1);
 
+// Paired FP32 row sweep (dvm_sweep_pair.cuh): a warp sweeps two velocity groups of one quadrant, lane l
+// holding velocity l of each (entries 2l, 2l+1 of a 64-wide ring row).  Sweep-map entries of paired
+// blocks carry kPairFlag; their group field is the first group of the first pair and the 4-bit field the
+// number of pairs side by side.  Layout: the ring (R warps x 3 x CW cells x kPairRS floats), the record
+// stages, the 1/denominator tables and weights of each pair (interleaved like the ring), the weights'
+// tensor-core fragments, progress words.
+constexpr int kPairFlag = 1 << 30;
+constexpr int kPairRS = 68;  // 64 velocities + 16 bytes: ldmatrix rows at 272-byte stride are conflict-free
+struct SweepPairSmemLayout {
+  size_t ring, stage, inv, wts, bfr, prog, total;
+};
+__host__ __device__ inline SweepPairSmemLayout sweep_pair_smem_layout(int R, int cw, int ntile) {
+  SweepPairSmemLayout L;
+  size_t off = 0;
+  auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  L.ring = off;
+  off = align16(off + (size_t)R * 3 * cw * kPairRS * 4);
+  L.stage = off;
+  off = align16(off + (size_t)R * 2 * cw * 48);
+  L.inv = off;
+  off = align16(off + (size_t)ntile * kInvRows * 2 * kLanes * 4);
+  L.wts = off;
+  off = align16(off + (size_t)ntile * kSweepWtsRows * kPairRS * 4);
+  L.bfr = off;  // the weights as tensor-core B fragments: [pair][k-step 0-7][lane] x 16 bytes
+  off = align16(off + (size_t)ntile * 8 * kLanes * 16);
+  L.prog = off;
+  off = align16(off + (size_t)R * sizeof(int));
+  L.total = off;
+  return L;
+}
+
 // Column sweep (dvm_sweep_cols.cuh): shared-memory layout -- per-pair velocity constants, the
 // 1/denominator table of the block's velocities and the 3-deep ring of column results.
 constexpr int kColsMaxThreads = 512;

@@ -29,6 +29,7 @@
 #pragma once
 #include <climits>
 #include <cstdint>
+#include <algorithm>
 #include <type_traits>
 
 #include "dvm_device.cuh"
@@ -637,16 +638,34 @@ __device__ __forceinline__ void sweep_tile(const LaunchDesc &L, int map, unsigne
   if (lane == 0) st_release(&prog[w], INT_MAX / 2);  // no more rows: never wait on this warp again
 }
 
+}  // namespace sweep
+}  // namespace dvm
+
+#include "dvm_sweep_pair.cuh"
+
+namespace dvm {
+namespace sweep {
+
+// One block per sweep-map entry: a tile of one velocity group per warp, or (FP32 forward launches with a
+// uniform collision rate) a tile of group pairs when the entry carries kPairFlag.
 template <typename T, bool UNIF, int CW, bool ADJ>
 __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) sweep_kernel(LaunchDesc L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  sweep_tile<T, UNIF, CW, ADJ, false>(L, L.sweep_map[blockIdx.x], smem, (int)(blockDim.x >> 5));
+  const int map = L.sweep_map[blockIdx.x];
+  if constexpr (sizeof(T) == 4 && UNIF && !ADJ) {
+    if (map & kPairFlag) {
+      sweep_tile_pair<CW>(L, map, smem, (int)(blockDim.x >> 5));
+      return;
+    }
+  }
+  sweep_tile<T, UNIF, CW, ADJ, false>(L, map, smem, (int)(blockDim.x >> 5));
 }
 
 template <typename T, bool UNIF, int CW, bool ADJ>
 cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   auto kern = sweep_kernel<T, UNIF, CW, ADJ>;
-  const size_t smem = layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total;
+  size_t smem = layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total;
+  if (L.pair_tiles > 0) smem = std::max(smem, sweep_pair_smem_layout(L.pair_warps, CW, L.pair_tiles).total);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<nblocks, L.warps * kLanes, smem, stream>>>(L);

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdvm.so")
 
 DVM_OK, DVM_EINVAL, DVM_ENOMEM, DVM_ECUDA, DVM_ENOCONV, DVM_ETIMEOUT, DVM_ENUMERIC, DVM_ESTATE = range(8)
+PAIRING = {"auto": 0, "on": 1, "off": 2}  # dvm_pairing
 QUAD_KINDS = {"gh": 0, "nc": 1, "cubic": 2}
 STORAGE = {"auto": 0, "as_given": 1, "transposed": 2}
 FP64, FP32_ACC64 = 0, 1
@@ -105,6 +106,8 @@ def lib():
         L.dvm_probe_peaks.argtypes = [I, D, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.dvm_batch_set_persistent.argtypes = [P, I]
         L.dvm_batch_get_persistent.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+        L.dvm_batch_set_pairing.argtypes = [P, I]
+        L.dvm_batch_get_pairing.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
         for name in ("dvm_params_init", "dvm_create", "dvm_set_delta_field", "dvm_reset", "dvm_solve",
                      "dvm_iterate", "dvm_flowrate", "dvm_fields", "dvm_get_info", "dvm_distribution",
                      "dvm_quadrature", "dvm_batch_solve", "dvm_velocity_grid", "dvm_batch_create",
@@ -112,7 +115,8 @@ def lib():
                      "dvm_moments_noalloc", "dvm_adjoint", "dvm_set_schedule", "dvm_get_schedule",
                      "dvm_batch_set_schedule", "dvm_batch_get_schedule", "dvm_batch_autotune",
                      "dvm_batch_enqueue", "dvm_batch_check", "dvm_selftest_wait", "dvm_probe_peaks",
-                     "dvm_batch_set_persistent", "dvm_batch_get_persistent"):
+                     "dvm_batch_set_persistent", "dvm_batch_get_persistent", "dvm_batch_set_pairing",
+                     "dvm_batch_get_pairing"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -381,6 +385,21 @@ class Batch:
         if st != DVM_OK:
             self._err(st)
         return bool(on.value), blocks.value
+
+    def set_pairing(self, mode):
+        """Paired velocity groups in the FP32 row sweep: "auto", "on" or "off" (dvm_batch_set_pairing)."""
+        self._touch()
+        st = lib().dvm_batch_set_pairing(self._b, PAIRING[mode])
+        if st != DVM_OK:
+            self._err(st)
+
+    def pairing(self):
+        """(mode, sweep blocks of the planned launch that sweep paired groups)."""
+        mode, blocks = ctypes.c_int(), ctypes.c_int()
+        st = lib().dvm_batch_get_pairing(self._b, ctypes.byref(mode), ctypes.byref(blocks))
+        if st != DVM_OK:
+            self._err(st)
+        return {v: k for k, v in PAIRING.items()}[mode.value], blocks.value
 
     def autotune(self, sweeps=5):
         """Time every fitting sweep kernel (the trial sweeps advance the state); keeps the fastest.
