@@ -399,8 +399,7 @@ LaunchDesc make_launch(const InstanceDesc *insts, const int *sweep_map, const in
   L.warps = warps;
   L.row_tiles = 1;
   L.cw = cw;
-  L.pair_tiles = 0;
-  L.pair_warps = 0;
+  L.pair_smem = 0;
   L.anderson = 0;
   L.aa_blocks = 0;
   return L;
@@ -631,11 +630,11 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
     while (row_tiles > 1 && sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles) > (size_t)smem_optin) --row_tiles;
   }
   // Paired groups (FP32 row sweep with a uniform collision rate, per-kernel launches): a member sweeps two
-  // velocity groups of a quadrant per warp, k pairs side by side, when the paired layout of the launch
-  // fits the shared memory; the widest members that would not fit keep one group per warp.
-  // Pairing halves the blocks, so it is used only when the launch has at least three waves of single-
-  // group blocks (otherwise the SMs it leaves idle cost more than it saves).
-  int pair_tiles = 0, pair_warps = 0;
+  // velocity groups of a quadrant per warp, k pairs side by side (as many as fill the block's warps and
+  // fit the shared memory), when its paired layout fits at all.  Pairing halves the blocks, so it is used
+  // only when the launch has at least three waves of single-group blocks (otherwise the SMs it leaves
+  // idle cost more than it saves).
+  size_t pair_smem = 0;
   std::vector<int> pair_k(n, 0);
   long long single_blocks = 0;
   if (!cols)
@@ -650,21 +649,18 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   if (!cols && !b->fp64 && b->uniform && !spec && !sched.persistent && n < (1 << 14) &&
       (sched.pairing == DVM_PAIRING_ON ||
        (sched.pairing == DVM_PAIRING_AUTO && single_blocks >= 3LL * std::max(nsm, 1)))) {
-    for (int cap = b->warps; cap >= 1 && pair_tiles == 0; --cap) {
-      int tiles = 0, warps = 0;
-      for (int i = 0; i < n; ++i) {
-        const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
-        pair_k[i] = (need <= cap && ctxs[i]->gq >= 2) ? std::min(std::min(cap / need, ctxs[i]->gq / 2), 7) : 0;
-        tiles = std::max(tiles, pair_k[i]);
-        warps = std::max(warps, pair_k[i] * need);
-      }
-      if (tiles == 0) break;
-      if (sweep_pair_smem_layout(warps, b->cw, tiles).total <= (size_t)smem_optin) {
-        pair_tiles = tiles;
-        pair_warps = warps;
+    for (int i = 0; i < n; ++i) {
+      const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
+      if (ctxs[i]->gq < 2) continue;
+      for (int k = std::min(std::min(b->warps / need, ctxs[i]->gq / 2), 7); k >= 1; --k) {
+        const size_t bytes = sweep_pair_smem_layout(k * need, b->cw, k).total;
+        if (bytes <= (size_t)smem_optin) {
+          pair_k[i] = k;
+          pair_smem = std::max(pair_smem, bytes);
+          break;
+        }
       }
     }
-    if (pair_tiles == 0) std::fill(pair_k.begin(), pair_k.end(), 0);
   }
   for (int i = 0; i < n; ++i) {
     if (cols) {
@@ -696,7 +692,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   b->row_tiles = row_tiles;
   size_t smem = cols ? cols_smem_bytes(b->fp64, b->cols_v, b->warps)
                      : sweep_smem_bytes(b->fp64, b->warps, b->cw, row_tiles);
-  if (pair_tiles > 0) smem = std::max(smem, sweep_pair_smem_layout(pair_warps, b->cw, pair_tiles).total);
+  smem = std::max(smem, pair_smem);
   if ((!cols && b->warps > kMaxSweepWarps) || (cols && b->warps * kLanes > kColsMaxThreads) || smem > (size_t)smem_optin) {
     batch_free(b);
     return fail(c0, DVM_EINVAL, "batched grids too wide for the sweep's shared memory");
@@ -724,8 +720,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
 #undef BATCH_CUDA
   LaunchDesc L = make_launch(b->d_descs, b->d_smap, b->d_fmap, n, b->warps, b->cw, b->cols_v, spec);
   L.row_tiles = b->row_tiles;
-  L.pair_tiles = pair_tiles;
-  L.pair_warps = pair_warps;
+  L.pair_smem = (int)pair_smem;
   {
     long long aa_max = 0;
     for (int i = 0; i < n; ++i) aa_max = std::max(aa_max, ctxs[i]->aa_n);

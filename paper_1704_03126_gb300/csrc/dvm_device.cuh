@@ -207,9 +207,8 @@ struct LaunchDesc {
   int row_tiles;             // row sweep: most velocity groups a block sweeps side by side (shared-memory
                              // layout); a sweep-map entry carries its own count
   int cw;                    // chunk width (cells per warp and step) of the sweep: 1, 2, 4, 8 or 16
-  int pair_tiles;            // FP32 row sweep: most group pairs a paired block sweeps side by side (0: the
-                             // launch has no paired blocks; sweep-map entries flagged kPairFlag)
-  int pair_warps;            // ... and the most warps a paired block uses (its shared-memory layout)
+  int pair_smem;             // FP32 row sweep: shared-memory bytes of the largest paired block's layout (0: the
+                             // launch has no paired blocks; their sweep-map entries carry kPairFlag)
   int cols_v;                // 0: row-wavefront sweep; 1, 2, 4: column sweep with that many threads per
                              // column (the block's velocity set is split among them)
   int specular;              // 1: some instance has accommodation < 1 or a moving plate (column sweep only)

@@ -43,9 +43,10 @@ size_t sweep_smem_bytes(bool fp64, int warps, int cw, int ntile = 1);
 // Paired FP32 row sweep (dvm_sweep_pair.cuh): a warp sweeps two velocity groups of one quadrant, lane l
 // holding velocity l of each (entries 2l, 2l+1 of a 64-wide ring row).  Sweep-map entries of paired
 // blocks carry kPairFlag; their group field is the first group of the first pair and the 4-bit field the
-// number of pairs side by side.  Layout: the ring (R warps x 3 x CW cells x kPairRS floats), the record
-// stages, the 1/denominator tables and weights of each pair (interleaved like the ring), the weights'
-// tensor-core fragments, progress words.
+// number of pairs side by side.  Each paired block lays out its own shared memory for its R warps and
+// ntile pairs: the ring (R x 3 x CW cells x kPairRS floats), one record stage per warp, the
+// 1/denominator tables and weights of each pair (interleaved like the ring), the weights' tensor-core
+// fragments, progress words.
 constexpr int kPairFlag = 1 << 30;
 constexpr int kPairRS = 68;  // 64 velocities + 16 bytes: ldmatrix rows at 272-byte stride are conflict-free
 struct SweepPairSmemLayout {
@@ -58,7 +59,7 @@ __host__ __device__ inline SweepPairSmemLayout sweep_pair_smem_layout(int R, int
   L.ring = off;
   off = align16(off + (size_t)R * 3 * cw * kPairRS * 4);
   L.stage = off;
-  off = align16(off + (size_t)R * 2 * cw * 48);
+  off = align16(off + (size_t)R * cw * 48);
   L.inv = off;
   off = align16(off + (size_t)ntile * kInvRows * 2 * kLanes * 4);
   L.wts = off;

@@ -665,7 +665,7 @@ template <typename T, bool UNIF, int CW, bool ADJ>
 cudaError_t launch(const LaunchDesc &L, int nblocks, cudaStream_t stream) {
   auto kern = sweep_kernel<T, UNIF, CW, ADJ>;
   size_t smem = layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total;
-  if (L.pair_tiles > 0) smem = std::max(smem, sweep_pair_smem_layout(L.pair_warps, CW, L.pair_tiles).total);
+  smem = std::max(smem, (size_t)L.pair_smem);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<nblocks, L.warps * kLanes, smem, stream>>>(L);

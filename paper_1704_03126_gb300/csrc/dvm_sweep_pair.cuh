@@ -71,7 +71,8 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
   const int quad = min(ga, D->ngroups - 1) / D->groups_per_quadrant;
   const bool xneg = (quad & 1) != 0, yneg = (quad & 2) != 0;
 
-  const SweepPairSmemLayout SL = sweep_pair_smem_layout(L.pair_warps, CW, L.pair_tiles);
+  // this block's own layout (the launch provides the largest any paired block needs)
+  const SweepPairSmemLayout SL = sweep_pair_smem_layout(ntile * R, CW, ntile);
   float *ring = reinterpret_cast<float *>(smem + SL.ring);
   SweepRec<float> *stage = reinterpret_cast<SweepRec<float> *>(smem + SL.stage);
   float *invt_all = reinterpret_cast<float *>(smem + SL.inv);
@@ -98,7 +99,7 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
       wts_all[(j * kSweepWtsRows + m) * RS + e] = ((e & 1) ? vB : vA)[fld * kLanes + (e >> 1)];
     }
   }
-  for (int i = threadIdx.x; i < min(Rb, L.pair_warps); i += Rb * kLanes) prog[i] = i % R;
+  for (int i = threadIdx.x; i < min(Rb, ntile * R); i += Rb * kLanes) prog[i] = i % R;
   __syncthreads();
   for (int i = threadIdx.x; i < ntile * 8 * kLanes; i += Rb * kLanes) {
     const int j = i / (8 * kLanes), sl = i - j * 8 * kLanes;
@@ -147,9 +148,11 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
     st_dst[k] = l * (int)sizeof(SweepRec<float>) + 16 * (pc - r * NPC);
   }
   float2 pf_hp1 = bcast(0.f), pf_hp2 = bcast(0.f);
-  auto issue = [&](int q, int c, int buf) {
+  // records of chunk (q, c) into the warp's stage (one buffer: the next chunk is staged as soon as the
+  // cell loop of the current one is done, overlapping the copy with its sums and the next wait)
+  auto issue = [&](int q, int c) {
     const int j = yneg ? ny - 1 - q : q;
-    SweepRec<float> *sdst = stage + ((size_t)w * 2 + buf) * CW;
+    SweepRec<float> *sdst = stage + (size_t)w * CW;
     const int p0 = c * CW;
     const int cnt = min(CW, nx - p0);
     const char *src = reinterpret_cast<const char *>(rec + j * nx + (xneg ? nx - p0 - cnt : p0));
@@ -183,7 +186,7 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
   // from the seam buffers; MODE 2 (row 1) row q-1 from the ring, row q-2 from the seam buffers
   float2 hp1 = bcast(0.f), hp2 = bcast(0.f), row_hp1 = bcast(0.f), row_hp2 = bcast(0.f);
   auto run_chunk = [&](auto mode_tag, int q, int c, int t, const SweepRec<float> *rs, float *myr, const float *pr1,
-                       const float *pr2) {
+                       const float *pr2, int nq, int nc) {
     constexpr int MODE = decltype(mode_tag)::value;
     const int j = yneg ? ny - 1 - q : q;
     if (c == 0) {
@@ -238,7 +241,12 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
     }
     __syncwarp();
     if (lane == 0) st_release(&prog[w], t + 1);
+    // the codes the sums need, then the stage is free for the next chunk
+    const uint32_t code0 = g4 < cnt ? rs[g4].code : kSolid;
+    const uint32_t code1 = (CW > 8 && g4 + 8 < cnt) ? rs[g4 + 8].code : kSolid;
     __syncwarp();
+    if (nq < ny) issue(nq, nc);
+    else cp_async_commit();
     if (houtA) {
       for (int l = 0; l < cnt; ++l) {
         const int i = xneg ? nx - 1 - (p0 + l) : p0 + l;
@@ -270,7 +278,7 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         if ((hf == 0 || CW > 8) && g4 + 8 * hf < cnt) {
-          const uint32_t code = rs[g4 + 8 * hf].code;
+          const uint32_t code = hf ? code1 : code0;
           const int e = e0 + hf * de;
           if ((code & red_am0) == red_cv0) red_add(red_p0 + e, static_cast<double>(d[2 * hf]));
           if ((code & red_am1) == red_cv1) red_add(red_p1 + e, static_cast<double>(d[2 * hf + 1]));
@@ -284,39 +292,35 @@ __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, un
     atomicExch(&st->err_flag, 1);
   };
 
-  int item = 0;
   int s0 = lw % 3;  // ring slot of the current step t: the warp's steps are lw, lw + 1, ...
   float *ring_w = ring + (size_t)w * 3 * CW * RS;
   const float *ring_p1 = ring + (size_t)wprev * 3 * CW * RS;
   const float *ring_p2 = ring + (size_t)(wb + (lw + 2 * R - 2) % R) * 3 * CW * RS;
-  issue(lw, 0, 0);
+  issue(lw, 0);
   for (int q = lw; q < ny; q += R) {
-    for (int c = 0; c < R; ++c, ++item) {
+    for (int c = 0; c < R; ++c) {
       const int t = q + c;
-      const int buf = item & 1;
       if (c == 0) {
         row_hp1 = pf_hp1;
         row_hp2 = pf_hp2;
       }
       const int nq = (c + 1 < R) ? q : q + R, nc = (c + 1 < R) ? c + 1 : 0;
-      if (nq < ny) issue(nq, nc, buf ^ 1);
-      else cp_async_commit();
-      cp_async_wait<1>();
+      cp_async_wait<0>();
       __syncwarp();
       // row q-1 finished this chunk, and row q+2 has read the ring slot written three steps ago
       if (R > 1 && !wait_at_least(&prog[wprev], t)) return give_up();
       if (R > 2 && !wait_at_least(&prog[wnext2], t)) return give_up();
-      const SweepRec<float> *rs = stage + ((size_t)w * 2 + buf) * CW;
+      const SweepRec<float> *rs = stage + (size_t)w * CW;
       const int s1 = s0 == 0 ? 2 : s0 - 1, s2 = s0 == 2 ? 0 : s0 + 1;
       float *myr = ring_w + s0 * (CW * RS);
       const float *pr1 = ring_p1 + s1 * (CW * RS);
       const float *pr2 = ring_p2 + s2 * (CW * RS);
       s0 = s2;
       if (py && q < 2) {
-        if (q == 0) run_chunk(std::integral_constant<int, 1>(), q, c, t, rs, myr, pr1, pr2);
-        else run_chunk(std::integral_constant<int, 2>(), q, c, t, rs, myr, pr1, pr2);
+        if (q == 0) run_chunk(std::integral_constant<int, 1>(), q, c, t, rs, myr, pr1, pr2, nq, nc);
+        else run_chunk(std::integral_constant<int, 2>(), q, c, t, rs, myr, pr1, pr2, nq, nc);
       } else {
-        run_chunk(std::integral_constant<int, 0>(), q, c, t, rs, myr, pr1, pr2);
+        run_chunk(std::integral_constant<int, 0>(), q, c, t, rs, myr, pr1, pr2, nq, nc);
       }
       __syncwarp();
     }
