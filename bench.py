@@ -76,12 +76,12 @@ FLOPS_PER_UPDATE = {"fp32": 25, "fp64": 25}
 # shape), each with the hash of the sweep kernels' sources it was measured on (kernel_source_hash);
 # a figure whose hash no longer matches is reported as null
 NCU_TRAFFIC = {
-    ("batched", "fp32", "rows", 16): {"bytes": 704.28e6, "src": "cac1214a4399438b"},
-    ("porous", "fp32", "rows", 16): {"bytes": 73.33e6, "src": "cac1214a4399438b"},
-    ("rough", "fp32", "rows", 8): {"bytes": 14.36e6, "src": "cac1214a4399438b"},
-    ("rough", "fp32", "rows", 16): {"bytes": 14.37e6, "src": "cac1214a4399438b"},
-    ("batched", "fp64", "rows", 16): {"bytes": 1124.2e6, "src": "cac1214a4399438b"},
-    ("rough", "fp64", "rows", 8): {"bytes": 21.05e6, "src": "cac1214a4399438b"},
+    ("batched", "fp32", "rows", 16): {"bytes": 719.09e6, "src": "78f5fcfc62be9d66"},
+    ("porous", "fp32", "rows", 16): {"bytes": 73.47e6, "src": "78f5fcfc62be9d66"},
+    ("rough", "fp32", "rows", 8): {"bytes": 14.40e6, "src": "78f5fcfc62be9d66"},
+    ("rough", "fp32", "rows", 16): {"bytes": 14.41e6, "src": "78f5fcfc62be9d66"},
+    ("rough", "fp64", "rows", 8): {"bytes": 21.06e6, "src": "78f5fcfc62be9d66"},
+    ("batched", "fp64", "rows", 16): {"bytes": 1123.98e6, "src": "78f5fcfc62be9d66"},
 }
 L2_FLUSH_BYTES = 256 << 20
 
