@@ -96,6 +96,9 @@ struct dvm_batch {
   int row_tiles = 1;                 // row sweep: most velocity groups a block sweeps side by side
   int kind = DVM_SWEEP_COLUMNS, cols_v = 1;  // resolved sweep schedule of the launch
   int pairing = DVM_PAIRING_AUTO, pair_blocks = 0;  // paired-group policy and the paired blocks planned
+  std::vector<int> single_blocks;  // per member: its blocks with one group per warp (pairing decisions)
+  bool tail_unpaired = false;      // AUTO: pairs dropped for the tail of the last solve
+  bool fixed_plan = false;         // no re-planning (the refinement's correction phase has edited d_descs)
   InstanceDesc *d_descs = nullptr;
   int *d_smap = nullptr, *d_fmap = nullptr;
   cudaStream_t stream = nullptr;
@@ -637,11 +640,13 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   size_t pair_smem = 0;
   std::vector<int> pair_k(n, 0);
   long long single_blocks = 0;
+  b->single_blocks.assign(n, 0);
   if (!cols)
     for (int i = 0; i < n; ++i) {
       const int need = (ctxs[i]->nx + b->cw - 1) / b->cw;
       const int k = std::max(1, std::min(b->warps / need, row_tiles));
-      single_blocks += (ctxs[i]->ngroups + k - 1) / k;
+      b->single_blocks[i] = (ctxs[i]->ngroups + k - 1) / k;
+      single_blocks += b->single_blocks[i];
     }
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
@@ -767,13 +772,17 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
 }
 
 // Rebuild the launch of an existing batch for another schedule; the members' state is untouched.
-dvm_status batch_replan(dvm_batch *b, const Schedule &sched) {
+dvm_status batch_replan(dvm_batch *b, const Schedule &sched, int pairing_override = -1) {
   dvm_batch *nb = nullptr;
   dvm_ctx *c0 = b->ctxs[0];
   DVM_CUDA(c0, cudaStreamSynchronize(b->stream));
   Schedule s2 = sched;
-  s2.pairing = b->pairing;  // the batch's pairing policy outlives schedule changes
+  // the batch's pairing policy outlives schedule changes (an override plans one launch without
+  // changing the policy)
+  s2.pairing = pairing_override >= 0 ? pairing_override : b->pairing;
+  const int policy = b->pairing;
   dvm_status st = batch_build(b->ctxs.data(), (int)b->ctxs.size(), &nb, &s2);
+  if (st == DVM_OK) nb->pairing = policy;
   if (st != DVM_OK) return st;
   std::swap(*b, *nb);
   batch_free(nb);
@@ -812,9 +821,38 @@ dvm_status batch_arm(dvm_batch *b, double tol, int count, std::vector<int> &star
   return DVM_OK;
 }
 
+// The schedule a batch was planned with (for re-planning it).
+Schedule batch_schedule(const dvm_batch *b) {
+  Schedule sc;
+  sc.kind = b->kind;
+  sc.v = b->kind == DVM_SWEEP_ROWS ? b->cw : b->cols_v;
+  sc.persistent = b->persistent;
+  return sc;
+}
+
+// AUTO pairing is planned for every member; once the members still iterating no longer fill three waves
+// of single-group blocks, the rest of the solve runs without pairs (re-planned; the state is untouched).
+dvm_status batch_unpair_tail(dvm_batch *b) {
+  if (b->fixed_plan || b->pairing != DVM_PAIRING_AUTO || b->pair_blocks == 0) return DVM_OK;
+  long long active = 0;
+  for (size_t i = 0; i < b->ctxs.size(); ++i)
+    if (!b->ctxs[i]->h_state->done) active += b->single_blocks[i];
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->ctxs[0]->device);
+  if (active >= 3LL * std::max(nsm, 1)) return DVM_OK;
+  dvm_status st = batch_replan(b, batch_schedule(b), DVM_PAIRING_OFF);
+  if (st == DVM_OK) b->tail_unpaired = true;
+  return st;
+}
+
 dvm_status batch_run(dvm_batch *b, double tol, int max_iter, dvm_status *per, int *iters, double *est) {
   dvm_ctx *c0 = b->ctxs[0];
   if (max_iter < 1) return fail(c0, DVM_EINVAL, "max_iter must be >= 1");
+  if (b->tail_unpaired && !b->fixed_plan) {
+    // a new solve starts with every member: plan the pairs again
+    dvm_status st = batch_replan(b, batch_schedule(b));
+    if (st != DVM_OK) return st;
+  }
   std::vector<int> start;
   dvm_status st = batch_arm(b, tol, max_iter, start);
   if (st != DVM_OK) return st;
@@ -828,6 +866,8 @@ dvm_status batch_run(dvm_batch *b, double tol, int max_iter, dvm_status *per, in
     st = batch_poll(b, &all);
     if (st != DVM_OK) return st;
     if (all) break;
+    st = batch_unpair_tail(b);
+    if (st != DVM_OK) return st;
   }
   dvm_status result = DVM_OK;
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
@@ -1002,7 +1042,9 @@ dvm_status batch_refine(dvm_batch *b, double tol, int max_iter) {
     }
     DVM_CUDA(c0, cudaStreamSynchronize(s));
     std::vector<dvm_status> per(n);
+    b->fixed_plan = true;  // the members' descriptors on the device are the correction phase's
     st = batch_run(b, kCorrectionTol, max_iter, per.data(), nullptr, nullptr);
+    b->fixed_plan = false;
     // back to the members' own descriptors, then x = x~ + d and the records of x with the full drive
     for (int i = 0; i < n; ++i)
       DVM_CUDA(c0, cudaMemcpyAsync(b->d_descs + i, &b->hdescs[i], sizeof(InstanceDesc), cudaMemcpyHostToDevice, s));

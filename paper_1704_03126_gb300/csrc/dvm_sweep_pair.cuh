@@ -7,10 +7,11 @@
 // broadcast operand, which costs nothing).  The two groups share the cell records, the waits, the
 // staging and the loop control, so those are paid once per 64 velocities.  The ring rows hold the 64
 // values interleaved (entry 2l + k is velocity l of the pair's group k), and the per-cell sums are the
-// same tensor-core contraction over 64 velocities.  The ring of a warp is twice as wide, so the paired
-// blocks serve grids up to 192 cells wide (12 warps at 16 cells per chunk); wider grids keep one group
-// per warp.  FP32 storage, forward sweeps, uniform collision rate; rows 0 and 1 of a periodic y axis read
-// their wrapped upstream rows straight from the seam buffers.
+// same tensor-core contraction over 64 velocities.  The ring of a warp is twice as wide: each paired
+// block lays out its own shared memory (a 256-cell grid, 16 warps at 16 cells per chunk, fits one pair
+// per block in 224 of the 227 KB; narrower grids fit several), with one record stage per warp that is
+// refilled as soon as the cell loop is done.  FP32 storage, forward sweeps, uniform collision rate;
+// rows 0 and 1 of a periodic y axis read their wrapped upstream rows straight from the seam buffers.
 #pragma once
 
 namespace dvm {
