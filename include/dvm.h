@@ -150,7 +150,9 @@ typedef struct {
  *                      or 4 (FP64) velocities; `threads_per_column` (1, 2 or 4) threads share a
  *                      column, so a block holds 8, 16 or 32 (FP32) velocities; nx * threads_per_column
  *                      <= 512.
- *   DVM_SWEEP_AUTO     columns, with the most threads per column that fit. */
+ *   DVM_SWEEP_AUTO     rows (chunk width 0) where they apply (accommodation 1, no moving plate, equal
+ *                      rows, nx <= 256) and the launch has velocity groups for at least half the SMs;
+ *                      otherwise columns, with the most threads per column that fit. */
 typedef enum { DVM_SWEEP_AUTO = 0, DVM_SWEEP_ROWS = 1, DVM_SWEEP_COLUMNS = 2 } dvm_sweep_kind;
 
 /* Fill defaults: periodic_x = 1, periodic_y = 0, ly = 1, kn = 0.1, delta = -1, Gauss-Hermite 12,
@@ -315,12 +317,14 @@ dvm_status dvm_batch_get_persistent(const dvm_batch *batch, int *on, int *blocks
  * equal rows, per-kernel launches and a shared-memory layout that fits (up to 256 cells wide at 16 cells
  * per chunk, one pair per block there); members outside these keep one group per warp.  Pairing halves the blocks of a
  * launch, so DVM_PAIRING_AUTO (the default) pairs only when the launch has at least three waves of
- * single-group blocks; DVM_PAIRING_ON pairs wherever eligible, DVM_PAIRING_OFF never.  The batch is
- * re-planned (its graphs rebuilt; the members' state is untouched).  DVM_EINVAL for another mode. */
+ * single-group blocks, and a solve under AUTO re-plans the launch without pairs once the members still
+ * iterating no longer do (the next solve plans them again); DVM_PAIRING_ON pairs wherever eligible,
+ * DVM_PAIRING_OFF never.  The batch is re-planned (its graphs rebuilt; the members' state is
+ * untouched).  DVM_EINVAL for another mode. */
 enum dvm_pairing { DVM_PAIRING_AUTO = 0, DVM_PAIRING_ON = 1, DVM_PAIRING_OFF = 2 };
 dvm_status dvm_batch_set_pairing(dvm_batch *batch, int mode);
-/* mode: the batch's dvm_pairing policy; paired_blocks: sweep blocks of the planned launch that sweep
- * paired groups (0 when none). */
+/* mode: the batch's dvm_pairing policy; paired_blocks: sweep blocks of the launch as currently planned
+ * that sweep paired groups (0 when none, e.g. after a solve that dropped them for its tail). */
 dvm_status dvm_batch_get_pairing(const dvm_batch *batch, int *mode, int *paired_blocks);
 void dvm_batch_destroy(dvm_batch *batch);
 

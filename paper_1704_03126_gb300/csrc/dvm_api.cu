@@ -558,6 +558,18 @@ dvm_status capture_persistent(dvm_batch *b, const LaunchDesc &L, int sweeps, cud
 
 // Build a batch over ctxs (errors reported on ctxs[0]) with the given sweep schedule, or with the
 // first member's requested one.
+// DVM_SWEEP_AUTO: the row sweep where it applies (fully diffuse fixed walls, equal rows, nx <= 256) and the
+// launch has velocity groups for at least half the SMs; otherwise the column sweep, which spreads a few
+// groups over more threads.
+int auto_sweep_kind(dvm_ctx *const *ctxs, int n, int nx_max, bool spec) {
+  if (spec || nx_max > 16 * kMaxSweepWarps) return DVM_SWEEP_COLUMNS;
+  long long groups = 0;
+  for (int i = 0; i < n; ++i) groups += ctxs[i]->ngroups;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctxs[0]->device);
+  return 2 * groups >= std::max(nsm, 1) ? DVM_SWEEP_ROWS : DVM_SWEEP_COLUMNS;
+}
+
 dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Schedule *force = nullptr) {
   if (!ctxs || n < 1 || !ctxs[0]) return DVM_EINVAL;
   dvm_ctx *c0 = ctxs[0];
@@ -582,7 +594,10 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
                                   "no moving plate, no row heights)");
   } else {
     std::string why;
-    if (!resolve_schedule(nx_max, c0->sched_kind, c0->sched_v, &sched, &why, spec)) return fail(c0, DVM_EINVAL, why);
+    const bool automatic = c0->sched_kind == DVM_SWEEP_AUTO;
+    const int kind = automatic ? auto_sweep_kind(ctxs, n, nx_max, spec) : c0->sched_kind;
+    if (!resolve_schedule(nx_max, kind, automatic ? 0 : c0->sched_v, &sched, &why, spec))
+      return fail(c0, DVM_EINVAL, why);
   }
   const bool cols = sched.kind == DVM_SWEEP_COLUMNS;
   dvm_batch *b = new (std::nothrow) dvm_batch();
@@ -1926,8 +1941,11 @@ dvm_status dvm_get_schedule(const dvm_ctx *ctx, int *kind, int *threads_per_colu
   if (!ctx) return DVM_EINVAL;
   Schedule sc;
   std::string why;
-  if (!resolve_schedule(ctx->nx, ctx->sched_kind, ctx->sched_v, &sc, &why, needs_special(ctx)))
-    return fail(const_cast<dvm_ctx *>(ctx), DVM_EINVAL, why);
+  dvm_ctx *c = const_cast<dvm_ctx *>(ctx);
+  const bool automatic = ctx->sched_kind == DVM_SWEEP_AUTO;
+  const int k = automatic ? auto_sweep_kind(&c, 1, ctx->nx, needs_special(ctx)) : ctx->sched_kind;
+  if (!resolve_schedule(ctx->nx, k, automatic ? 0 : ctx->sched_v, &sc, &why, needs_special(ctx)))
+    return fail(c, DVM_EINVAL, why);
   if (kind) *kind = sc.kind;
   if (threads_per_column) *threads_per_column = (sc.kind == DVM_SWEEP_ROWS && sc.v == 0) ? ctx->cw : sc.v;
   return DVM_OK;
