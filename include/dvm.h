@@ -314,8 +314,9 @@ dvm_status dvm_batch_get_persistent(const dvm_batch *batch, int *on, int *blocks
  * (iteration)): a warp sweeps two groups of 32 velocities of one quadrant, each lane holding one velocity
  * of each, so the cell records, the waits and the loop control serve 64 velocities and the update runs
  * as packed FP32x2 arithmetic.  Needs FP32 storage, a uniform collision rate, fully diffuse fixed walls,
- * equal rows, per-kernel launches and a shared-memory layout that fits (up to 256 cells wide at 16 cells
- * per chunk, one pair per block there); members outside these keep one group per warp.  Pairing halves the blocks of a
+ * equal rows and a shared-memory layout that fits (up to 256 cells wide at 16 cells per chunk, one pair
+ * per block there), with per-kernel or persistent launches; members outside these keep one group per
+ * warp.  Pairing halves the blocks of a
  * launch, so DVM_PAIRING_AUTO (the default) pairs only when the launch has at least three waves of
  * single-group blocks, and a solve under AUTO re-plans the launch without pairs once the members still
  * iterating no longer do (the next solve plans them again); DVM_PAIRING_ON pairs wherever eligible,

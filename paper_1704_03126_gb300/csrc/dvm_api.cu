@@ -496,7 +496,7 @@ dvm_status persist_setup(dvm_batch *b, const std::vector<int> &smap, const std::
   for (int i = 0; i < n; ++i) {
     base[i] = (int)tiles.size();
     for (int e : smap)
-      if ((e >> 16) == i) {
+      if (((e >> 16) & 0x3fff) == i) {
         tiles.push_back(e);
         ++count[i];
       }
@@ -666,7 +666,7 @@ dvm_status batch_build(dvm_ctx *const *ctxs, int n, dvm_batch **out, const Sched
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c0->device);
   b->pairing = sched.pairing;
-  if (!cols && !b->fp64 && b->uniform && !spec && !sched.persistent && n < (1 << 14) &&
+  if (!cols && !b->fp64 && b->uniform && !spec && n < (1 << 14) &&
       (sched.pairing == DVM_PAIRING_ON ||
        (sched.pairing == DVM_PAIRING_AUTO && single_blocks >= 3LL * std::max(nsm, 1)))) {
     for (int i = 0; i < n; ++i) {

@@ -19,6 +19,7 @@
 // Coherence.  Items read data that other blocks wrote earlier in the same launch (accumulators, fluxes,
 // records, seams, the instance state).  The writer fences before counting its item finished; the
 // taker fences after its compare-and-swap; reads of such data go through L2 (cp.async.cg, __ldcg).
+#include <algorithm>
 #include <climits>
 
 #include "dvm_device.cuh"
@@ -213,7 +214,15 @@ __global__ void __launch_bounds__(kMaxSweepWarps * kLanes, 1) persist_kernel(Lau
     __threadfence();  // order this block's reads after the take
     const InstanceDesc *D = L.inst + inst;
     if (stage == 0) {
-      sweep::sweep_tile<T, UNIF, CW, false, true>(L, P.tiles[P.tile_base[inst] + idx], smem, Rb);
+      const int map = P.tiles[P.tile_base[inst] + idx];
+      bool paired = false;
+      if constexpr (sizeof(T) == 4 && UNIF) {
+        if (map & kPairFlag) {
+          sweep::sweep_tile_pair<CW, true>(L, map, smem, Rb);
+          paired = true;
+        }
+      }
+      if (!paired) sweep::sweep_tile<T, UNIF, CW, false, true>(L, map, smem, Rb);
     } else if (stage == 1) {
       fin1_item(D, idx, P.fin_cells, sh);
     } else {
@@ -257,7 +266,8 @@ __global__ void persist_selftest_kernel(PersistDesc P, int *result) {
 template <typename T, bool UNIF, int CW>
 cudaError_t launch_p(const LaunchDesc &L, const PersistDesc &P, int blocks, cudaStream_t stream) {
   auto kern = persist_kernel<T, UNIF, CW>;
-  const size_t smem = sweep::layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total;
+  const size_t smem = std::max(sweep::layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total,
+                               (size_t)L.pair_smem);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<blocks, L.warps * kLanes, smem, stream>>>(L, P);
@@ -279,7 +289,8 @@ cudaError_t launch_cw(const LaunchDesc &L, const PersistDesc &P, int blocks, cud
 template <typename T, bool UNIF, int CW>
 int occupancy_p(const LaunchDesc &L) {
   int n = 0;
-  const size_t smem = sweep::layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total;
+  const size_t smem = std::max(sweep::layout<T>(L.warps, CW, L.row_tiles > 0 ? L.row_tiles : 1).total,
+                               (size_t)L.pair_smem);
   auto kern = persist_kernel<T, UNIF, CW>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, L.warps * kLanes, smem) != cudaSuccess) return 0;

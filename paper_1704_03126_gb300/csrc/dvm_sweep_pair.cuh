@@ -53,13 +53,15 @@ __device__ __forceinline__ void cell_sums_mma64(uint32_t base, const uint4 *bfl,
   }
 }
 
-template <int CW>
+// PER as for sweep_tile: the persistent kernel hands out tiles of active members only (every read of data
+// written earlier in the same launch below already goes through L2: cp.async.cg, __ldcg).
+template <int CW, bool PER = false>
 __device__ __forceinline__ void sweep_tile_pair(const LaunchDesc &L, int map, unsigned char *smem, int Rb) {
   constexpr int RS = kPairRS;
   constexpr int NPC = (int)sizeof(SweepRec<float>) / 16, NPIECE = NPC * CW, PPL = (NPIECE + kLanes - 1) / kLanes;
   const InstanceDesc *__restrict__ D = L.inst + ((map >> 16) & 0x3fff);
   DeviceState *st = D->state;
-  if (*reinterpret_cast<volatile int *>(&st->done)) return;
+  if (!PER && *reinterpret_cast<volatile int *>(&st->done)) return;
 
   const int nx = D->nx, ny = D->ny, ncell = D->ncell;
   const bool px = D->periodic_x != 0, py = D->periodic_y != 0;

@@ -35,12 +35,14 @@ CASES = [
 ]
 
 
-def _solve(case, pairing, store=False, schedule=("rows", 0)):
+def _solve(case, pairing, store=False, schedule=("rows", 0), persistent=False):
     _, mask, px, py, kn, quad = case
     sol = dvm.Solver(mask, px, py, kn=kn, quad=quad, precision="fp32", store_distribution=store)
     b = dvm.Batch([sol])
     b.set_schedule(*schedule)
     b.set_pairing(pairing)
+    if persistent:
+        b.set_persistent(True)
     mode, blocks = b.pairing()
     st = b.run(tol=1e-7, max_iter=200000)
     assert all(v == dvm.DVM_OK for v in st)
@@ -64,6 +66,44 @@ def test_paired_groups_match_single_groups_and_the_oracle(case, schedule):
     orc = oracle.solve(oracle.Problem.make(mask, px, py, dvm.kn_to_delta(kn), quad), tol=1e-12, max_iter=400000)
     assert orc["converged"]
     assert abs(q_on - orc["Q"]) < 1e-5 * abs(orc["Q"]), (q_on, orc["Q"])
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_paired_groups_in_the_persistent_launch(case):
+    """The persistent launch hands out paired tiles like single ones: the same sweeps as per-kernel
+    launches with pairs (same sweep count; sums in another order), the same fixed point as launches
+    without pairs (the FP32 stopping test ends on rounding noise, which pairing changes: no sweep count
+    there)."""
+    on, b, blocks_on = _solve(case, "on", persistent=True)
+    assert b.persistent()[0] and blocks_on > 0
+    kern, _, _ = _solve(case, "on")
+    off, _, _ = _solve(case, "off")
+    assert abs(on.info()["iterations"] - kern.info()["iterations"]) <= 2, \
+        (on.info()["iterations"], kern.info()["iterations"], off.info()["iterations"])
+    q_on, q_kern, q_off = on.flowrate()[0], kern.flowrate()[0], off.flowrate()[0]
+    assert abs(q_on - q_kern) < 1e-7 * abs(q_kern), (q_on, q_kern)
+    assert abs(q_on - q_off) < 1e-6 * abs(q_off), (q_on, q_off)
+    gas = case[1] == 0
+    for nm in ("rho", "u1"):
+        f_on, f_off = on.fields()[nm], off.fields()[nm]
+        assert np.abs(f_on[gas] - f_off[gas]).max() < 1e-5 * max(1.0, np.abs(f_off[gas]).max()), nm
+
+
+def test_persistent_batch_of_paired_and_single_members():
+    """All four geometries in one persistent batch (paired and leftover single tiles of several members
+    in one scheduler, members retiring at different sweeps) against separate unpaired solves."""
+    def members():
+        return [dvm.Solver(c[1], c[2], c[3], kn=c[4], quad=c[5], precision="fp32") for c in CASES]
+    sols = members()
+    b = dvm.Batch(sols)
+    b.set_schedule("rows", 0)
+    b.set_pairing("on")
+    b.set_persistent(True)
+    assert b.pairing()[1] > 0
+    assert all(v == dvm.DVM_OK for v in b.run(tol=1e-7, max_iter=200000))
+    for s, case in zip(sols, CASES):
+        off, _, _ = _solve(case, "off")
+        assert abs(s.flowrate()[0] - off.flowrate()[0]) < 1e-6 * abs(off.flowrate()[0]), case[0]
 
 
 def test_paired_sweep_stores_the_same_distribution():
@@ -109,3 +149,20 @@ def test_pairing_policy():
     bm = dvm.Batch(many)
     bm.set_schedule("rows", 16)
     assert bm.pairing()[1] > 0
+    # a solve drops the pairs once the members still iterating fill fewer than three waves, and the
+    # next solve plans them again; the fixed points are those of a launch that never pairs
+    assert all(v == dvm.DVM_OK for v in bm.run(tol=1e-6, max_iter=50000))
+    assert bm.pairing()[0] == "auto"
+    ref = [dvm.Solver(inputs.rough_channel_mask(96), True, False, kn=kn, quad=("cubic", 32, 4.0), precision="fp32")
+           for kn in np.geomspace(0.1, 10.0, 16)]
+    br = dvm.Batch(ref)
+    br.set_schedule("rows", 16)
+    br.set_pairing("off")
+    assert all(v == dvm.DVM_OK for v in br.run(tol=1e-6, max_iter=50000))
+    for a, r in zip(many, ref):
+        assert abs(a.flowrate()[0] - r.flowrate()[0]) < 1e-6 * abs(r.flowrate()[0])
+    for s in many:
+        s.reset()
+    assert all(v == dvm.DVM_OK for v in bm.run(tol=1e-6, max_iter=50000))
+    for a, r in zip(many, ref):
+        assert abs(a.flowrate()[0] - r.flowrate()[0]) < 1e-6 * abs(r.flowrate()[0])
