@@ -876,13 +876,8 @@ def run_adjoint(args, rank, world, local_rank):
     dir2_fd = (qs[-2] - qs[-1]) / (2 * eps_dir)
     dir2_adj = float((grad.ravel() * base.ravel() * dirn2).sum())
     value = a_iters * upd / (adj_ms / 1e3)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak64 = 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
+    alu = device_peaks(dvm)
+    peak64 = alu["fp64"]
     achieved = FLOPS_PER_UPDATE["fp64"] * value / 1e12
     out = {
         "metric": METRICS["adjoint"], "value": value, "unit": UNIT, "n_gpus": world, "steps": a_iters,
@@ -891,8 +886,10 @@ def run_adjoint(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                      "frac": achieved / peak64, "traffic": None,
                      "kernel": f"transposed sweep, {sched[0]} kernel (fp64), whole adjoint iteration incl. bookkeeping",
-                     "flops_per_update": FLOPS_PER_UPDATE["fp64"]},
+                     "flops_per_update": FLOPS_PER_UPDATE["fp64"],
+                     "peak_note": "FP64 FMA chains measured live by dvm_probe_peaks (of measured)"},
         "clocks": clocks,
+        "device_peaks_measured": alu,
         # per adjoint sweep: transposed sweep, seam sums, two finalize kernels; plus arm, reset, gradient
         "gpu_launches": 4 * a_iters + 3,
         "adjoint_vs_plain": {"tol": tol, "forward_iterations": f_iters, "forward_ms": fwd_ms,
