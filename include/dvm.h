@@ -300,8 +300,9 @@ int dvm_batch_kernels_per_sweep(const dvm_batch *batch);
  * from a device-side scheduler: members advance independently, a converged member drops out at once
  * and one member's finalize overlaps the others' sweeps; the launch (with its arming kernel) is one
  * CUDA graph.  Needs the row sweep (dvm_batch_set_schedule rows), fully diffuse fixed walls, equal rows
- * and the plain iteration (DVM_EINVAL otherwise).  Same fixed point and stopping test; sums are
- * accumulated in another order (results agree to rounding).  Every wait of the scheduler is bounded:
+ * and the plain iteration (DVM_EINVAL otherwise).  FP32 batches sweep paired velocity groups under the
+ * batch's dvm_pairing policy, as the per-kernel launches do.  Same fixed point and stopping test; sums
+ * are accumulated in another order (results agree to rounding).  Every wait of the scheduler is bounded:
  * an idle block that finds no work for about a second gives up and the batch reports DVM_ETIMEOUT.
  * dvm_batch_timing then reports the whole launch as the sweep time and 0 for the finalize.  The
  * autotuner returns a batch to per-kernel launches.  The paper has no counterpart (Sec. II.A iterates
