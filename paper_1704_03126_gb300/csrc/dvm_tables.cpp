@@ -131,7 +131,6 @@ void build_geometry(const uint8_t *mask, int nx, int ny, bool px, bool py, bool 
     }
     return mask[(size_t)j * nx + i] != 0;
   };
-  auto id = [&](int i, int j) -> int { return (((j % ny) + ny) % ny) * nx + (((i % nx) + nx) % nx); };
   for (int j = 0; j < ny; ++j) {
     for (int i = 0; i < nx; ++i) {
       const int cell = j * nx + i;
